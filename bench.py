@@ -1,0 +1,340 @@
+"""Benchmark of the GaBP hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+
+Workload: the 4096 x 4096 roofline configuration (kappa = 0.02, 96 satellite-like tracks of
+~1.2M samples plus 200k uniform points, sigma ~ U[0.02, 0.1]), FP32 messages with compensated
+belief sums, damping 0.3.  One step = ITERS_PER_STEP synchronous GaBP iterations (fused
+kernel, CUDA-graph replays) + the FP64 relative residual + the marginal means, all on
+device-resident inputs.  The metric is node-updates/s = nodes x iterations / GPU time.
+
+`e2e` repeats the step through the public C ABI from host buffers: gabp_create from the host
+observation arrays (upload, sort, FP64 precompute), the iterations, the residual, the
+marginal means copied back to host memory, gabp_destroy.
+
+Under torchrun (N > 1) every rank solves its own instance (an ensemble member with its own
+seed): weak scaling, no collective on the data path; a barrier and a max over ranks frame
+the timed region.
+
+`--impl reference` times the CPU oracle (serial FP64 GaBP in C with OpenMP over factors) on
+the host cores, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ITERS_PER_STEP = 100
+DAMPING = 0.3
+METRIC = "GaBP node-updates/s and HBM GB/s at 4096²; time-to-1e-5 residual, warm vs cold"
+UNIT = "node-updates/s"
+WORKLOAD = "gabp_4096x4096_kappa0.02_96tracks_1.2M+200k_uniform_fp32"
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if the summary
+    was taken on the current kernel source (matching source hash)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_fused_4096_ncu.md")
+    src = os.path.join(ROOT, "paper_2404_12968_gb300", "csrc", "gabp_fused.cu")
+    dev = os.path.join(ROOT, "paper_2404_12968_gb300", "csrc", "gabp_device.cuh")
+    try:
+        h = hashlib.sha256(open(src, "rb").read() + open(dev, "rb").read()).hexdigest()[:16]
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != h:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def make_problem(rank: int, size: int = 4096):
+    """The 4096^2 roofline workload; other sizes (profiling only) scale the observation counts
+    with the area."""
+    import gabp_synth
+    if size == 4096:
+        return gabp_synth.config_roofline_4096(seed=rank)
+    f = (size / 4096.0) ** 2
+    return gabp_synth.make_problem(size, size, 0.02, rank, n_uniform=int(200_000 * f), n_tracks=96,
+                                   per_track=max(1, int(round(1_200_000 * f / 96))), sigma=(0.02, 0.1))
+
+
+def own_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2404_12968_gb300 import Solver, gabp_create, gabp_destroy, gabp_iterate, gabp_marginals, gabp_residual, _lib
+
+    rank, world, local = dist_info()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not os.path.exists(_lib.LIB_PATH):
+        raise RuntimeError("libgabp.so missing: run `python -c 'import __graft_entry__ as g; g.build()'` first")
+
+    p = make_problem(rank, args.size)
+    stream = torch.cuda.current_stream(dev)
+    s = Solver(p, precision="fp32", stream=stream.cuda_stream, device=local)
+    st = s.stats()
+    n = p.n
+    mean_dev = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def step(ev_pair=None):
+        if ev_pair is not None:
+            ev_pair[0].record(stream)
+        s.iterate(ITERS_PER_STEP, DAMPING)
+        if ev_pair is not None:
+            ev_pair[1].record(stream)
+        r = s.residual()
+        s.marginals(out_mean=mean_dev, want_var=False)
+        return r
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    residuals = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for k in range(args.steps):
+            residuals.append(step(evs[k]))
+        t1.record(stream)
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    if world > 1:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    iter_ms = sum(a.elapsed_time(b) for a, b in evs) / (args.steps * ITERS_PER_STEP)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    s.close()
+
+    # end to end through the public API from host buffers
+    obs_xy = np.ascontiguousarray(np.stack([p.obs_x, p.obs_y], 1))
+    y = np.ascontiguousarray(p.y)
+    nv = np.ascontiguousarray(p.noise_var)
+    mean_host = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+
+    def e2e_step():
+        ctx = gabp_create(p.nx, p.ny, p.kappa, obs_xy, y, nv, precision=0, stream=stream.cuda_stream,
+                          device=local)
+        try:
+            gabp_iterate(ctx, ITERS_PER_STEP, DAMPING)
+            r = gabp_residual(ctx)
+            gabp_marginals(ctx, mean_host, None)
+        finally:
+            gabp_destroy(ctx)
+        return r
+
+    e_steps = max(1, min(args.steps, 5))
+    e_ms = float("nan")
+    if not args.no_e2e:
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        tt = time.perf_counter()
+        for _ in range(e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - tt) * 1e3 / e_steps
+    if world > 1:
+        t = torch.tensor([e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+
+    node_updates = n * ITERS_PER_STEP
+    value = world * node_updates * args.steps / (ms / 1e3)
+    peak, peak_kind = measured_peak_gbs()
+    achieved = st["bytes_per_iter"] / (iter_ms / 1e3) / 1e9
+    traffic = profiled_traffic()
+    h2d = 32 * p.m + 4 * p.m + 4 * (n + 1)   # obs (x, y, value, variance) + base cells + cell pointers
+    d2h = 8 * n + 16                          # marginal means + residual scalars
+    launches_per_step = ITERS_PER_STEP + 6 + 2
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.size == 4096 else f"profiling_{args.size}", "nx": p.nx, "ny": p.ny, "kappa": p.kappa, "m": p.m,
+                   "iters_per_step": ITERS_PER_STEP, "damping": DAMPING, "kernel": "fused",
+                   "tile": [st["tile_x"], st["tile_y"]], "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (message planes 1.3 GB ping-pong)"},
+        "hbm_gbs": achieved, "rel_residual_last_step": residuals[-1],
+        "clocks": clocks,
+        "e2e": {"value": world * node_updates / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "k_fused", "algorithmic_bytes_per_launch": st["bytes_per_iter"],
+                     "launch_ms": iter_ms},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _oracle_rate(p, iters: int):
+    """Time `iters` oracle GaBP iterations on the problem; returns (node-updates/s, seconds, cores)."""
+    import oracle
+    fl = oracle.build_factors(p.nx, p.ny, p.kappa, p.obs_x, p.obs_y, p.y, p.noise_var)
+    me, ml = oracle.init_messages(fl, "cold")
+    t = time.perf_counter()
+    oracle.gabp(fl, DAMPING, iters, messages=(me, ml))
+    dt = time.perf_counter() - t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return p.n * iters / dt, dt, cores
+
+
+def cpu_baseline(p):
+    rate, dt, cores = _oracle_rate(p, 2)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"2 oracle GaBP iterations (FP64, C + OpenMP over factors) on the full "
+                      f"{p.nx}x{p.ny} workload, {dt:.1f} s"}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    p = make_problem(0)
+    import oracle
+    fl = oracle.build_factors(p.nx, p.ny, p.kappa, p.obs_x, p.obs_y, p.y, p.noise_var)
+    me, ml = oracle.init_messages(fl, "cold")
+    for _ in range(args.warmup):
+        _, _, (me, ml) = oracle.gabp(fl, DAMPING, 1, messages=(me, ml))
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        _, _, (me, ml) = oracle.gabp(fl, DAMPING, 1, messages=(me, ml))
+    dt = time.perf_counter() - t
+    value = p.n * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"one oracle GaBP iteration per step (FP64, C + OpenMP over factors) on the full "
+              f"{p.nx}x{p.ny} workload")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.size == 4096 else f"profiling_{args.size}", "nx": p.nx, "ny": p.ny, "kappa": p.kappa, "m": p.m,
+                       "iters_per_step": 1, "damping": DAMPING, "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--size", type=int, default=4096, help="grid side; 4096 is the benchmark workload")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        own_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * gabp.h — C ABI of the GB300 Gaussian belief propagation library (libgabp.so).
+ *
+ * The library solves the spatial data-assimilation posterior of "Scalable Data
+ * Assimilation with Message Passing" (Key, Takao, Giles, Deisenroth): a 2-D grid field f
+ * with the SPDE/GMRF prior of Sec. 3.1 (L f = w, L = kappa^2 I - Delta_h, prior precision
+ * gamma L^T L) and linear Gaussian observations y = H f + noise (Sec. 2.1), by synchronous
+ * ("flooding") Gaussian belief propagation in information form (Sec. 2.3, Alg. 1; App. A;
+ * Alg. 2 "Iterate MP Until Convergence").
+ *
+ * Factor graph.  One rank-1 factor exp(-(gamma/2) (l_i . f)^2) per grid cell i, with l_i
+ * the i-th row of L (the cell itself and its existing 4-neighbours; zero-Neumann
+ * boundary, i.e. kappa^2 + deg(i) on the diagonal and -1 per neighbour), and one 4-node
+ * factor exp(-(1/(2 sigma_k^2)) (h_k . f - y_k)^2) per observation, with h_k the bilinear
+ * interpolation weights of the observation's location.  Messages are (eta, Lambda) pairs
+ * per factor-variable edge; the beliefs are their sums (App. A, state update) and the
+ * marginals are mu = eta / Lambda, sigma^2 = 1 / Lambda (App. A, marginal extraction with
+ * c = 1).  The converged mean equals the exact posterior mean A^-1 b with
+ * A = gamma L^T L + H^T R^-1 H and b = H^T R^-1 y.
+ *
+ * Conventions.
+ *   - Grid: nx columns (x), ny rows (y), unit spacing, node (i, j) at x = j, y = i, stored
+ *     row-major (index i * nx + j).  Every array of per-node values has nx * ny entries in
+ *     that order.
+ *   - Observation k sits at (obs_xy[2k], obs_xy[2k+1]) = (x, y) in grid units, inside
+ *     [0, nx-1] x [0, ny-1].  Its base cell is j0 = min(floor(x), nx-2),
+ *     i0 = min(floor(y), ny-2) (so x = nx-1 falls in the last cell with weight 1 on the far
+ *     node); weights on (i0,j0), (i0,j0+1), (i0+1,j0), (i0+1,j0+1) are (1-fu)(1-fv),
+ *     fu(1-fv), (1-fu)fv, fu fv with fu = x - j0, fv = y - i0.
+ *   - Damping beta is the weight on the OLD message: m_t = beta m_{t-1} + (1 - beta) m_new
+ *     (Sec. 3.2 "Update Damping" writes the weight on the new message, eta = 1 - beta).
+ *   - Pointers named "host or device" may point to host memory (pageable or pinned) or to
+ *     device memory of the context's device; the library detects which.
+ *   - All calls are synchronous with respect to the host unless stated otherwise; they run
+ *     on the context's stream (gabp_options.stream, or a stream the context creates).
+ *   - The library never exits, traps or prints.  Every call returns a status code; the text
+ *     of the last error is available from gabp_last_error().  After GABP_ERR_CUDA the
+ *     context should be destroyed.
+ */
+#ifndef GABP_H
+#define GABP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GABP_OK 0
+#define GABP_ERR_ARG 1       /* an argument is out of range, NULL or inconsistent */
+#define GABP_ERR_OOM 2       /* device or host allocation failed */
+#define GABP_ERR_CUDA 3      /* a CUDA runtime call or kernel launch failed */
+#define GABP_ERR_DIVERGED 4  /* the residual became NaN/Inf or grew by more than 1e6 */
+#define GABP_ERR_TIMEOUT 5   /* gabp_iterate(n < 0) reached max_iters above the tolerance, or a
+                                bounded wait inside a kernel gave up (the kernel returned early;
+                                the messages of that call are incomplete) */
+#define GABP_ERR_STATE 6     /* call not valid in the context's current state */
+
+/* message precision */
+#define GABP_FP32 0          /* FP32 messages, compensated (two-term) belief sums */
+#define GABP_FP64 1          /* FP64 messages and sums */
+
+/* message initialisation (gabp_options.init) */
+#define GABP_INIT_COLD 0     /* Lambda = s a_v^2 (the factor's own diagonal term), eta = 0 */
+#define GABP_INIT_PAPER 1    /* Lambda = 1e-8, eta = 0 (Alg. 1 / Alg. 2 initialisation) */
+
+/* iteration kernel (gabp_options.kernel) */
+#define GABP_KERNEL_AUTO 0   /* GABP_KERNEL_TMA where supported, else GABP_KERNEL_FUSED */
+#define GABP_KERNEL_FUSED 1  /* one fused kernel per iteration (beliefs + all factors) */
+#define GABP_KERNEL_SPLIT 2  /* three kernels per iteration: beliefs, prior factors, obs factors */
+#define GABP_KERNEL_TMA 3    /* the fused kernel as persistent blocks fed by TMA tensor loads;
+                                FP32 and nx a multiple of 4 only */
+
+typedef struct gabp_ctx gabp_ctx;   /* opaque; owns every device buffer it allocates */
+
+typedef struct {
+    int nx;        /* columns, >= 1 (>= 2 when there are observations) */
+    int ny;        /* rows,    >= 1 (>= 2 when there are observations) */
+    double h;      /* grid spacing; must be 1.0 (unit spacing) */
+} gabp_grid;
+
+typedef struct {
+    double gamma;  /* prior precision scale gamma of P = gamma L^T L (Sec. 3.1); > 0 */
+    int boundary;  /* 0 = zero-Neumann (the only boundary implemented) */
+} gabp_prior;
+
+typedef struct {
+    int precision;    /* GABP_FP32 (default) or GABP_FP64 */
+    int init;         /* GABP_INIT_COLD (default) or GABP_INIT_PAPER */
+    int kernel;       /* GABP_KERNEL_AUTO (default), _FUSED or _SPLIT */
+    int tile_x;       /* fused-kernel tile width in cells; 0 = the default / autotuned shape */
+    int tile_y;       /* fused-kernel tile height in cells; 0 = the default / autotuned shape.
+                         GABP_KERNEL_FUSED: 32x8, 32x16, 32x32, 64x8, 64x16, 128x8;
+                         GABP_KERNEL_TMA: 32x16, 32x32, 64x8, 64x16 */
+    double tol;       /* relative-residual target of gabp_iterate(n < 0); default 1e-5 */
+    int check_every;  /* iterations between residual checks when n < 0; default 50 */
+    int max_iters;    /* iteration cap when n < 0; default 200000 */
+    int device;       /* CUDA device ordinal; -1 (default) = the calling thread's device */
+    void *stream;     /* cudaStream_t to run on; NULL (default) = a stream the context owns */
+    int debug_flags;  /* 0 (default).  Bit 0 is a test hook for failure detection: every launch of
+                         the TMA kernel first waits on an mbarrier that nothing completes, so its
+                         bounded wait runs out (after ~2 ms) and gabp_iterate returns
+                         GABP_ERR_TIMEOUT without having changed the messages. */
+} gabp_options;
+
+typedef struct {
+    int64_t iterations;     /* iterations run since create / the last re-initialisation */
+    double last_residual;   /* last relative residual computed (NaN if none yet) */
+    int64_t n;              /* nodes */
+    int64_t m;              /* observations */
+    int64_t edges;          /* factor-variable edges: sum of prior factor sizes + 4 m */
+    int precision;          /* GABP_FP32 / GABP_FP64 */
+    int kernel;             /* the iteration kernel in use (GABP_KERNEL_FUSED / _SPLIT / _TMA) */
+    int tile_x, tile_y;     /* tile shape in use by the fused kernel */
+    double bytes_per_iter;  /* algorithmic HBM bytes of one iteration (messages read and
+                               written once, plus the static observation data) */
+} gabp_stats;
+
+/* Fill *opt with the defaults listed above. */
+void gabp_default_options(gabp_options *opt);
+
+/*
+ * Build the factor graph (Sec. 3.1 "Derivation of the Factor Graph"; Sec. 3.2
+ * "Including Observations", here with bilinear observation rows) and initialise messages.
+ *
+ *   out        receives the new context (set to NULL on failure).
+ *   grid       grid size; grid.h must be 1.0.
+ *   kappa      SPDE parameter kappa of (kappa^2 - Delta) (Eq. for the Matern SPDE); > 0.
+ *   prior      prior options; NULL = { gamma = 1, zero-Neumann }.
+ *   m          number of observations, >= 0.
+ *   obs_xy     2m doubles (x0, y0, x1, y1, ...), HOST memory.
+ *   y          m observed values, HOST memory.
+ *   noise_var  m observation noise variances sigma_k^2 > 0, HOST memory.
+ *   opt        options; NULL = defaults.
+ *
+ * The host arrays are read during the call only (the caller keeps ownership).  Observation
+ * locations are validated (finite, inside the grid) and sorted by base cell on the host;
+ * the interpolation weights and 1/sigma^2 are then computed on the GPU in FP64 and stored
+ * in the message precision.  Errors: GABP_ERR_ARG for invalid sizes, NaN/Inf values,
+ * non-positive kappa/gamma/variances or locations outside the grid; GABP_ERR_OOM;
+ * GABP_ERR_CUDA.
+ */
+int gabp_create(gabp_ctx **out, gabp_grid grid, double kappa, const gabp_prior *prior,
+                int64_t m, const double *obs_xy, const double *y, const double *noise_var,
+                const gabp_options *opt);
+
+/*
+ * Run synchronous damped GaBP iterations (Alg. 2, "Iterate MP Until Convergence", with the
+ * damping of Sec. 3.2): every new message uses only the previous iteration's messages.
+ *
+ *   n_iters >= 0: run exactly n_iters iterations.
+ *   n_iters <  0: iterate until the relative residual ||b - A mu|| / ||b|| (FP64) is at most
+ *                 opt.tol, checking every opt.check_every iterations; returns
+ *                 GABP_ERR_TIMEOUT after opt.max_iters iterations and GABP_ERR_DIVERGED if
+ *                 the residual becomes non-finite or grows by 1e6 over its best value.
+ *   damping       beta in [0, 1): weight on the old message.
+ *
+ * Runs as CUDA-graph replays on the context's stream and synchronises before returning.
+ */
+int gabp_iterate(gabp_ctx *ctx, int n_iters, double damping);
+
+/*
+ * Marginals from the current messages (App. A, marginal extraction, c = 1):
+ * mean = eta / Lambda and var = 1 / Lambda per node, written as FP64.
+ *   mean  nx*ny doubles, host or device; must not be NULL.
+ *   var   nx*ny doubles, host or device; may be NULL.
+ */
+int gabp_marginals(gabp_ctx *ctx, double *mean, double *var);
+
+/*
+ * Relative residual ||b - A mu||_2 / ||b||_2 of the current mean, computed in FP64 on the
+ * GPU (A applied as gamma L (L mu) + H^T R^-1 (H mu), deterministic reductions).  This is the
+ * convergence measure used in place of the paper's message-change early stop (App. B).
+ *   rel_residual  one double, host memory.  If ||b|| = 0 (no observations) the absolute
+ *                 norm ||A mu|| is returned instead.
+ */
+int gabp_residual(gabp_ctx *ctx, double *rel_residual);
+
+/*
+ * Re-initialise the messages from predicted beliefs (a warm start; the closest paper
+ * counterpart is the multigrid "Upscale Messages" of App. B, which also seeds messages
+ * from a previous estimate): every edge into node v gets Lambda = lam0[v] / deg(v) and
+ * eta = mu0[v] * Lambda, deg(v) being the number of factors touching v, so that the
+ * initial beliefs equal (mu0, lam0).
+ *   mu0, lam0   nx*ny doubles each, host or device; lam0 > 0.
+ */
+int gabp_warm_start(gabp_ctx *ctx, const double *mu0, const double *lam0);
+
+/* Re-initialise the messages with the context's initialisation mode (opt.init). */
+int gabp_reset(gabp_ctx *ctx);
+
+/*
+ * Copy the current messages out / in (checkpoint and resume).  The buffer is opaque:
+ * gabp_message_bytes() bytes, host or device, valid only for a context with the same
+ * problem and precision.
+ */
+int64_t gabp_message_bytes(const gabp_ctx *ctx);
+int gabp_get_messages(gabp_ctx *ctx, void *buf);
+int gabp_set_messages(gabp_ctx *ctx, const void *buf);
+
+/* Statistics of the context (host struct). */
+int gabp_get_stats(const gabp_ctx *ctx, gabp_stats *stats);
+
+/* Text of the last error on this context ("" if none); valid until the next call. */
+const char *gabp_last_error(const gabp_ctx *ctx);
+
+/* Text of the last error of a gabp_create call that failed on this thread. */
+const char *gabp_create_error(void);
+
+/* Release the context and all its device memory.  NULL is ignored. */
+void gabp_destroy(gabp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GABP_H */

@@ -25,6 +25,7 @@
  * pragma because every factor of a synchronous iteration is independent (Alg. 1 note that
  * the inner loops are independent); the result does not depend on the thread count.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -50,8 +51,11 @@ int orc_version(void) { return 1; }
  *     V_v = 1/s + sum_{u != v} a_u^2 / lam_c[u]          (variance of a_v x_v - r given the rest)
  *     m_v = r - sum_{u != v} a_u * eta_c[u] / lam_c[u]  (its mean)
  *     Lambda_out[v] = a_v^2 / V_v,   eta_out[v] = a_v * m_v / V_v.
- * Slots with a_u = 0 are skipped.  A slot u != v with a_u != 0 and lam_c[u] <= 0 carries
- * no information about x_u, so V_v is infinite and the message is (0, 0).
+ * Slots with a_u = 0 are skipped.  A slot u != v with a_u != 0 whose cavity precision is
+ * below the smallest normal double (non-positive, or so small that 1/lam_c overflows) carries
+ * no information about x_u, so V_v is infinite and the message is (0, 0).  (Such cavities do
+ * occur: away from the observations the precision recursion can drive the neighbour-slot
+ * messages of the cell factors geometrically towards zero.)
  */
 void orc_factor_update(int k, const double *a, double s, double r, const double *lam_c,
                        const double *eta_c, double *lam_out, double *eta_out) {
@@ -61,7 +65,7 @@ void orc_factor_update(int k, const double *a, double s, double r, const double 
         int infinite = 0;
         for (int u = 0; u < k; ++u) {
             if (u == v || a[u] == 0.0) continue;
-            if (!(lam_c[u] > 0.0)) { infinite = 1; break; }
+            if (!(lam_c[u] >= DBL_MIN)) { infinite = 1; break; }
             V += a[u] * a[u] / lam_c[u];
             mv -= a[u] * (eta_c[u] / lam_c[u]);
         }

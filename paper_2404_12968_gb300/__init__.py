@@ -1,0 +1,190 @@
+"""GB300 Gaussian belief propagation for spatial data assimilation.
+
+Python binding of the C ABI in ``include/gabp.h`` (libgabp.so).  The functions keep the C
+names (``gabp_create``, ``gabp_iterate``, ``gabp_marginals``, ``gabp_residual``, ...) and
+only marshal arguments; ``Solver`` is a small convenience wrapper that owns a context.
+
+Array arguments may be NumPy arrays (host memory) or CUDA torch tensors (device memory);
+both must be contiguous float64 where the C ABI takes ``double*``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (GABP_ERR_ARG, GABP_ERR_CUDA, GABP_ERR_DIVERGED, GABP_ERR_OOM,  # noqa: F401
+                   GABP_ERR_STATE, GABP_ERR_TIMEOUT, GABP_FP32, GABP_FP64, GABP_INIT_COLD,
+                   GABP_INIT_PAPER, GABP_KERNEL_AUTO, GABP_KERNEL_FUSED, GABP_KERNEL_SPLIT, GABP_KERNEL_TMA,
+                   GABP_OK, GabpError)
+
+__all__ = [
+    "gabp_default_options", "gabp_create", "gabp_iterate", "gabp_marginals", "gabp_residual",
+    "gabp_warm_start", "gabp_reset", "gabp_message_bytes", "gabp_get_messages",
+    "gabp_set_messages", "gabp_get_stats", "gabp_destroy", "Solver", "GabpError",
+]
+
+
+def _ptr(a):
+    """Address of a contiguous float64 host array or CUDA tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(rc: int, ctx=None, create: bool = False):
+    if rc != GABP_OK:
+        L = _lib.load()
+        msg = (L.gabp_create_error() if create else L.gabp_last_error(ctx)) or b""
+        raise GabpError(rc, msg.decode(errors="replace"))
+
+
+def gabp_default_options(**over) -> _lib.gabp_options:
+    o = _lib.gabp_options()
+    _lib.load().gabp_default_options(ctypes.byref(o))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+def gabp_create(nx: int, ny: int, kappa: float, obs_xy, y, noise_var, *, gamma: float = 1.0,
+                options: _lib.gabp_options | None = None, **opts) -> int:
+    """Create a context; returns its handle.  ``obs_xy`` is (m, 2) float64 host data."""
+    L = _lib.load()
+    obs_xy = np.ascontiguousarray(obs_xy, np.float64).reshape(-1)
+    y = np.ascontiguousarray(y, np.float64).reshape(-1)
+    noise_var = np.ascontiguousarray(noise_var, np.float64).reshape(-1)
+    m = y.shape[0]
+    if obs_xy.shape[0] != 2 * m or noise_var.shape[0] != m:
+        raise ValueError("obs_xy must be (m, 2) and noise_var (m,)")
+    o = options if options is not None else gabp_default_options(**opts)
+    prior = _lib.gabp_prior(gamma, 0)
+    h = ctypes.c_void_p()
+    rc = L.gabp_create(ctypes.byref(h), _lib.gabp_grid(nx, ny, 1.0), float(kappa), ctypes.byref(prior),
+                       m, obs_xy.ctypes.data if m else None, y.ctypes.data if m else None,
+                       noise_var.ctypes.data if m else None, ctypes.byref(o))
+    _check(rc, create=True)
+    return h.value
+
+
+def gabp_iterate(ctx: int, n_iters: int, damping: float) -> None:
+    _check(_lib.load().gabp_iterate(ctx, int(n_iters), float(damping)), ctx)
+
+
+def gabp_marginals(ctx: int, mean, var=None) -> None:
+    _check(_lib.load().gabp_marginals(ctx, _ptr(mean), _ptr(var)), ctx)
+
+
+def gabp_residual(ctx: int) -> float:
+    out = ctypes.c_double()
+    _check(_lib.load().gabp_residual(ctx, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def gabp_warm_start(ctx: int, mu0, lam0) -> None:
+    _check(_lib.load().gabp_warm_start(ctx, _ptr(mu0), _ptr(lam0)), ctx)
+
+
+def gabp_reset(ctx: int) -> None:
+    _check(_lib.load().gabp_reset(ctx), ctx)
+
+
+def gabp_message_bytes(ctx: int) -> int:
+    return int(_lib.load().gabp_message_bytes(ctx))
+
+
+def gabp_get_messages(ctx: int, buf) -> None:
+    _check(_lib.load().gabp_get_messages(ctx, _ptr(buf)), ctx)
+
+
+def gabp_set_messages(ctx: int, buf) -> None:
+    _check(_lib.load().gabp_set_messages(ctx, _ptr(buf)), ctx)
+
+
+def gabp_get_stats(ctx: int) -> dict:
+    s = _lib.gabp_stats()
+    _check(_lib.load().gabp_get_stats(ctx, ctypes.byref(s)), ctx)
+    return {f: getattr(s, f) for f, _ in s._fields_}
+
+
+def gabp_destroy(ctx: int) -> None:
+    if ctx:
+        _lib.load().gabp_destroy(ctx)
+
+
+class Solver:
+    """Owns one context.  ``Solver(problem, precision='fp32')`` with a ``gabp_synth.Problem``-like
+    object (fields nx, ny, kappa, obs_x, obs_y, y, noise_var)."""
+
+    def __init__(self, problem=None, *, nx=None, ny=None, kappa=None, obs_xy=None, y=None,
+                 noise_var=None, precision: str = "fp32", gamma: float = 1.0, **opts):
+        if problem is not None:
+            nx, ny, kappa = problem.nx, problem.ny, problem.kappa
+            obs_xy = np.stack([problem.obs_x, problem.obs_y], axis=1)
+            y, noise_var = problem.y, problem.noise_var
+        opts.setdefault("precision", GABP_FP64 if precision == "fp64" else GABP_FP32)
+        self.nx, self.ny = int(nx), int(ny)
+        self.ctx = gabp_create(self.nx, self.ny, kappa, obs_xy, y, noise_var, gamma=gamma, **opts)
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny
+
+    def iterate(self, n_iters: int, damping: float) -> "Solver":
+        gabp_iterate(self.ctx, n_iters, damping)
+        return self
+
+    def residual(self) -> float:
+        return gabp_residual(self.ctx)
+
+    def marginals(self, out_mean=None, out_var=None, want_var: bool = True):
+        mean = out_mean if out_mean is not None else np.empty(self.n)
+        var = out_var if out_var is not None else (np.empty(self.n) if want_var else None)
+        gabp_marginals(self.ctx, mean, var)
+        return mean, var
+
+    def warm_start(self, mu0, lam0) -> None:
+        gabp_warm_start(self.ctx, np.ascontiguousarray(mu0, np.float64).reshape(-1)
+                        if isinstance(mu0, np.ndarray) else mu0,
+                        np.ascontiguousarray(lam0, np.float64).reshape(-1)
+                        if isinstance(lam0, np.ndarray) else lam0)
+
+    def reset(self) -> None:
+        gabp_reset(self.ctx)
+
+    def get_messages(self) -> np.ndarray:
+        buf = np.empty(gabp_message_bytes(self.ctx), np.uint8)
+        gabp_get_messages(self.ctx, buf)
+        return buf
+
+    def set_messages(self, buf: np.ndarray) -> None:
+        gabp_set_messages(self.ctx, np.ascontiguousarray(buf))
+
+    def stats(self) -> dict:
+        return gabp_get_stats(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            gabp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

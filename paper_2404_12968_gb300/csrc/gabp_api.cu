@@ -1,0 +1,571 @@
+// Host engine and C ABI of libgabp (declared in include/gabp.h).
+//
+// A context owns the device buffers of one problem: ping-pong message buffers, the sorted
+// observation data, the residual scratch.  Iterations run as CUDA-graph replays of a chunk
+// of fused (or split) iteration kernels on the context's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gabp.h"
+#include "gabp_internal.h"
+
+using gabp::DevProblem;
+
+struct gabp_ctx {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap = nullptr;   // private stream used only for graph capture
+    DevProblem p{};
+    gabp_options opt{};
+    int kernel = GABP_KERNEL_FUSED;
+    gabp::FusedShape shape{64, 16};
+    gabp::TmaMaps maps;
+    int cur = 0;                  // buffer holding the current messages
+    int64_t iters = 0;
+    double last_res = NAN;
+    int64_t edges = 0;
+    double bytes_per_iter = 0.0;
+    std::string err;
+    std::vector<void *> allocs;
+    double *stage = nullptr;      // 2 n doubles of device staging for host <-> device transfers
+    double *hscal = nullptr;      // pinned host copy of p.scal
+    cudaGraphExec_t gexec = nullptr;
+    int g_len = 0;
+    double g_beta = -1.0;
+    int g_kernel = -1;
+};
+
+namespace {
+
+thread_local std::string t_create_err;
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(gabp_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(gabp_ctx *c, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    cudaGetLastError();   // clear a non-sticky error
+    return fail(c, e == cudaErrorMemoryAllocation ? GABP_ERR_OOM : GABP_ERR_CUDA, m);
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+int dalloc(gabp_ctx *c, void **ptr, size_t bytes, const char *what) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    c->allocs.push_back(*ptr);
+    return GABP_OK;
+}
+
+bool is_device_ptr(const void *ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void drop_graph(gabp_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->g_len = 0;
+    c->g_beta = -1.0;
+    c->g_kernel = -1;
+}
+
+cudaError_t launch_iteration(gabp_ctx *c, int src, double beta, cudaStream_t st) {
+    if (c->kernel == GABP_KERNEL_SPLIT) return gabp::launch_split_iteration(c->p, src, beta, st);
+    if (c->kernel == GABP_KERNEL_TMA) return gabp::launch_tma_iteration(c->p, c->maps, src, beta, st);
+    return gabp::launch_fused_iteration(c->p, src, beta, c->shape, st);
+}
+
+// A kernel's bounded wait gave up: report it (and clear the flag).
+int check_device_error(gabp_ctx *c) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, c->p.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "error flag copy");
+    CK(cudaStreamSynchronize(c->stream), "error flag sync");
+    if (h) {
+        CK(cudaMemsetAsync(c->p.err, 0, sizeof(int), c->stream), "error flag reset");
+        CK(cudaStreamSynchronize(c->stream), "error flag sync");
+        return fail(c, GABP_ERR_TIMEOUT, "a bounded wait inside the iteration kernel gave up");
+    }
+    return GABP_OK;
+}
+
+// Graph of `len` (even) iterations starting from buffer 0.
+int ensure_graph(gabp_ctx *c, int len, double beta) {
+    if (c->gexec && c->g_len == len && c->g_beta == beta && c->g_kernel == c->kernel) return GABP_OK;
+    drop_graph(c);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t le = cudaSuccess;
+    for (int t = 0; t < len && le == cudaSuccess; ++t) le = launch_iteration(c, t & 1, beta, c->cap);
+    cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, le, "iteration launch during capture");
+    }
+    if (ee != cudaSuccess) return cuda_fail(c, ee, "end capture");
+    cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail(c, ie, "graph instantiate");
+    }
+    c->g_len = len;
+    c->g_beta = beta;
+    c->g_kernel = c->kernel;
+    return GABP_OK;
+}
+
+int run_iterations(gabp_ctx *c, int64_t count, double beta) {
+    const int G = 20;
+    if (count > 0 && c->cur == 1) {
+        CK(launch_iteration(c, 1, beta, c->stream), "iteration launch");
+        c->cur = 0;
+        --count;
+        ++c->iters;
+    }
+    if (count >= G) {
+        int rc = ensure_graph(c, G, beta);
+        if (rc != GABP_OK) return rc;
+        while (count >= G) {
+            CK(cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+            count -= G;
+            c->iters += G;
+        }
+    }
+    while (count > 0) {
+        CK(launch_iteration(c, c->cur, beta, c->stream), "iteration launch");
+        c->cur ^= 1;
+        --count;
+        ++c->iters;
+    }
+    return GABP_OK;
+}
+
+int compute_residual(gabp_ctx *c, double *out) {
+    CK(gabp::launch_residual(c->p, c->cur, c->stream), "residual kernels");
+    CK(cudaMemcpyAsync(c->hscal, c->p.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "residual copy");
+    CK(cudaStreamSynchronize(c->stream), "residual sync");
+    const double r2 = c->hscal[0], b2 = c->hscal[1];
+    *out = b2 > 0.0 ? std::sqrt(r2) / std::sqrt(b2) : std::sqrt(r2);
+    c->last_res = *out;
+    return GABP_OK;
+}
+
+int init_messages(gabp_ctx *c) {
+    CK(gabp::launch_init_cold(c->p, 0, c->opt.init == GABP_INIT_PAPER, c->stream), "init kernels");
+    c->cur = 0;
+    c->iters = 0;
+    c->last_res = NAN;
+    return GABP_OK;
+}
+
+void free_all(gabp_ctx *c) {
+    drop_graph(c);
+    for (void *q : c->allocs) cudaFree(q);
+    c->allocs.clear();
+    if (c->hscal) cudaFreeHost(c->hscal);
+    c->hscal = nullptr;
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    c->cap = nullptr;
+    c->stream = nullptr;
+}
+
+size_t tsize(const gabp_ctx *c) { return c->p.prec ? sizeof(double) : sizeof(float); }
+
+int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *prior, int64_t m,
+                const double *obs_xy, const double *y, const double *noise_var) {
+    const int nx = grid.nx, ny = grid.ny;
+    if (nx < 1 || ny < 1) return fail(c, GABP_ERR_ARG, "grid sizes must be >= 1");
+    if ((int64_t)nx * ny > (int64_t)1 << 30) return fail(c, GABP_ERR_ARG, "grid larger than 2^30 nodes");
+    if (!(grid.h == 1.0)) return fail(c, GABP_ERR_ARG, "grid spacing h must be 1");
+    if (!(kappa > 0.0) || !std::isfinite(kappa)) return fail(c, GABP_ERR_ARG, "kappa must be finite and > 0");
+    const double gamma = prior ? prior->gamma : 1.0;
+    if (!(gamma > 0.0) || !std::isfinite(gamma)) return fail(c, GABP_ERR_ARG, "gamma must be finite and > 0");
+    if (prior && prior->boundary != 0) return fail(c, GABP_ERR_ARG, "only the zero-Neumann boundary (0) is implemented");
+    if (m < 0 || m > ((int64_t)1 << 28)) return fail(c, GABP_ERR_ARG, "observation count out of range");
+    if (m > 0 && (!obs_xy || !y || !noise_var)) return fail(c, GABP_ERR_ARG, "observation arrays must not be NULL");
+    if (m > 0 && (nx < 2 || ny < 2)) return fail(c, GABP_ERR_ARG, "observations need a grid of at least 2 x 2");
+    const gabp_options &o = c->opt;
+    if (o.precision != GABP_FP32 && o.precision != GABP_FP64) return fail(c, GABP_ERR_ARG, "bad precision");
+    if (o.init != GABP_INIT_COLD && o.init != GABP_INIT_PAPER) return fail(c, GABP_ERR_ARG, "bad init mode");
+    if (o.kernel < GABP_KERNEL_AUTO || o.kernel > GABP_KERNEL_TMA) return fail(c, GABP_ERR_ARG, "bad kernel");
+    if (!(o.tol > 0.0) || o.check_every < 1 || o.max_iters < 1) return fail(c, GABP_ERR_ARG, "bad tol/check_every/max_iters");
+    if ((o.tile_x || o.tile_y) && o.kernel != GABP_KERNEL_TMA && !gabp::fused_shape_supported(o.tile_x, o.tile_y))
+        return fail(c, GABP_ERR_ARG, "unsupported tile shape");
+    if ((o.tile_x || o.tile_y) && o.kernel == GABP_KERNEL_TMA && !gabp::tma_shape_supported(o.tile_x, o.tile_y))
+        return fail(c, GABP_ERR_ARG, "unsupported tile shape for the TMA kernel");
+
+    const int64_t n = (int64_t)nx * ny;
+    // validate observations and sort them by base cell (stable counting sort, FP64 floor)
+    std::vector<int> base((size_t)m);
+    for (int64_t k = 0; k < m; ++k) {
+        const double x = obs_xy[2 * k], yy = obs_xy[2 * k + 1];
+        if (!std::isfinite(x) || !std::isfinite(yy) || !std::isfinite(y[k]) || !std::isfinite(noise_var[k]))
+            return fail(c, GABP_ERR_ARG, "non-finite observation data at index " + std::to_string(k));
+        if (x < 0.0 || x > nx - 1.0 || yy < 0.0 || yy > ny - 1.0)
+            return fail(c, GABP_ERR_ARG, "observation " + std::to_string(k) + " outside the grid");
+        if (!(noise_var[k] > 0.0)) return fail(c, GABP_ERR_ARG, "noise variance must be > 0");
+        int j0 = (int)std::floor(x), i0 = (int)std::floor(yy);
+        if (j0 > nx - 2) j0 = nx - 2;
+        if (i0 > ny - 2) i0 = ny - 2;
+        base[(size_t)k] = i0 * nx + j0;
+    }
+    std::vector<int> optr((size_t)n + 1, 0);
+    for (int64_t k = 0; k < m; ++k) optr[(size_t)base[(size_t)k] + 1] += 1;
+    for (int64_t v = 0; v < n; ++v) optr[(size_t)v + 1] += optr[(size_t)v];
+    std::vector<int> fillpos(optr.begin(), optr.end() - 1);
+    std::vector<int> sbase((size_t)m);
+    std::vector<double> sxy((size_t)(2 * m)), sy((size_t)m), svar((size_t)m);
+    for (int64_t k = 0; k < m; ++k) {
+        const int b = base[(size_t)k];
+        const int dst = fillpos[(size_t)b]++;
+        sbase[(size_t)dst] = b;
+        sxy[2 * (size_t)dst] = obs_xy[2 * k];
+        sxy[2 * (size_t)dst + 1] = obs_xy[2 * k + 1];
+        sy[(size_t)dst] = y[k];
+        svar[(size_t)dst] = noise_var[k];
+    }
+
+    DevProblem &p = c->p;
+    p.nx = nx;
+    p.ny = ny;
+    p.n = n;
+    p.m = m;
+    p.prec = o.precision;
+    p.gamma = gamma;
+    p.debug_stall = (o.debug_flags & 1) ? 1 : 0;
+    for (int d = 0; d <= 4; ++d) p.aC[d] = kappa * kappa + (double)d;
+    const size_t T = tsize(c);
+    int rc;
+    void *q;
+    for (int b = 0; b < 2; ++b) {
+        if ((rc = dalloc(c, &p.P[b], 5 * (size_t)n * 2 * T, "alloc prior messages"))) return rc;
+        if ((rc = dalloc(c, &p.O[b], 8 * (size_t)m * T, "alloc obs messages"))) return rc;
+    }
+    if ((rc = dalloc(c, &q, (size_t)m * sizeof(int), "alloc obs base"))) return rc;
+    p.obase = (const int *)q;
+    if ((rc = dalloc(c, &q, 4 * (size_t)m * T, "alloc obs weights"))) return rc;
+    p.ow = q;
+    if ((rc = dalloc(c, &q, 2 * (size_t)m * T, "alloc obs values"))) return rc;
+    p.ovar = q;
+    if ((rc = dalloc(c, &q, 4 * (size_t)m * sizeof(double), "alloc obs weights fp64"))) return rc;
+    p.ow64 = (const double *)q;
+    if ((rc = dalloc(c, &q, 2 * (size_t)m * sizeof(double), "alloc obs values fp64"))) return rc;
+    p.oys64 = (const double *)q;
+    if ((rc = dalloc(c, &q, ((size_t)n + 1) * sizeof(int), "alloc obs pointers"))) return rc;
+    p.optr = (const int *)q;
+    if ((rc = dalloc(c, &p.belief, (size_t)n * 4 * T, "alloc beliefs"))) return rc;
+    if ((rc = dalloc(c, &q, (size_t)n * sizeof(double), "alloc residual scratch"))) return rc;
+    p.mu64 = (double *)q;
+    if ((rc = dalloc(c, &q, (size_t)n * sizeof(double), "alloc residual scratch"))) return rc;
+    p.z64 = (double *)q;
+    if ((rc = dalloc(c, &q, (size_t)m * sizeof(double), "alloc residual scratch"))) return rc;
+    p.e64 = (double *)q;
+    if ((rc = dalloc(c, &q, gabp::RES_BLOCKS * sizeof(double), "alloc partial sums"))) return rc;
+    p.part = (double *)q;
+    if ((rc = dalloc(c, &q, 2 * sizeof(double), "alloc scalars"))) return rc;
+    p.scal = (double *)q;
+    if ((rc = dalloc(c, &q, sizeof(int), "alloc error flag"))) return rc;
+    p.err = (int *)q;
+    CK(cudaMemsetAsync(p.err, 0, sizeof(int), c->stream), "memset");
+    if ((rc = dalloc(c, &q, 2 * (size_t)n * sizeof(double), "alloc staging"))) return rc;
+    c->stage = (double *)q;
+    CK(cudaMallocHost((void **)&c->hscal, 2 * sizeof(double)), "alloc pinned scalars");
+    CK(cudaMemsetAsync(p.scal, 0, 2 * sizeof(double), c->stream), "memset");
+
+    // upload the sorted observations; FP64 precompute of weights and 1/sigma^2 on the GPU
+    if (m > 0) {
+        double *raw = nullptr;
+        CK(cudaMalloc((void **)&raw, 4 * (size_t)m * sizeof(double)), "alloc raw observations");
+        cudaError_t e = cudaMemcpyAsync(raw, sxy.data(), 2 * (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 2 * m, sy.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 3 * m, svar.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync((void *)p.obase, sbase.data(), (size_t)m * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = gabp::launch_obs_precompute(p, raw, raw + 2 * m, raw + 3 * m, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(raw);
+        if (e != cudaSuccess) return cuda_fail(c, e, "observation upload/precompute");
+    }
+    CK(cudaMemcpyAsync((void *)p.optr, optr.data(), ((size_t)n + 1) * sizeof(int), cudaMemcpyHostToDevice, c->stream),
+       "upload obs pointers");
+    CK(gabp::launch_rhs_norm(p, c->stream), "rhs norm");
+    if ((rc = init_messages(c))) return rc;
+    CK(cudaStreamSynchronize(c->stream), "create sync");
+
+    // iteration kernel and tile shape
+    const bool tma_ok = gabp::tma_problem_supported(p);
+    if (o.kernel == GABP_KERNEL_TMA && !tma_ok)
+        return fail(c, GABP_ERR_ARG, "the TMA kernel needs FP32 messages and nx a multiple of 4");
+    if (o.kernel == GABP_KERNEL_SPLIT) c->kernel = GABP_KERNEL_SPLIT;
+    else if (o.kernel == GABP_KERNEL_TMA || (o.kernel == GABP_KERNEL_AUTO && tma_ok)) c->kernel = GABP_KERNEL_TMA;
+    else c->kernel = GABP_KERNEL_FUSED;
+    if (c->kernel == GABP_KERNEL_TMA) {
+        c->shape = o.tile_x ? gabp::FusedShape{o.tile_x, o.tile_y} : gabp::FusedShape{64, 16};
+        CK(gabp::make_tma_maps(p, c->shape.tx, c->shape.ty, c->maps), "tensor map encode");
+    } else if (o.tile_x) {
+        c->shape = {o.tile_x, o.tile_y};
+    } else {
+        c->shape = p.prec ? gabp::FusedShape{32, 8} : gabp::FusedShape{64, 16};
+    }
+    c->edges = 5 * n - 2 * (int64_t)(nx + ny) + 4 * m;
+    const double ebytes = 4.0 * (double)T;    // (eta, Lambda) read + write per edge
+    c->bytes_per_iter = ebytes * (double)c->edges + 5.0 * (double)T * (double)m;
+    return GABP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gabp_default_options(gabp_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = GABP_FP32;
+    o->init = GABP_INIT_COLD;
+    o->kernel = GABP_KERNEL_AUTO;
+    o->tol = 1e-5;
+    o->check_every = 50;
+    o->max_iters = 200000;
+    o->device = -1;
+    o->stream = nullptr;
+}
+
+const char *gabp_create_error(void) { return t_create_err.c_str(); }
+
+int gabp_create(gabp_ctx **out, gabp_grid grid, double kappa, const gabp_prior *prior, int64_t m,
+                const double *obs_xy, const double *y, const double *noise_var, const gabp_options *opt) {
+    t_create_err.clear();
+    if (!out) {
+        t_create_err = "out must not be NULL";
+        return GABP_ERR_ARG;
+    }
+    *out = nullptr;
+    gabp_ctx *c = new (std::nothrow) gabp_ctx();
+    if (!c) {
+        t_create_err = "host allocation failed";
+        return GABP_ERR_OOM;
+    }
+    if (opt) c->opt = *opt;
+    else gabp_default_options(&c->opt);
+    int dev = c->opt.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        t_create_err = "no CUDA device";
+        delete c;
+        return GABP_ERR_CUDA;
+    }
+    c->dev = dev;
+    int rc = GABP_OK;
+    {
+        DeviceGuard g(dev);
+        if (!g.ok) {
+            rc = fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
+        } else {
+            cudaError_t e = cudaSuccess;
+            if (c->opt.stream) {
+                c->stream = (cudaStream_t)c->opt.stream;
+            } else {
+                e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+                c->own_stream = e == cudaSuccess;
+            }
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+            if (e != cudaSuccess) rc = cuda_fail(c, e, "stream create");
+            else rc = create_impl(c, grid, kappa, prior, m, obs_xy, y, noise_var);
+        }
+        if (rc != GABP_OK) {
+            t_create_err = c->err;
+            free_all(c);
+        }
+    }
+    if (rc != GABP_OK) {
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return GABP_OK;
+}
+
+int gabp_iterate(gabp_ctx *c, int n_iters, double damping) {
+    if (!c) return GABP_ERR_ARG;
+    if (!(damping >= 0.0 && damping < 1.0)) return fail(c, GABP_ERR_ARG, "damping must be in [0, 1)");
+    DeviceGuard g(c->dev);
+    if (!g.ok) return fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
+    c->err.clear();
+    if (n_iters >= 0) {
+        const int cur0 = c->cur;
+        const int64_t iters0 = c->iters;
+        int rc = run_iterations(c, n_iters, damping);
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(c->stream), "iterate sync");
+        rc = check_device_error(c);
+        if (rc) {   // a kernel gave up: point back at the messages the call started from
+            c->cur = cur0;
+            c->iters = iters0;
+        }
+        return rc;
+    }
+    double best = INFINITY, res = NAN;
+    int64_t done = 0;
+    for (;;) {
+        int rc = compute_residual(c, &res);
+        if (rc) return rc;
+        if (!std::isfinite(res)) return fail(c, GABP_ERR_DIVERGED, "residual is not finite");
+        if (res <= c->opt.tol) return GABP_OK;
+        if (res > 1e6 * best) return fail(c, GABP_ERR_DIVERGED, "residual grew by more than 1e6");
+        best = res < best ? res : best;
+        if (done >= c->opt.max_iters)
+            return fail(c, GABP_ERR_TIMEOUT, "max_iters reached with residual " + std::to_string(res));
+        int64_t chunk = c->opt.check_every;
+        if (done + chunk > c->opt.max_iters) chunk = c->opt.max_iters - done;
+        rc = run_iterations(c, chunk, damping);
+        if (rc) return rc;
+        if ((rc = check_device_error(c))) return rc;
+        done += chunk;
+    }
+}
+
+int gabp_residual(gabp_ctx *c, double *rel) {
+    if (!c || !rel) return c ? fail(c, GABP_ERR_ARG, "rel_residual must not be NULL") : GABP_ERR_ARG;
+    DeviceGuard g(c->dev);
+    if (!g.ok) return fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
+    return compute_residual(c, rel);
+}
+
+int gabp_marginals(gabp_ctx *c, double *mean, double *var) {
+    if (!c) return GABP_ERR_ARG;
+    if (!mean) return fail(c, GABP_ERR_ARG, "mean must not be NULL");
+    DeviceGuard g(c->dev);
+    if (!g.ok) return fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
+    const int64_t n = c->p.n;
+    const bool dmean = is_device_ptr(mean);
+    const bool dvar = var ? is_device_ptr(var) : true;
+    double *kmean = dmean ? mean : c->stage;
+    double *kvar = var ? (dvar ? var : c->stage + n) : nullptr;
+    CK(gabp::launch_marginals(c->p, c->cur, kmean, kvar, c->stream), "marginal kernels");
+    if (!dmean) CK(cudaMemcpyAsync(mean, kmean, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy mean");
+    if (var && !dvar) CK(cudaMemcpyAsync(var, kvar, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy var");
+    CK(cudaStreamSynchronize(c->stream), "marginals sync");
+    return GABP_OK;
+}
+
+int gabp_warm_start(gabp_ctx *c, const double *mu0, const double *lam0) {
+    if (!c) return GABP_ERR_ARG;
+    if (!mu0 || !lam0) return fail(c, GABP_ERR_ARG, "mu0 and lam0 must not be NULL");
+    DeviceGuard g(c->dev);
+    if (!g.ok) return fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
+    const int64_t n = c->p.n;
+    const double *dm = mu0, *dl = lam0;
+    if (!is_device_ptr(mu0)) {
+        CK(cudaMemcpyAsync(c->stage, mu0, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy mu0");
+        dm = c->stage;
+    }
+    if (!is_device_ptr(lam0)) {
+        CK(cudaMemcpyAsync(c->stage + n, lam0, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy lam0");
+        dl = c->stage + n;
+    }
+    CK(gabp::launch_init_warm(c->p, 0, dm, dl, c->stream), "warm init kernels");
+    CK(cudaStreamSynchronize(c->stream), "warm start sync");
+    c->cur = 0;
+    c->iters = 0;
+    c->last_res = NAN;
+    return GABP_OK;
+}
+
+int gabp_reset(gabp_ctx *c) {
+    if (!c) return GABP_ERR_ARG;
+    DeviceGuard g(c->dev);
+    if (!g.ok) return fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
+    int rc = init_messages(c);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream), "reset sync");
+    return GABP_OK;
+}
+
+int64_t gabp_message_bytes(const gabp_ctx *c) {
+    if (!c) return -1;
+    const int64_t T = c->p.prec ? 8 : 4;
+    return 10 * c->p.n * T + 8 * c->p.m * T;
+}
+
+int gabp_get_messages(gabp_ctx *c, void *buf) {
+    if (!c || !buf) return c ? fail(c, GABP_ERR_ARG, "buffer must not be NULL") : GABP_ERR_ARG;
+    DeviceGuard g(c->dev);
+    const size_t T = tsize(c);
+    const size_t pb = 10 * (size_t)c->p.n * T, ob = 8 * (size_t)c->p.m * T;
+    CK(cudaMemcpyAsync(buf, c->p.P[c->cur], pb, cudaMemcpyDefault, c->stream), "copy messages");
+    if (ob) CK(cudaMemcpyAsync((char *)buf + pb, c->p.O[c->cur], ob, cudaMemcpyDefault, c->stream), "copy messages");
+    CK(cudaStreamSynchronize(c->stream), "messages sync");
+    return GABP_OK;
+}
+
+int gabp_set_messages(gabp_ctx *c, const void *buf) {
+    if (!c || !buf) return c ? fail(c, GABP_ERR_ARG, "buffer must not be NULL") : GABP_ERR_ARG;
+    DeviceGuard g(c->dev);
+    const size_t T = tsize(c);
+    const size_t pb = 10 * (size_t)c->p.n * T, ob = 8 * (size_t)c->p.m * T;
+    CK(cudaMemcpyAsync(c->p.P[0], buf, pb, cudaMemcpyDefault, c->stream), "copy messages");
+    if (ob) CK(cudaMemcpyAsync(c->p.O[0], (const char *)buf + pb, ob, cudaMemcpyDefault, c->stream), "copy messages");
+    CK(cudaStreamSynchronize(c->stream), "messages sync");
+    c->cur = 0;
+    return GABP_OK;
+}
+
+int gabp_get_stats(const gabp_ctx *c, gabp_stats *s) {
+    if (!c || !s) return GABP_ERR_ARG;
+    s->iterations = c->iters;
+    s->last_residual = c->last_res;
+    s->n = c->p.n;
+    s->m = c->p.m;
+    s->edges = c->edges;
+    s->precision = c->p.prec;
+    s->kernel = c->kernel;
+    s->tile_x = c->shape.tx;
+    s->tile_y = c->shape.ty;
+    s->bytes_per_iter = c->bytes_per_iter;
+    return GABP_OK;
+}
+
+const char *gabp_last_error(const gabp_ctx *c) { return c ? c->err.c_str() : ""; }
+
+void gabp_destroy(gabp_ctx *c) {
+    if (!c) return;
+    {
+        DeviceGuard g(c->dev);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        free_all(c);
+    }
+    delete c;
+}
+
+}  // extern "C"

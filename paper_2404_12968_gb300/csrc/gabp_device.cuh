@@ -1,0 +1,141 @@
+// Device-side arithmetic of one GaBP iteration, shared by the split and fused kernels.
+//
+// Message layout in HBM (both precisions, T = float or double):
+//   prior messages: 5 planes of n (eta, Lambda) pairs, "outgoing" order: plane d at cell c
+//     holds the message from the factor of cell c to node c + off_d, d = C, W, E, S, N
+//     (off = 0, -1, +1, -nx, +nx).  Slots whose neighbour does not exist hold (0, 0).
+//   observation messages: per observation (sorted by base cell), 8 values
+//     eta_0..eta_3, Lambda_0..Lambda_3, one per bilinear corner.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gabp {
+
+enum { DIR_C = 0, DIR_W = 1, DIR_E = 2, DIR_S = 3, DIR_N = 4 };
+
+template <typename T> struct vec2;
+template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+template <typename T> using T2 = typename vec2<T>::type;
+
+// Smallest normal number: a cavity precision below it has an overflowing reciprocal and is
+// treated as carrying no information.
+template <typename T> __device__ __forceinline__ T tiny_normal();
+template <> __device__ __forceinline__ float tiny_normal<float>() { return 1.17549435e-38f; }
+template <> __device__ __forceinline__ double tiny_normal<double>() { return 2.2250738585072014e-308; }
+
+template <typename T> __device__ __forceinline__ T pos_inf();
+template <> __device__ __forceinline__ float pos_inf<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double pos_inf<double>() {
+    return __longlong_as_double(0x7ff0000000000000LL);
+}
+
+// Reciprocal.  FP32: the hardware approximation (rcp.approx, <= 1 ulp) refined by one
+// Newton-Raphson step r <- r + r (1 - x r), which roughly squares the relative error.  The
+// callers never pass 0, a denormal or an infinity (cavities are guarded at the smallest
+// normal number and an infinite V is tested before the call).  FP64: IEEE division.
+template <typename T> __device__ __forceinline__ T recip(T x);
+template <> __device__ __forceinline__ float recip<float>(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    const float e = fmaf(-x, r, 1.0f);
+    return fmaf(r, e, r);
+}
+template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
+
+// Two-term compensated sum (TwoSum accumulation, Knuth TAOCP vol. 2 4.2.2): hi + lo carries
+// the running sum to about twice the working precision.  Used for the belief sums so that
+// the cavity (belief minus one message) keeps its relative accuracy even when that message
+// dominates the belief.
+template <typename T> struct CompSum {
+    T hi, lo;
+    __device__ __forceinline__ CompSum() : hi(T(0)), lo(T(0)) {}
+    __device__ __forceinline__ void add(T x) {
+        T t = hi + x;
+        T z = t - hi;
+        T e = (hi - (t - z)) + (x - z);
+        hi = t;
+        lo += e;
+    }
+    // renormalise so that hi = fl(hi + lo)
+    __device__ __forceinline__ void finish() {
+        T t = hi + lo;
+        lo = lo - (t - hi);
+        hi = t;
+    }
+};
+
+// A compensated belief: (eta_hi, eta_lo, lam_hi, lam_lo).
+template <typename T> struct Belief {
+    T ehi, elo, lhi, llo;
+};
+
+// Cavity of one edge: the belief minus the edge's own incoming message, evaluated as
+// (hi - own) + lo (App. A, variable-to-factor message).
+template <typename T>
+__device__ __forceinline__ void cavity(const Belief<T> &b, T own_eta, T own_lam, T &eta_c, T &lam_c) {
+    lam_c = (b.lhi - own_lam) + b.llo;
+    eta_c = (b.ehi - own_eta) + b.elo;
+}
+
+// Factor-to-variable messages of a rank-1 factor exp(-(1/(2 var)) (a . x - r)^2) with K slots
+// (App. A factor-to-variable message generalised to K variables): for every slot v
+//   V_v = var + sum_{u != v} a_u^2 / lam_u,   m_v = r - sum_{u != v} a_u eta_u / lam_u,
+//   Lambda_v = a_v^2 / V_v,                   eta_v = a_v m_v / V_v.
+// Leave-one-out sums come from prefix and suffix sums (no "total minus own" cancellation).
+// Slots with a_u = 0 are skipped; a slot with a_u != 0 whose cavity precision is below the
+// smallest normal number (non-positive, or so small that its reciprocal overflows) carries no
+// information: it makes V infinite for every other slot, whose message is then exactly (0, 0).
+template <typename T, int K>
+__device__ __forceinline__ void factor_messages(const T (&a)[K], T var, T r, const T (&lam)[K],
+                                                const T (&eta)[K], T (&L)[K], T (&E)[K]) {
+    T t[K], p[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        if (a[u] == T(0)) {
+            t[u] = T(0);
+            p[u] = T(0);
+        } else if (!(lam[u] >= tiny_normal<T>())) {
+            t[u] = pos_inf<T>();
+            p[u] = T(0);
+        } else {
+            T rl = recip(lam[u]);
+            t[u] = a[u] * a[u] * rl;
+            p[u] = a[u] * (eta[u] * rl);
+        }
+    }
+    T preV[K], preM[K];
+    preV[0] = var;
+    preM[0] = T(0);
+#pragma unroll
+    for (int v = 1; v < K; ++v) {
+        preV[v] = preV[v - 1] + t[v - 1];
+        preM[v] = preM[v - 1] + p[v - 1];
+    }
+    T sufV = T(0), sufM = T(0);
+#pragma unroll
+    for (int v = K - 1; v >= 0; --v) {
+        T V = preV[v] + sufV;
+        T M = preM[v] + sufM;
+        // V >= var > 0; an infinite V (a slot without information) gives the message (0, 0)
+        const bool inf_v = V == pos_inf<T>();
+        const T rV = inf_v ? T(0) : recip(V);
+        L[v] = a[v] * a[v] * rV;
+        E[v] = inf_v ? T(0) : a[v] * (r - M) * rV;
+        sufV += t[v];
+        sufM += p[v];
+    }
+}
+
+// Damped update m_t = beta m_{t-1} + (1 - beta) m_new, evaluated as m_new + beta (m_{t-1} - m_new).
+template <typename T> __device__ __forceinline__ T damp(T old, T fresh, T beta) {
+    return fresh + beta * (old - fresh);
+}
+
+// Number of existing 4-neighbours of node (i, j).
+__device__ __forceinline__ int grid_degree(int i, int j, int nx, int ny) {
+    return (j > 0) + (j < nx - 1) + (i > 0) + (i < ny - 1);
+}
+
+}  // namespace gabp

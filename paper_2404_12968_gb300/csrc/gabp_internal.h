@@ -1,0 +1,74 @@
+// Internal interface between the host engine (gabp_api.cu) and the kernel translation units.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gabp {
+
+// Device-resident description of one problem instance.  All pointers are device pointers.
+// Message buffers are typed by the precision (float or double) of the instance.
+struct DevProblem {
+    int nx, ny;
+    int64_t n, m;
+    int prec;            // 0 = FP32, 1 = FP64
+    double gamma;        // prior scale (factor precision of every cell factor)
+    double aC[5];        // kappa^2 + deg for deg = 0..4 (FP64; kernels round to T)
+    void *P[2];          // prior messages, ping-pong: 5 * n (eta, Lambda) pairs
+    void *O[2];          // observation messages, ping-pong: 8 * m values
+    const int *obase;    // m base-cell indices (sorted ascending)
+    const void *ow;      // 4 * m bilinear weights (T)
+    const void *ovar;    // 2 * m (y, sigma^2) pairs (T)
+    const double *ow64;  // 4 * m weights, FP64 (residual)
+    const double *oys64; // 2 * m (y, 1/sigma^2) pairs, FP64 (residual)
+    const int *optr;     // n + 1: observations with base cell c are optr[c] .. optr[c+1]-1
+    void *belief;        // n compensated beliefs (4 T each), split kernels only
+    double *mu64;        // n, residual scratch
+    double *z64;         // n, residual scratch
+    double *e64;         // m, residual scratch
+    double *part;        // residual partial sums (RES_BLOCKS)
+    double *scal;        // 2 doubles: [0] = ||r||^2, [1] = ||b||^2
+    int *err;            // device error flag (a bounded wait in a kernel gave up)
+    int debug_stall;     // test hook: the TMA kernel first waits on a barrier nothing completes
+};
+
+constexpr int RES_BLOCKS = 1024;   // fixed partition of the deterministic residual reduction
+
+// ---- split path (gabp_split.cu) ----
+cudaError_t launch_split_iteration(const DevProblem &p, int src, double beta, cudaStream_t st);
+cudaError_t launch_beliefs(const DevProblem &p, int src, cudaStream_t st);
+cudaError_t launch_init_cold(const DevProblem &p, int dst, int paper, cudaStream_t st);
+cudaError_t launch_init_warm(const DevProblem &p, int dst, const double *mu0, const double *lam0,
+                             cudaStream_t st);
+cudaError_t launch_obs_precompute(const DevProblem &p, const double *raw_xy, const double *raw_y,
+                                  const double *raw_var, cudaStream_t st);
+cudaError_t launch_rhs_norm(const DevProblem &p, cudaStream_t st);   // scal[1] = ||b||^2
+// residual of the messages in buffer src; leaves ||r||^2 in scal[0] (beliefs recomputed)
+cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st);
+cudaError_t launch_marginals(const DevProblem &p, int src, double *mean, double *var,
+                             cudaStream_t st);
+
+// ---- fused path (gabp_fused.cu) ----
+struct FusedShape {
+    int tx, ty;   // tile in cells
+};
+bool fused_shape_supported(int tx, int ty);
+cudaError_t launch_fused_iteration(const DevProblem &p, int src, double beta, FusedShape shape,
+                                   cudaStream_t st);
+size_t fused_smem_bytes(int prec, FusedShape shape);
+
+// ---- TMA-fed persistent fused path, FP32 (gabp_fused_tma.cu) ----
+struct TmaMaps {
+    CUtensorMap planes[2];   // message planes of buffer 0 / 1
+    CUtensorMap optr;        // observations-by-base-cell index
+    int tx = 0, ty = 0;
+    bool valid = false;
+};
+bool tma_shape_supported(int tx, int ty);
+bool tma_problem_supported(const DevProblem &p);
+cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps);
+size_t tma_smem_bytes(int tx, int ty);
+cudaError_t launch_tma_iteration(const DevProblem &p, const TmaMaps &maps, int src, double beta,
+                                 cudaStream_t st);
+
+}  // namespace gabp

@@ -1,0 +1,437 @@
+// Split GaBP iteration (three kernels: beliefs, prior factors, observation factors) and the
+// auxiliary kernels: message initialisation, FP64 observation precompute, FP64 residual and
+// marginals.  The split iteration is the plain form of one synchronous iteration; the fused
+// kernel (gabp_fused.cu) computes the same messages in one pass.
+#include "gabp_device.cuh"
+#include "gabp_internal.h"
+
+namespace gabp {
+
+namespace {
+
+constexpr int TPB = 256;
+
+template <typename T> struct __align__(4 * sizeof(T)) BeliefStore {
+    T ehi, elo, lhi, llo;
+};
+
+__device__ __forceinline__ int64_t gtid() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }
+
+inline unsigned nblocks(int64_t count) { return (unsigned)((count + TPB - 1) / TPB); }
+
+// ---- beliefs (App. A, state update): sum of every incoming message, compensated ----
+template <typename T> __global__ void k_beliefs(DevProblem p, int src) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const int nx = p.nx, ny = p.ny;
+    const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
+    const T2<T> *P = (const T2<T> *)p.P[src];
+    const T *O = (const T *)p.O[src];
+    const int64_t n = p.n;
+    CompSum<T> se, sl;
+    T2<T> q = P[DIR_C * n + v];
+    se.add(q.x);
+    sl.add(q.y);
+    if (j > 0) { q = P[DIR_E * n + v - 1]; se.add(q.x); sl.add(q.y); }
+    if (j < nx - 1) { q = P[DIR_W * n + v + 1]; se.add(q.x); sl.add(q.y); }
+    if (i > 0) { q = P[DIR_N * n + v - nx]; se.add(q.x); sl.add(q.y); }
+    if (i < ny - 1) { q = P[DIR_S * n + v + nx]; se.add(q.x); sl.add(q.y); }
+    if (p.m > 0) {
+        const int *optr = p.optr;
+        // corner 0: base v; corner 1: base v-1; corner 2: base v-nx; corner 3: base v-nx-1
+        for (int k = optr[v]; k < optr[v + 1]; ++k) { se.add(O[8 * (int64_t)k + 0]); sl.add(O[8 * (int64_t)k + 4]); }
+        if (j > 0)
+            for (int k = optr[v - 1]; k < optr[v]; ++k) { se.add(O[8 * (int64_t)k + 1]); sl.add(O[8 * (int64_t)k + 5]); }
+        if (i > 0)
+            for (int k = optr[v - nx]; k < optr[v - nx + 1]; ++k) { se.add(O[8 * (int64_t)k + 2]); sl.add(O[8 * (int64_t)k + 6]); }
+        if (i > 0 && j > 0)
+            for (int k = optr[v - nx - 1]; k < optr[v - nx]; ++k) { se.add(O[8 * (int64_t)k + 3]); sl.add(O[8 * (int64_t)k + 7]); }
+    }
+    se.finish();
+    sl.finish();
+    BeliefStore<T> b;
+    b.ehi = se.hi; b.elo = se.lo; b.lhi = sl.hi; b.llo = sl.lo;
+    ((BeliefStore<T> *)p.belief)[v] = b;
+}
+
+template <typename T> __device__ __forceinline__ Belief<T> load_belief(const DevProblem &p, int64_t v) {
+    BeliefStore<T> s = ((const BeliefStore<T> *)p.belief)[v];
+    Belief<T> b;
+    b.ehi = s.ehi; b.elo = s.elo; b.lhi = s.lhi; b.llo = s.llo;
+    return b;
+}
+
+// ---- prior cell factors: a = row c of L over (C, W, E, S, N), var = 1/gamma, r = 0 ----
+template <typename T> __global__ void k_prior(DevProblem p, int src, T beta) {
+    const int64_t c = gtid();
+    if (c >= p.n) return;
+    const int nx = p.nx, ny = p.ny;
+    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    const int64_t n = p.n;
+    const T2<T> *P = (const T2<T> *)p.P[src];
+    T2<T> *Q = (T2<T> *)p.P[src ^ 1];
+    const int deg = grid_degree(i, j, nx, ny);
+    const T a[5] = {T(p.aC[deg]), j > 0 ? T(-1) : T(0), j < nx - 1 ? T(-1) : T(0),
+                    i > 0 ? T(-1) : T(0), i < ny - 1 ? T(-1) : T(0)};
+    const int64_t node[5] = {c, c - 1, c + 1, c - nx, c + nx};
+    T2<T> own[5];
+    T lam[5], eta[5];
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+        own[u] = P[u * n + c];
+        if (a[u] != T(0)) {
+            cavity(load_belief<T>(p, node[u]), own[u].x, own[u].y, eta[u], lam[u]);
+        } else {
+            lam[u] = T(1);
+            eta[u] = T(0);
+        }
+    }
+    T L[5], E[5];
+    factor_messages<T, 5>(a, T(1.0 / p.gamma), T(0), lam, eta, L, E);
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+        T2<T> out;
+        if (a[u] != T(0)) {
+            out.x = damp(own[u].x, E[u], beta);
+            out.y = damp(own[u].y, L[u], beta);
+        } else {
+            out.x = T(0);
+            out.y = T(0);
+        }
+        Q[u * n + c] = out;
+    }
+}
+
+// ---- observation factors: a = bilinear weights, var = sigma^2, r = y ----
+template <typename T> __global__ void k_obs(DevProblem p, int src, T beta) {
+    const int64_t k = gtid();
+    if (k >= p.m) return;
+    const int nx = p.nx;
+    const int64_t b = p.obase[k];
+    const T *W = (const T *)p.ow;
+    const T *YV = (const T *)p.ovar;
+    const T *O = (const T *)p.O[src];
+    T *Q = (T *)p.O[src ^ 1];
+    const T a[4] = {W[4 * k], W[4 * k + 1], W[4 * k + 2], W[4 * k + 3]};
+    const int64_t node[4] = {b, b + 1, b + nx, b + nx + 1};
+    T oe[4], ol[4], lam[4], eta[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        oe[u] = O[8 * k + u];
+        ol[u] = O[8 * k + 4 + u];
+        cavity(load_belief<T>(p, node[u]), oe[u], ol[u], eta[u], lam[u]);
+    }
+    T L[4], E[4];
+    factor_messages<T, 4>(a, YV[2 * k + 1], YV[2 * k], lam, eta, L, E);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        Q[8 * k + u] = damp(oe[u], E[u], beta);
+        Q[8 * k + 4 + u] = damp(ol[u], L[u], beta);
+    }
+}
+
+// ---- initialisation ----
+template <typename T> __global__ void k_init_prior(DevProblem p, int dst, int paper) {
+    const int64_t c = gtid();
+    if (c >= p.n) return;
+    const int nx = p.nx, ny = p.ny;
+    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    const int deg = grid_degree(i, j, nx, ny);
+    const double a[5] = {p.aC[deg], j > 0 ? -1.0 : 0.0, j < nx - 1 ? -1.0 : 0.0, i > 0 ? -1.0 : 0.0,
+                         i < ny - 1 ? -1.0 : 0.0};
+    T2<T> *Q = (T2<T> *)p.P[dst];
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+        T2<T> o;
+        o.x = T(0);
+        o.y = a[u] == 0.0 ? T(0) : (paper ? T(1e-8) : T(p.gamma * a[u] * a[u]));
+        Q[u * p.n + c] = o;
+    }
+}
+
+template <typename T> __global__ void k_init_obs(DevProblem p, int dst, int paper) {
+    const int64_t k = gtid();
+    if (k >= p.m) return;
+    T *Q = (T *)p.O[dst];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const double w = p.ow64[4 * k + u];
+        Q[8 * k + u] = T(0);
+        Q[8 * k + 4 + u] = paper ? T(1e-8) : T(p.oys64[2 * k + 1] * w * w);
+    }
+}
+
+// number of factor slots touching node v (prior factors + observation corners)
+__device__ __forceinline__ int node_slots(const DevProblem &p, int64_t v) {
+    const int nx = p.nx, ny = p.ny;
+    const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
+    int d = 1 + grid_degree(i, j, nx, ny);
+    if (p.m > 0) {
+        const int *o = p.optr;
+        d += o[v + 1] - o[v];
+        if (j > 0) d += o[v] - o[v - 1];
+        if (i > 0) d += o[v - nx + 1] - o[v - nx];
+        if (i > 0 && j > 0) d += o[v - nx] - o[v - nx - 1];
+    }
+    return d;
+}
+
+template <typename T>
+__global__ void k_init_warm_prior(DevProblem p, int dst, const double *mu0, const double *lam0) {
+    const int64_t c = gtid();
+    if (c >= p.n) return;
+    const int nx = p.nx, ny = p.ny;
+    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    const bool exists[5] = {true, j > 0, j < nx - 1, i > 0, i < ny - 1};
+    const int64_t node[5] = {c, c - 1, c + 1, c - nx, c + nx};
+    T2<T> *Q = (T2<T> *)p.P[dst];
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+        T2<T> o;
+        o.x = T(0);
+        o.y = T(0);
+        if (exists[u]) {
+            const double L = lam0[node[u]] / (double)node_slots(p, node[u]);
+            o.x = T(mu0[node[u]] * L);
+            o.y = T(L);
+        }
+        Q[u * p.n + c] = o;
+    }
+}
+
+template <typename T>
+__global__ void k_init_warm_obs(DevProblem p, int dst, const double *mu0, const double *lam0) {
+    const int64_t k = gtid();
+    if (k >= p.m) return;
+    const int64_t b = p.obase[k];
+    const int64_t node[4] = {b, b + 1, b + p.nx, b + p.nx + 1};
+    T *Q = (T *)p.O[dst];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const double L = lam0[node[u]] / (double)node_slots(p, node[u]);
+        Q[8 * k + u] = T(mu0[node[u]] * L);
+        Q[8 * k + 4 + u] = T(L);
+    }
+}
+
+// ---- FP64 observation precompute (the factor precompute of the observation factors) ----
+template <typename T>
+__global__ void k_obs_precompute(DevProblem p, const double *xy, const double *yv, const double *var) {
+    const int64_t k = gtid();
+    if (k >= p.m) return;
+    const int nx = p.nx;
+    const int b = p.obase[k];
+    const int i0 = b / nx, j0 = b - i0 * nx;
+    const double fu = xy[2 * k] - (double)j0;
+    const double fv = xy[2 * k + 1] - (double)i0;
+    const double w[4] = {(1.0 - fu) * (1.0 - fv), fu * (1.0 - fv), (1.0 - fu) * fv, fu * fv};
+    T *W = (T *)p.ow;
+    T *YV = (T *)p.ovar;
+    double *W64 = (double *)p.ow64;
+    double *YS64 = (double *)p.oys64;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        W[4 * k + u] = T(w[u]);
+        W64[4 * k + u] = w[u];
+    }
+    YV[2 * k] = T(yv[k]);
+    YV[2 * k + 1] = T(var[k]);
+    YS64[2 * k] = yv[k];
+    YS64[2 * k + 1] = 1.0 / var[k];
+}
+
+// ---- deterministic FP64 reductions: fixed grid, fixed per-thread order, smem tree ----
+__device__ __forceinline__ double block_sum(double x) {
+    __shared__ double sh[TPB];
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int s = TPB / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+__global__ void k_final_sum(const double *part, int count, double *out) {
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < count; q += TPB) acc += part[q];
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// sum over observation edges into node v of w_kc * val_k (FP64), corners in fixed order
+__device__ __forceinline__ double obs_gather64(const DevProblem &p, int64_t v, int i, int j,
+                                               const double *val, int stride, int off) {
+    const int nx = p.nx;
+    const int *o = p.optr;
+    double acc = 0.0;
+    for (int k = o[v]; k < o[v + 1]; ++k) acc += p.ow64[4 * (int64_t)k + 0] * val[stride * (int64_t)k + off];
+    if (j > 0)
+        for (int k = o[v - 1]; k < o[v]; ++k) acc += p.ow64[4 * (int64_t)k + 1] * val[stride * (int64_t)k + off];
+    if (i > 0)
+        for (int k = o[v - nx]; k < o[v - nx + 1]; ++k) acc += p.ow64[4 * (int64_t)k + 2] * val[stride * (int64_t)k + off];
+    if (i > 0 && j > 0)
+        for (int k = o[v - nx - 1]; k < o[v - nx]; ++k) acc += p.ow64[4 * (int64_t)k + 3] * val[stride * (int64_t)k + off];
+    return acc;
+}
+
+// ||b||^2 with b_v = sum over incoming observation edges of w * s * y
+__global__ void k_rhs_norm(DevProblem p) {
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * TPB;
+    for (int64_t v = gtid(); v < p.n; v += stride) {
+        const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+        double bv = 0.0;
+        if (p.m > 0) {
+            // w * (s * y): gather w_kc * y_k * s_k
+            const int *o = p.optr;
+            const int nx = p.nx;
+            for (int k = o[v]; k < o[v + 1]; ++k) bv += p.ow64[4 * (int64_t)k] * p.oys64[2 * (int64_t)k] * p.oys64[2 * (int64_t)k + 1];
+            if (j > 0)
+                for (int k = o[v - 1]; k < o[v]; ++k) bv += p.ow64[4 * (int64_t)k + 1] * p.oys64[2 * (int64_t)k] * p.oys64[2 * (int64_t)k + 1];
+            if (i > 0)
+                for (int k = o[v - nx]; k < o[v - nx + 1]; ++k) bv += p.ow64[4 * (int64_t)k + 2] * p.oys64[2 * (int64_t)k] * p.oys64[2 * (int64_t)k + 1];
+            if (i > 0 && j > 0)
+                for (int k = o[v - nx - 1]; k < o[v - nx]; ++k) bv += p.ow64[4 * (int64_t)k + 3] * p.oys64[2 * (int64_t)k] * p.oys64[2 * (int64_t)k + 1];
+        }
+        acc += bv * bv;
+    }
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) p.part[blockIdx.x] = s;
+}
+
+template <typename T> __global__ void k_mu(DevProblem p) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const BeliefStore<T> b = ((const BeliefStore<T> *)p.belief)[v];
+    p.mu64[v] = ((double)b.ehi + (double)b.elo) / ((double)b.lhi + (double)b.llo);
+}
+
+__global__ void k_obs_err(DevProblem p) {
+    const int64_t k = gtid();
+    if (k >= p.m) return;
+    const int64_t b = p.obase[k];
+    const double *w = p.ow64 + 4 * k;
+    const double hm = w[0] * p.mu64[b] + w[1] * p.mu64[b + 1] + w[2] * p.mu64[b + p.nx] +
+                      w[3] * p.mu64[b + p.nx + 1];
+    p.e64[k] = p.oys64[2 * k + 1] * (hm - p.oys64[2 * k]);
+}
+
+// (L x)_v = (kappa^2 + deg) x_v - sum of existing neighbours
+__device__ __forceinline__ double apply_L(const DevProblem &p, const double *x, int64_t v, int i, int j) {
+    const int nx = p.nx, ny = p.ny;
+    double s = p.aC[grid_degree(i, j, nx, ny)] * x[v];
+    if (j > 0) s -= x[v - 1];
+    if (j < nx - 1) s -= x[v + 1];
+    if (i > 0) s -= x[v - nx];
+    if (i < ny - 1) s -= x[v + nx];
+    return s;
+}
+
+__global__ void k_Lmu(DevProblem p) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+    p.z64[v] = apply_L(p, p.mu64, v, i, j);
+}
+
+// r = b - A mu = -gamma L (L mu) - H^T S (H mu - y); accumulate ||r||^2
+__global__ void k_res(DevProblem p) {
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * TPB;
+    for (int64_t v = gtid(); v < p.n; v += stride) {
+        const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+        double r = -p.gamma * apply_L(p, p.z64, v, i, j);
+        if (p.m > 0) r -= obs_gather64(p, v, i, j, p.e64, 1, 0);
+        acc += r * r;
+    }
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) p.part[blockIdx.x] = s;
+}
+
+template <typename T> __global__ void k_marg(DevProblem p, double *mean, double *var) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const BeliefStore<T> b = ((const BeliefStore<T> *)p.belief)[v];
+    const double L = (double)b.lhi + (double)b.llo;
+    mean[v] = ((double)b.ehi + (double)b.elo) / L;
+    if (var) var[v] = 1.0 / L;
+}
+
+template <typename T> cudaError_t split_iteration(const DevProblem &p, int src, double beta, cudaStream_t st) {
+    k_beliefs<T><<<nblocks(p.n), TPB, 0, st>>>(p, src);
+    k_prior<T><<<nblocks(p.n), TPB, 0, st>>>(p, src, (T)beta);
+    if (p.m > 0) k_obs<T><<<nblocks(p.m), TPB, 0, st>>>(p, src, (T)beta);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_split_iteration(const DevProblem &p, int src, double beta, cudaStream_t st) {
+    return p.prec ? split_iteration<double>(p, src, beta, st) : split_iteration<float>(p, src, beta, st);
+}
+
+cudaError_t launch_beliefs(const DevProblem &p, int src, cudaStream_t st) {
+    if (p.prec) k_beliefs<double><<<nblocks(p.n), TPB, 0, st>>>(p, src);
+    else k_beliefs<float><<<nblocks(p.n), TPB, 0, st>>>(p, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_cold(const DevProblem &p, int dst, int paper, cudaStream_t st) {
+    if (p.prec) {
+        k_init_prior<double><<<nblocks(p.n), TPB, 0, st>>>(p, dst, paper);
+        if (p.m > 0) k_init_obs<double><<<nblocks(p.m), TPB, 0, st>>>(p, dst, paper);
+    } else {
+        k_init_prior<float><<<nblocks(p.n), TPB, 0, st>>>(p, dst, paper);
+        if (p.m > 0) k_init_obs<float><<<nblocks(p.m), TPB, 0, st>>>(p, dst, paper);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_warm(const DevProblem &p, int dst, const double *mu0, const double *lam0,
+                             cudaStream_t st) {
+    if (p.prec) {
+        k_init_warm_prior<double><<<nblocks(p.n), TPB, 0, st>>>(p, dst, mu0, lam0);
+        if (p.m > 0) k_init_warm_obs<double><<<nblocks(p.m), TPB, 0, st>>>(p, dst, mu0, lam0);
+    } else {
+        k_init_warm_prior<float><<<nblocks(p.n), TPB, 0, st>>>(p, dst, mu0, lam0);
+        if (p.m > 0) k_init_warm_obs<float><<<nblocks(p.m), TPB, 0, st>>>(p, dst, mu0, lam0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_obs_precompute(const DevProblem &p, const double *xy, const double *yv,
+                                  const double *var, cudaStream_t st) {
+    if (p.m == 0) return cudaSuccess;
+    if (p.prec) k_obs_precompute<double><<<nblocks(p.m), TPB, 0, st>>>(p, xy, yv, var);
+    else k_obs_precompute<float><<<nblocks(p.m), TPB, 0, st>>>(p, xy, yv, var);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_norm(const DevProblem &p, cudaStream_t st) {
+    k_rhs_norm<<<RES_BLOCKS, TPB, 0, st>>>(p);
+    k_final_sum<<<1, TPB, 0, st>>>(p.part, RES_BLOCKS, p.scal + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st) {
+    cudaError_t e = launch_beliefs(p, src, st);
+    if (e != cudaSuccess) return e;
+    if (p.prec) k_mu<double><<<nblocks(p.n), TPB, 0, st>>>(p);
+    else k_mu<float><<<nblocks(p.n), TPB, 0, st>>>(p);
+    if (p.m > 0) k_obs_err<<<nblocks(p.m), TPB, 0, st>>>(p);
+    k_Lmu<<<nblocks(p.n), TPB, 0, st>>>(p);
+    k_res<<<RES_BLOCKS, TPB, 0, st>>>(p);
+    k_final_sum<<<1, TPB, 0, st>>>(p.part, RES_BLOCKS, p.scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_marginals(const DevProblem &p, int src, double *mean, double *var, cudaStream_t st) {
+    cudaError_t e = launch_beliefs(p, src, st);
+    if (e != cudaSuccess) return e;
+    if (p.prec) k_marg<double><<<nblocks(p.n), TPB, 0, st>>>(p, mean, var);
+    else k_marg<float><<<nblocks(p.n), TPB, 0, st>>>(p, mean, var);
+    return cudaGetLastError();
+}
+
+}  // namespace gabp

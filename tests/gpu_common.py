@@ -1,0 +1,54 @@
+"""Helpers shared by the GPU tests: building the library on the GPU machine, running the CUDA path
+and the oracle on the same seeded inputs, and decoding the message buffer."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+import gabp_synth
+
+
+def ensure_built():
+    from paper_2404_12968_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2404_12968_gb300.build import build
+        build()
+    _lib.load()
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def oracle_factors(orc, p: gabp_synth.Problem, gamma: float = 1.0):
+    return orc.build_factors(p.nx, p.ny, p.kappa, p.obs_x, p.obs_y, p.y, p.noise_var, gamma)
+
+
+def solver(p: gabp_synth.Problem, precision="fp32", **opts):
+    from paper_2404_12968_gb300 import Solver
+    return Solver(p, precision=precision, **opts)
+
+
+def decode_messages(buf: np.ndarray, p: gabp_synth.Problem, precision="fp32"):
+    """Split the opaque message buffer into prior planes (5, n, 2) and obs messages (m, 8).
+
+    The layout is the library's (documented in its device header): 5 prior planes of
+    (eta, Lambda) pairs in outgoing order C, W, E, S, N, then 8 values per observation in
+    base-cell-sorted order."""
+    dt = np.float64 if precision == "fp64" else np.float32
+    a = buf.view(dt)
+    n, m = p.n, p.m
+    prior = a[: 10 * n].reshape(5, n, 2)
+    obs = a[10 * n: 10 * n + 8 * m].reshape(m, 8)
+    return prior, obs
+
+
+def sorted_obs_order(orc, p: gabp_synth.Problem):
+    """Stable order of observations by base cell (the oracle's own bilinear rule)."""
+    i0, j0, w = orc.bilinear_base_weights(p.nx, p.ny, p.obs_x, p.obs_y)
+    base = i0 * p.nx + j0
+    return np.argsort(base, kind="stable"), base, w

@@ -111,6 +111,11 @@ def test_nonpositive_cavity_gives_zero_messages(orc):
     assert lo[0] == 0 and eo[0] == 0 and lo[2] == 0 and eo[2] == 0
     L1, E1 = _schur_message(a, 1.0, 0.3, np.array([1.0, 0.0, 2.0]), np.array([0.1, 0.2, 0.3]), 1)
     assert lo[1] == pytest.approx(L1) and eo[1] == pytest.approx(E1)
+    # a positive cavity below the smallest normal double (reciprocal overflows) counts as no
+    # information too: the other slots get exactly (0, 0), never NaN
+    lo, eo = orc.factor_update(a, 1.0, 0.3, np.array([1.0, 1e-310, 2.0]), np.array([0.1, 0.5, 0.3]))
+    assert lo[0] == 0 and eo[0] == 0 and lo[2] == 0 and eo[2] == 0
+    assert np.all(np.isfinite(lo)) and np.all(np.isfinite(eo))
     # zero coefficients are skipped even when the cavity is non-positive
     lo, eo = orc.factor_update(np.array([1.0, 0.0]), 2.0, 0.5, np.array([1.0, -1.0]),
                                np.array([0.0, 0.0]))
