@@ -66,11 +66,13 @@ extern "C" {
 #define GABP_INIT_PAPER 1    /* Lambda = 1e-8, eta = 0 (Alg. 1 / Alg. 2 initialisation) */
 
 /* iteration kernel (gabp_options.kernel) */
-#define GABP_KERNEL_AUTO 0   /* GABP_KERNEL_TMA where supported, else GABP_KERNEL_FUSED */
+#define GABP_KERNEL_AUTO 0   /* GABP_KERNEL_SWEEP for FP32 messages, GABP_KERNEL_FUSED for FP64 */
 #define GABP_KERNEL_FUSED 1  /* one fused kernel per iteration (beliefs + all factors) */
 #define GABP_KERNEL_SPLIT 2  /* three kernels per iteration: beliefs, prior factors, obs factors */
 #define GABP_KERNEL_TMA 3    /* the fused kernel as persistent blocks fed by TMA tensor loads;
                                 FP32 and nx a multiple of 4 only */
+#define GABP_KERNEL_SWEEP 4  /* one fused kernel per iteration as warp-synchronous column sweeps
+                                (30-column strips, beliefs in registers); FP32 only */
 
 typedef struct gabp_ctx gabp_ctx;   /* opaque; owns every device buffer it allocates */
 
@@ -92,7 +94,8 @@ typedef struct {
     int tile_x;       /* fused-kernel tile width in cells; 0 = the default / autotuned shape */
     int tile_y;       /* fused-kernel tile height in cells; 0 = the default / autotuned shape.
                          GABP_KERNEL_FUSED: 32x8, 32x16, 32x32, 64x8, 64x16, 128x8;
-                         GABP_KERNEL_TMA: 32x16, 32x32, 64x8, 64x16 */
+                         GABP_KERNEL_TMA: 32x16, 32x32, 64x8, 64x16;
+                         GABP_KERNEL_SWEEP: 30x16, 30x32, 30x64, 30x128 */
     double tol;       /* relative-residual target of gabp_iterate(n < 0); default 1e-5 */
     int check_every;  /* iterations between residual checks when n < 0; default 50 */
     int max_iters;    /* iteration cap when n < 0; default 200000 */
@@ -111,7 +114,7 @@ typedef struct {
     int64_t m;              /* observations */
     int64_t edges;          /* factor-variable edges: sum of prior factor sizes + 4 m */
     int precision;          /* GABP_FP32 / GABP_FP64 */
-    int kernel;             /* the iteration kernel in use (GABP_KERNEL_FUSED / _SPLIT / _TMA) */
+    int kernel;             /* the iteration kernel in use (GABP_KERNEL_FUSED/_SPLIT/_TMA/_SWEEP) */
     int tile_x, tile_y;     /* tile shape in use by the fused kernel */
     double bytes_per_iter;  /* algorithmic HBM bytes of one iteration (messages read and
                                written once, plus the static observation data) */

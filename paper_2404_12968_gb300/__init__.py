@@ -17,6 +17,7 @@ from . import _lib
 from ._lib import (GABP_ERR_ARG, GABP_ERR_CUDA, GABP_ERR_DIVERGED, GABP_ERR_OOM,  # noqa: F401
                    GABP_ERR_STATE, GABP_ERR_TIMEOUT, GABP_FP32, GABP_FP64, GABP_INIT_COLD,
                    GABP_INIT_PAPER, GABP_KERNEL_AUTO, GABP_KERNEL_FUSED, GABP_KERNEL_SPLIT, GABP_KERNEL_TMA,
+                   GABP_KERNEL_SWEEP,
                    GABP_OK, GabpError)
 
 __all__ = [

@@ -26,6 +26,7 @@ GABP_KERNEL_AUTO = 0
 GABP_KERNEL_FUSED = 1
 GABP_KERNEL_SPLIT = 2
 GABP_KERNEL_TMA = 3
+GABP_KERNEL_SWEEP = 4
 
 _ERRNAMES = {1: "GABP_ERR_ARG", 2: "GABP_ERR_OOM", 3: "GABP_ERR_CUDA", 4: "GABP_ERR_DIVERGED",
              5: "GABP_ERR_TIMEOUT", 6: "GABP_ERR_STATE"}

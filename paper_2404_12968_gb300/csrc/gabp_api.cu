@@ -102,6 +102,7 @@ void drop_graph(gabp_ctx *c) {
 cudaError_t launch_iteration(gabp_ctx *c, int src, double beta, cudaStream_t st) {
     if (c->kernel == GABP_KERNEL_SPLIT) return gabp::launch_split_iteration(c->p, src, beta, st);
     if (c->kernel == GABP_KERNEL_TMA) return gabp::launch_tma_iteration(c->p, c->maps, src, beta, st);
+    if (c->kernel == GABP_KERNEL_SWEEP) return gabp::launch_sweep_iteration(c->p, src, beta, c->shape.ty, st);
     return gabp::launch_fused_iteration(c->p, src, beta, c->shape, st);
 }
 
@@ -219,13 +220,20 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     const gabp_options &o = c->opt;
     if (o.precision != GABP_FP32 && o.precision != GABP_FP64) return fail(c, GABP_ERR_ARG, "bad precision");
     if (o.init != GABP_INIT_COLD && o.init != GABP_INIT_PAPER) return fail(c, GABP_ERR_ARG, "bad init mode");
-    if (o.kernel < GABP_KERNEL_AUTO || o.kernel > GABP_KERNEL_TMA) return fail(c, GABP_ERR_ARG, "bad kernel");
+    if (o.kernel < GABP_KERNEL_AUTO || o.kernel > GABP_KERNEL_SWEEP) return fail(c, GABP_ERR_ARG, "bad kernel");
     if (!(o.tol > 0.0) || o.check_every < 1 || o.max_iters < 1) return fail(c, GABP_ERR_ARG, "bad tol/check_every/max_iters");
-    if ((o.tile_x || o.tile_y) && o.kernel != GABP_KERNEL_TMA && !gabp::fused_shape_supported(o.tile_x, o.tile_y))
-        return fail(c, GABP_ERR_ARG, "unsupported tile shape");
-    if ((o.tile_x || o.tile_y) && o.kernel == GABP_KERNEL_TMA && !gabp::tma_shape_supported(o.tile_x, o.tile_y))
-        return fail(c, GABP_ERR_ARG, "unsupported tile shape for the TMA kernel");
-
+    {
+        // the kernel AUTO resolves to: the sweep for FP32, the plain fused kernel for FP64
+        const int k = o.kernel != GABP_KERNEL_AUTO ? o.kernel
+                                                   : (o.precision == GABP_FP32 ? GABP_KERNEL_SWEEP : GABP_KERNEL_FUSED);
+        const bool tiled = o.tile_x || o.tile_y;
+        if (tiled && (k == GABP_KERNEL_FUSED || k == GABP_KERNEL_SPLIT) && !gabp::fused_shape_supported(o.tile_x, o.tile_y))
+            return fail(c, GABP_ERR_ARG, "unsupported tile shape");
+        if (tiled && k == GABP_KERNEL_SWEEP && !(o.tile_x == 30 && gabp::sweep_shape_supported(o.tile_y)))
+            return fail(c, GABP_ERR_ARG, "unsupported tile shape for the sweep kernel (30 x 16/32/64/128)");
+        if (tiled && k == GABP_KERNEL_TMA && !gabp::tma_shape_supported(o.tile_x, o.tile_y))
+            return fail(c, GABP_ERR_ARG, "unsupported tile shape for the TMA kernel");
+    }
     const int64_t n = (int64_t)nx * ny;
     // validate observations and sort them by base cell (stable counting sort, FP64 floor)
     std::vector<int> base((size_t)m);
@@ -327,10 +335,15 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     const bool tma_ok = gabp::tma_problem_supported(p);
     if (o.kernel == GABP_KERNEL_TMA && !tma_ok)
         return fail(c, GABP_ERR_ARG, "the TMA kernel needs FP32 messages and nx a multiple of 4");
+    if (o.kernel == GABP_KERNEL_SWEEP && p.prec != 0)
+        return fail(c, GABP_ERR_ARG, "the sweep kernel needs FP32 messages");
     if (o.kernel == GABP_KERNEL_SPLIT) c->kernel = GABP_KERNEL_SPLIT;
-    else if (o.kernel == GABP_KERNEL_TMA || (o.kernel == GABP_KERNEL_AUTO && tma_ok)) c->kernel = GABP_KERNEL_TMA;
+    else if (o.kernel == GABP_KERNEL_TMA) c->kernel = GABP_KERNEL_TMA;
+    else if (o.kernel == GABP_KERNEL_SWEEP || (o.kernel == GABP_KERNEL_AUTO && p.prec == 0)) c->kernel = GABP_KERNEL_SWEEP;
     else c->kernel = GABP_KERNEL_FUSED;
-    if (c->kernel == GABP_KERNEL_TMA) {
+    if (c->kernel == GABP_KERNEL_SWEEP) {
+        c->shape = o.tile_y ? gabp::FusedShape{30, o.tile_y} : gabp::FusedShape{30, 64};
+    } else if (c->kernel == GABP_KERNEL_TMA) {
         c->shape = o.tile_x ? gabp::FusedShape{o.tile_x, o.tile_y} : gabp::FusedShape{64, 16};
         CK(gabp::make_tma_maps(p, c->shape.tx, c->shape.ty, c->maps), "tensor map encode");
     } else if (o.tile_x) {

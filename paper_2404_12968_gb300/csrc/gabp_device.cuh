@@ -31,16 +31,15 @@ template <> __device__ __forceinline__ double pos_inf<double>() {
     return __longlong_as_double(0x7ff0000000000000LL);
 }
 
-// Reciprocal.  FP32: the hardware approximation (rcp.approx, <= 1 ulp) refined by one
-// Newton-Raphson step r <- r + r (1 - x r), which roughly squares the relative error.  The
-// callers never pass 0, a denormal or an infinity (cavities are guarded at the smallest
-// normal number and an infinite V is tested before the call).  FP64: IEEE division.
+// Reciprocal.  FP32: the hardware approximation rcp.approx.ftz.f32, within 1 ulp over the
+// range the callers use (they never pass 0, a denormal or an infinity: cavities are guarded at
+// the smallest normal number and an infinite V is tested before the call; a result below the
+// smallest normal number flushes to 0).  FP64: IEEE division.
 template <typename T> __device__ __forceinline__ T recip(T x);
 template <> __device__ __forceinline__ float recip<float>(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    const float e = fmaf(-x, r, 1.0f);
-    return fmaf(r, e, r);
+    return r;
 }
 template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
 
@@ -51,6 +50,8 @@ template <> __device__ __forceinline__ double recip<double>(double x) { return 1
 template <typename T> struct CompSum {
     T hi, lo;
     __device__ __forceinline__ CompSum() : hi(T(0)), lo(T(0)) {}
+    // start from a first term: identical to adding it to an empty sum (TwoSum(0, x) = (x, 0))
+    __device__ __forceinline__ explicit CompSum(T first) : hi(first), lo(T(0)) {}
     __device__ __forceinline__ void add(T x) {
         T t = hi + x;
         T z = t - hi;

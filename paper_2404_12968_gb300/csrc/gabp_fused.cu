@@ -90,9 +90,8 @@ __global__ void __launch_bounds__(FT) k_fused(DevProblem p, int src, T beta) {
         if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;
         const int rx = lx + 1, ry = ly + 1;
         const int64_t v = (int64_t)gy * nx + gx;
-        CompSum<T> se, sl;
         T2<T> m = sm[(DIR_C * RY + ry) * RX + rx];
-        se.add(m.x); sl.add(m.y);
+        CompSum<T> se(m.x), sl(m.y);
         if (gx > 0) { m = sm[(DIR_E * RY + ry) * RX + rx - 1]; se.add(m.x); sl.add(m.y); }
         if (gx < nx - 1) { m = sm[(DIR_W * RY + ry) * RX + rx + 1]; se.add(m.x); sl.add(m.y); }
         if (gy > 0) { m = sm[(DIR_N * RY + ry - 1) * RX + rx]; se.add(m.x); sl.add(m.y); }

@@ -180,9 +180,8 @@ __global__ void __launch_bounds__(NT) k_fused_tma(const __grid_constant__ CUtens
             const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
             if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;
             const int rx = lx + 1, ry = ly + 1;
-            CompSum<float> se, sl;
             float2 m = sm[(DIR_C * RY + ry) * RX + rx];
-            se.add(m.x); sl.add(m.y);
+            CompSum<float> se(m.x), sl(m.y);
             if (gx > 0) { m = sm[(DIR_E * RY + ry) * RX + rx - 1]; se.add(m.x); sl.add(m.y); }
             if (gx < nx - 1) { m = sm[(DIR_W * RY + ry) * RX + rx + 1]; se.add(m.x); sl.add(m.y); }
             if (gy > 0) { m = sm[(DIR_N * RY + ry - 1) * RX + rx]; se.add(m.x); sl.add(m.y); }

@@ -57,6 +57,10 @@ cudaError_t launch_fused_iteration(const DevProblem &p, int src, double beta, Fu
                                    cudaStream_t st);
 size_t fused_smem_bytes(int prec, FusedShape shape);
 
+// ---- warp-synchronous column sweep, FP32 (gabp_sweep.cu); tile 30 columns x h rows ----
+bool sweep_shape_supported(int h);
+cudaError_t launch_sweep_iteration(const DevProblem &p, int src, double beta, int h, cudaStream_t st);
+
 // ---- TMA-fed persistent fused path, FP32 (gabp_fused_tma.cu) ----
 struct TmaMaps {
     CUtensorMap planes[2];   // message planes of buffer 0 / 1

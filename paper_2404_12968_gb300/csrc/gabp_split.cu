@@ -28,10 +28,8 @@ template <typename T> __global__ void k_beliefs(DevProblem p, int src) {
     const T2<T> *P = (const T2<T> *)p.P[src];
     const T *O = (const T *)p.O[src];
     const int64_t n = p.n;
-    CompSum<T> se, sl;
     T2<T> q = P[DIR_C * n + v];
-    se.add(q.x);
-    sl.add(q.y);
+    CompSum<T> se(q.x), sl(q.y);
     if (j > 0) { q = P[DIR_E * n + v - 1]; se.add(q.x); sl.add(q.y); }
     if (j < nx - 1) { q = P[DIR_W * n + v + 1]; se.add(q.x); sl.add(q.y); }
     if (i > 0) { q = P[DIR_N * n + v - nx]; se.add(q.x); sl.add(q.y); }

@@ -113,6 +113,8 @@ def test_split_and_fused_bit_identical(prec, shape):
     variants = [(2, (0, 0)), (1, (32, 8)), (1, (64, 16)), (1, (128, 8)), (1, (32, 32))]
     if prec == "fp32" and nx % 4 == 0:
         variants += [(3, (64, 16)), (3, (32, 16)), (3, (64, 8)), (3, (32, 32))]
+    if prec == "fp32":
+        variants += [(4, (30, 16)), (4, (30, 32)), (4, (30, 64)), (4, (30, 128))]
     bufs = []
     for kernel, tile in variants:
         with solver(p, prec, kernel=kernel, tile_x=tile[0], tile_y=tile[1]) as s:
@@ -285,8 +287,8 @@ def test_argument_errors():
 
 
 def test_auto_kernel_selection():
-    from paper_2404_12968_gb300 import GABP_KERNEL_FUSED, GABP_KERNEL_TMA
-    for (nx, prec, expect) in [(64, "fp32", GABP_KERNEL_TMA), (66, "fp32", GABP_KERNEL_FUSED),
+    from paper_2404_12968_gb300 import GABP_KERNEL_FUSED, GABP_KERNEL_SWEEP
+    for (nx, prec, expect) in [(64, "fp32", GABP_KERNEL_SWEEP), (66, "fp32", GABP_KERNEL_SWEEP),
                                (64, "fp64", GABP_KERNEL_FUSED)]:
         p = gabp_synth.make_problem(nx, 40, 0.3, 0, n_uniform=50)
         with solver(p, prec) as s:
