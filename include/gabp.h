@@ -214,6 +214,44 @@ const char *gabp_create_error(void);
 /* Release the context and all its device memory.  NULL is ignored. */
 void gabp_destroy(gabp_ctx *ctx);
 
+/*
+ * Allocation-free residual.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory through this library, e.g. a process whose device memory
+ * is held by another allocator (a framework's caching allocator keeps freed blocks, so a plain
+ * cudaMalloc can fail while that allocator still has room), or a loop with a fixed memory
+ * budget.  It computes the same FP64 relative residual ||b - A mu|| / ||b|| as
+ * gabp_residual(), for a mean the caller supplies, using only memory the caller passes in plus
+ * a static scratch array inside the library.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ *   grid, kappa, gamma  as for gabp_create (gamma > 0; zero-Neumann boundary).
+ *   m                   number of observations, >= 0.
+ *   obs_xy, y, noise_var  DEVICE arrays (2m, m, m doubles) of the current device, with the
+ *                       observations SORTED by base cell (i0 * nx + j0 non-decreasing, base
+ *                       cell as defined for gabp_create); GABP_ERR_ARG if they are not, or if an
+ *                       observation lies outside the grid or has a variance <= 0.
+ *   mean                DEVICE array of nx*ny doubles (the field mu).
+ *   rel_residual        HOST pointer to one double, written on success.  If ||b|| = 0 the
+ *                       absolute norm ||A mu|| is returned instead.
+ *   stream              cudaStream_t to run on (NULL = the legacy default stream); the call
+ *                       synchronises that stream before returning.
+ *
+ * Scratch: a file-scope device array of GABP_NOALLOC_MAX_DOUBLES doubles (24 MiB) that every
+ * GPU loading the library holds until the process exits; nx*ny + m must not exceed
+ * GABP_NOALLOC_MAX_DOUBLES - 2052 (GABP_ERR_ARG otherwise, before any GPU work).  Every call
+ * shares the array and it keeps the last call's contents (the call clears what must start at
+ * zero), so calls that overlap on the GPU (from two streams or two host threads) race and
+ * must be serialised by the caller.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture.  The text of the last error on the calling thread is returned by
+ * gabp_residual_noalloc_error().
+ */
+#define GABP_NOALLOC_MAX_DOUBLES (3 * 1024 * 1024)
+int gabp_residual_noalloc(gabp_grid grid, double kappa, double gamma, int64_t m, const double *obs_xy,
+                          const double *y, const double *noise_var, const double *mean,
+                          double *rel_residual, void *stream);
+const char *gabp_residual_noalloc_error(void);
+
 #ifdef __cplusplus
 }
 #endif

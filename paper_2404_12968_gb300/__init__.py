@@ -23,7 +23,8 @@ from ._lib import (GABP_ERR_ARG, GABP_ERR_CUDA, GABP_ERR_DIVERGED, GABP_ERR_OOM,
 __all__ = [
     "gabp_default_options", "gabp_create", "gabp_iterate", "gabp_marginals", "gabp_residual",
     "gabp_warm_start", "gabp_reset", "gabp_message_bytes", "gabp_get_messages",
-    "gabp_set_messages", "gabp_get_stats", "gabp_destroy", "Solver", "GabpError",
+    "gabp_set_messages", "gabp_get_stats", "gabp_destroy", "gabp_residual_noalloc", "Solver",
+    "GabpError",
 ]
 
 
@@ -120,6 +121,24 @@ def gabp_get_stats(ctx: int) -> dict:
 def gabp_destroy(ctx: int) -> None:
     if ctx:
         _lib.load().gabp_destroy(ctx)
+
+
+def gabp_residual_noalloc(nx: int, ny: int, kappa: float, obs_xy, y, noise_var, mean, *,
+                          gamma: float = 1.0, stream=None) -> float:
+    """Relative residual of ``mean`` without any allocation by the library.
+
+    ``obs_xy`` (2m), ``y``, ``noise_var`` (m) and ``mean`` (nx*ny) are contiguous float64 CUDA
+    tensors on the current device; the observations must be sorted by base cell.  ``stream`` is
+    a ``cudaStream_t`` value (e.g. ``torch.cuda.current_stream().cuda_stream``) or None."""
+    L = _lib.load()
+    m = int(y.numel()) if hasattr(y, "numel") else len(y)
+    out = ctypes.c_double()
+    rc = L.gabp_residual_noalloc(_lib.gabp_grid(nx, ny, 1.0), float(kappa), float(gamma), m,
+                                 _ptr(obs_xy) if m else None, _ptr(y) if m else None,
+                                 _ptr(noise_var) if m else None, _ptr(mean), ctypes.byref(out), stream)
+    if rc != GABP_OK:
+        raise GabpError(rc, (L.gabp_residual_noalloc_error() or b"").decode(errors="replace"))
+    return out.value
 
 
 class Solver:

@@ -103,5 +103,10 @@ def load():
     L.gabp_create_error.restype = ctypes.c_char_p
     L.gabp_destroy.argtypes = [_vp]
     L.gabp_destroy.restype = None
+    L.gabp_residual_noalloc.argtypes = [gabp_grid, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                        _vp, _vp, _vp, _vp, _dp, _vp]
+    L.gabp_residual_noalloc.restype = ctypes.c_int
+    L.gabp_residual_noalloc_error.argtypes = []
+    L.gabp_residual_noalloc_error.restype = ctypes.c_char_p
     _LIB = L
     return L
