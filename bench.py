@@ -40,6 +40,7 @@ DAMPING = 0.3
 METRIC = "GaBP node-updates/s and HBM GB/s at 4096²; time-to-1e-5 residual, warm vs cold"
 UNIT = "node-updates/s"
 WORKLOAD = "gabp_4096x4096_kappa0.02_96tracks_1.2M+200k_uniform_fp32"
+KERNEL_NAMES = {1: "k_fused", 2: "k_beliefs+k_prior+k_obs", 3: "k_fused_tma", 4: "k_sweep"}
 
 
 def dist_info():
@@ -58,15 +59,27 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if the summary
-    was taken on the current kernel source (matching source hash)."""
+KERNEL_SOURCES = {"k_fused": "gabp_fused.cu", "k_fused_tma": "gabp_fused_tma.cu", "k_sweep": "gabp_sweep.cu",
+                  "k_beliefs+k_prior+k_obs": "gabp_split.cu"}
+
+
+def kernel_source_hash(kernel: str) -> str:
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_fused_4096_ncu.md")
-    src = os.path.join(ROOT, "paper_2404_12968_gb300", "csrc", "gabp_fused.cu")
-    dev = os.path.join(ROOT, "paper_2404_12968_gb300", "csrc", "gabp_device.cuh")
+    csrc = os.path.join(ROOT, "paper_2404_12968_gb300", "csrc")
+    data = b""
+    for fn in (KERNEL_SOURCES[kernel], "gabp_device.cuh"):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            data += f.read()
+    return hashlib.sha256(data).hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of the iteration kernel from the committed ncu summary
+    (profiles/<kernel>_4096_traffic.md), if that summary was taken on the current kernel source
+    (matching source hash); None otherwise."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_4096_traffic.md")
     try:
-        h = hashlib.sha256(open(src, "rb").read() + open(dev, "rb").read()).hexdigest()[:16]
+        h = kernel_source_hash(kernel)
         txt = open(path).read()
     except OSError:
         return None
@@ -162,7 +175,7 @@ def own_arm(args):
 
     p = make_problem(rank, args.size)
     stream = torch.cuda.current_stream(dev)
-    s = Solver(p, precision="fp32", stream=stream.cuda_stream, device=local)
+    s = Solver(p, precision="fp32", stream=stream.cuda_stream, device=local, kernel=args.kernel)
     st = s.stats()
     n = p.n
     mean_dev = torch.empty(n, dtype=torch.float64, device=dev)
@@ -212,7 +225,7 @@ def own_arm(args):
 
     def e2e_step():
         ctx = gabp_create(p.nx, p.ny, p.kappa, obs_xy, y, nv, precision=0, stream=stream.cuda_stream,
-                          device=local)
+                          device=local, kernel=args.kernel)
         try:
             gabp_iterate(ctx, ITERS_PER_STEP, DAMPING)
             r = gabp_residual(ctx)
@@ -242,7 +255,7 @@ def own_arm(args):
     value = world * node_updates * args.steps / (ms / 1e3)
     peak, peak_kind = measured_peak_gbs()
     achieved = st["bytes_per_iter"] / (iter_ms / 1e3) / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic(KERNEL_NAMES[st["kernel"]])
     h2d = 32 * p.m + 4 * p.m + 4 * (n + 1)   # obs (x, y, value, variance) + base cells + cell pointers
     d2h = 8 * n + 16                          # marginal means + residual scalars
     launches_per_step = ITERS_PER_STEP + 6 + 2
@@ -251,7 +264,7 @@ def own_arm(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.size == 4096 else f"profiling_{args.size}", "nx": p.nx, "ny": p.ny, "kappa": p.kappa, "m": p.m,
-                   "iters_per_step": ITERS_PER_STEP, "damping": DAMPING, "kernel": "fused",
+                   "iters_per_step": ITERS_PER_STEP, "damping": DAMPING, "kernel": KERNEL_NAMES[st["kernel"]],
                    "tile": [st["tile_x"], st["tile_y"]], "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (message planes 1.3 GB ping-pong)"},
         "hbm_gbs": achieved, "rel_residual_last_step": residuals[-1],
@@ -261,7 +274,7 @@ def own_arm(args):
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "k_fused", "algorithmic_bytes_per_launch": st["bytes_per_iter"],
+                     "kernel": KERNEL_NAMES[st["kernel"]], "algorithmic_bytes_per_launch": st["bytes_per_iter"],
                      "launch_ms": iter_ms},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -329,6 +342,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--size", type=int, default=4096, help="grid side; 4096 is the benchmark workload")
+    ap.add_argument("--kernel", type=int, default=0, help="iteration kernel (gabp.h GABP_KERNEL_*); 0 = auto")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

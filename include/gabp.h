@@ -94,7 +94,7 @@ typedef struct {
     int tile_x;       /* fused-kernel tile width in cells; 0 = the default / autotuned shape */
     int tile_y;       /* fused-kernel tile height in cells; 0 = the default / autotuned shape.
                          GABP_KERNEL_FUSED: 32x8, 32x16, 32x32, 64x8, 64x16, 128x8;
-                         GABP_KERNEL_TMA: 32x16, 32x32, 64x8, 64x16;
+                         GABP_KERNEL_TMA: 30x14, 30x22, 30x30;
                          GABP_KERNEL_SWEEP: 30x16, 30x32, 30x64, 30x128 */
     double tol;       /* relative-residual target of gabp_iterate(n < 0); default 1e-5 */
     int check_every;  /* iterations between residual checks when n < 0; default 50 */
@@ -213,6 +213,60 @@ const char *gabp_create_error(void);
 
 /* Release the context and all its device memory.  NULL is ignored. */
 void gabp_destroy(gabp_ctx *ctx);
+
+/* ---------------------------------------------------------------------------------------
+ * Batches: many independent problems (ensemble members, successive analysis windows) of
+ * uneven sizes iterated together.  Every iteration of the whole batch is ONE persistent
+ * kernel launch (the column-sweep kernel over the strips of all problems; FP32 messages),
+ * replayed from a CUDA graph; the per-problem residual checks are a second graph.  The strip
+ * height is chosen by the autotuner (timed candidates on this batch at create time; the choice
+ * is cached per device and batch shape in the file named by GABP_AUTOTUNE_CACHE, if set).
+ * --------------------------------------------------------------------------------------- */
+typedef struct gabp_batch gabp_batch;   /* opaque; owns the device memory of all its problems */
+
+typedef struct {
+    gabp_grid grid;             /* as for gabp_create */
+    double kappa;               /* > 0 */
+    double gamma;               /* > 0 (prior scale); 0 means 1 */
+    int64_t m;                  /* observations, >= 0 */
+    const double *obs_xy;       /* 2m doubles, HOST */
+    const double *y;            /* m doubles, HOST */
+    const double *noise_var;    /* m doubles, HOST */
+} gabp_problem;
+
+/*
+ * Create a batch of `count` problems (each built as in gabp_create: Sec. 3.1 and Sec. 3.2).
+ * opt: NULL = defaults; precision must be GABP_FP32; opt->tile_y, if non-zero, fixes the
+ * strip height (16, 32, 64 or 128) instead of the autotuner; tol, check_every (rounded up to
+ * even), max_iters, device and stream apply to the whole batch.  Host arrays are read during
+ * the call only.  Errors as for gabp_create; the failing problem's index is in the message.
+ */
+int gabp_batch_create(gabp_batch **out, int count, const gabp_problem *problems, const gabp_options *opt);
+
+/*
+ * Iterate every problem of the batch in lockstep (Alg. 2 with damping, as gabp_iterate).
+ *   n_iters >= 0: exactly n_iters iterations of every problem.
+ *   n_iters <  0: iterate until every problem's relative residual is <= opt.tol; a problem that
+ *                 reaches it stops being updated at the next check (every check_every
+ *                 iterations).  GABP_ERR_TIMEOUT after max_iters, GABP_ERR_DIVERGED if a
+ *                 residual becomes non-finite.
+ */
+int gabp_batch_iterate(gabp_batch *b, int n_iters, double damping);
+
+/* Relative residuals of every problem (count doubles, HOST), computed now in FP64. */
+int gabp_batch_residuals(gabp_batch *b, double *rel);
+
+/* Marginals of problem `index` (as gabp_marginals). */
+int gabp_batch_marginals(gabp_batch *b, int index, double *mean, double *var);
+
+/* Statistics of problem `index` (iterations it has been updated, last residual, sizes). */
+int gabp_batch_get_stats(const gabp_batch *b, int index, gabp_stats *stats);
+
+/* Strip height in use (chosen by the autotuner or opt.tile_y). */
+int gabp_batch_strip_height(const gabp_batch *b);
+
+const char *gabp_batch_last_error(const gabp_batch *b);
+void gabp_batch_destroy(gabp_batch *b);
 
 /*
  * Allocation-free residual.  The paper has no counterpart: this entry point exists for callers

@@ -23,7 +23,9 @@ from ._lib import (GABP_ERR_ARG, GABP_ERR_CUDA, GABP_ERR_DIVERGED, GABP_ERR_OOM,
 __all__ = [
     "gabp_default_options", "gabp_create", "gabp_iterate", "gabp_marginals", "gabp_residual",
     "gabp_warm_start", "gabp_reset", "gabp_message_bytes", "gabp_get_messages",
-    "gabp_set_messages", "gabp_get_stats", "gabp_destroy", "gabp_residual_noalloc", "Solver",
+    "gabp_set_messages", "gabp_get_stats", "gabp_destroy", "gabp_residual_noalloc",
+    "gabp_batch_create", "gabp_batch_iterate", "gabp_batch_residuals", "gabp_batch_marginals",
+    "gabp_batch_get_stats", "gabp_batch_strip_height", "gabp_batch_destroy", "Solver", "Batch",
     "GabpError",
 ]
 
@@ -139,6 +141,112 @@ def gabp_residual_noalloc(nx: int, ny: int, kappa: float, obs_xy, y, noise_var, 
     if rc != GABP_OK:
         raise GabpError(rc, (L.gabp_residual_noalloc_error() or b"").decode(errors="replace"))
     return out.value
+
+
+def _bcheck(rc: int, b):
+    if rc != GABP_OK:
+        raise GabpError(rc, (_lib.load().gabp_batch_last_error(b) or b"").decode(errors="replace"))
+
+
+def gabp_batch_create(problems, **opts) -> int:
+    """Create a batch from ``gabp_synth.Problem``-like objects; returns its handle."""
+    L = _lib.load()
+    keep = []
+    arr = (_lib.gabp_problem * len(problems))()
+    for i, pr in enumerate(problems):
+        xy = np.ascontiguousarray(np.stack([pr.obs_x, pr.obs_y], axis=1).reshape(-1), np.float64)
+        y = np.ascontiguousarray(pr.y, np.float64)
+        nv = np.ascontiguousarray(pr.noise_var, np.float64)
+        keep += [xy, y, nv]
+        m = y.shape[0]
+        arr[i] = _lib.gabp_problem(_lib.gabp_grid(pr.nx, pr.ny, 1.0), float(pr.kappa),
+                                   float(getattr(pr, "gamma", 1.0)), m, xy.ctypes.data if m else None,
+                                   y.ctypes.data if m else None, nv.ctypes.data if m else None)
+    o = gabp_default_options(**opts)
+    h = ctypes.c_void_p()
+    rc = L.gabp_batch_create(ctypes.byref(h), len(problems), arr, ctypes.byref(o))
+    if rc != GABP_OK:
+        raise GabpError(rc, (L.gabp_batch_last_error(None) or b"").decode(errors="replace"))
+    return h.value
+
+
+def gabp_batch_iterate(b: int, n_iters: int, damping: float) -> None:
+    _bcheck(_lib.load().gabp_batch_iterate(b, int(n_iters), float(damping)), b)
+
+
+def gabp_batch_residuals(b: int, count: int) -> np.ndarray:
+    out = np.empty(count)
+    _bcheck(_lib.load().gabp_batch_residuals(b, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), b)
+    return out
+
+
+def gabp_batch_marginals(b: int, index: int, mean, var=None) -> None:
+    _bcheck(_lib.load().gabp_batch_marginals(b, int(index), _ptr(mean), _ptr(var)), b)
+
+
+def gabp_batch_get_stats(b: int, index: int) -> dict:
+    s = _lib.gabp_stats()
+    _bcheck(_lib.load().gabp_batch_get_stats(b, int(index), ctypes.byref(s)), b)
+    return {f: getattr(s, f) for f, _ in s._fields_}
+
+
+def gabp_batch_strip_height(b: int) -> int:
+    return int(_lib.load().gabp_batch_strip_height(b))
+
+
+def gabp_batch_destroy(b: int) -> None:
+    if b:
+        _lib.load().gabp_batch_destroy(b)
+
+
+class Batch:
+    """Owns a batch of independent problems iterated together (one persistent launch per
+    iteration)."""
+
+    def __init__(self, problems, **opts):
+        self.sizes = [(int(p.nx), int(p.ny)) for p in problems]
+        self.handle = gabp_batch_create(problems, **opts)
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def iterate(self, n_iters: int, damping: float) -> "Batch":
+        gabp_batch_iterate(self.handle, n_iters, damping)
+        return self
+
+    def residuals(self) -> np.ndarray:
+        return gabp_batch_residuals(self.handle, len(self))
+
+    def marginals(self, index: int, want_var: bool = False):
+        nx, ny = self.sizes[index]
+        mean = np.empty(nx * ny)
+        var = np.empty(nx * ny) if want_var else None
+        gabp_batch_marginals(self.handle, index, mean, var)
+        return mean, var
+
+    def stats(self, index: int) -> dict:
+        return gabp_batch_get_stats(self.handle, index)
+
+    @property
+    def strip_height(self) -> int:
+        return gabp_batch_strip_height(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gabp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Solver:

@@ -54,6 +54,12 @@ class gabp_stats(ctypes.Structure):
                 ("tile_y", ctypes.c_int), ("bytes_per_iter", ctypes.c_double)]
 
 
+class gabp_problem(ctypes.Structure):
+    _fields_ = [("grid", gabp_grid), ("kappa", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("m", ctypes.c_int64), ("obs_xy", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("noise_var", ctypes.c_void_p)]
+
+
 class GabpError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
@@ -103,6 +109,23 @@ def load():
     L.gabp_create_error.restype = ctypes.c_char_p
     L.gabp_destroy.argtypes = [_vp]
     L.gabp_destroy.restype = None
+    L.gabp_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(gabp_problem),
+                                    ctypes.POINTER(gabp_options)]
+    L.gabp_batch_create.restype = ctypes.c_int
+    L.gabp_batch_iterate.argtypes = [_vp, ctypes.c_int, ctypes.c_double]
+    L.gabp_batch_iterate.restype = ctypes.c_int
+    L.gabp_batch_residuals.argtypes = [_vp, _dp]
+    L.gabp_batch_residuals.restype = ctypes.c_int
+    L.gabp_batch_marginals.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+    L.gabp_batch_marginals.restype = ctypes.c_int
+    L.gabp_batch_get_stats.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(gabp_stats)]
+    L.gabp_batch_get_stats.restype = ctypes.c_int
+    L.gabp_batch_strip_height.argtypes = [_vp]
+    L.gabp_batch_strip_height.restype = ctypes.c_int
+    L.gabp_batch_last_error.argtypes = [_vp]
+    L.gabp_batch_last_error.restype = ctypes.c_char_p
+    L.gabp_batch_destroy.argtypes = [_vp]
+    L.gabp_batch_destroy.restype = None
     L.gabp_residual_noalloc.argtypes = [gabp_grid, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                         _vp, _vp, _vp, _vp, _dp, _vp]
     L.gabp_residual_noalloc.restype = ctypes.c_int

@@ -5,11 +5,12 @@
 // of fused (or split) iteration kernels on the context's stream.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
-#include "../../include/gabp.h"
+#include "gabp.h"
 #include "gabp_internal.h"
 
 using gabp::DevProblem;
@@ -344,7 +345,7 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     if (c->kernel == GABP_KERNEL_SWEEP) {
         c->shape = o.tile_y ? gabp::FusedShape{30, o.tile_y} : gabp::FusedShape{30, 64};
     } else if (c->kernel == GABP_KERNEL_TMA) {
-        c->shape = o.tile_x ? gabp::FusedShape{o.tile_x, o.tile_y} : gabp::FusedShape{64, 16};
+        c->shape = o.tile_x ? gabp::FusedShape{o.tile_x, o.tile_y} : gabp::FusedShape{30, 22};
         CK(gabp::make_tma_maps(p, c->shape.tx, c->shape.ty, c->maps), "tensor map encode");
     } else if (o.tile_x) {
         c->shape = {o.tile_x, o.tile_y};
@@ -579,6 +580,461 @@ void gabp_destroy(gabp_ctx *c) {
         free_all(c);
     }
     delete c;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------------------
+
+struct gabp_batch {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap = nullptr;
+    gabp_options opt{};
+    std::vector<gabp_ctx *> inst;
+    gabp::DevProblem *d_table = nullptr;
+    int *d_prefix = nullptr;     // count + 1 strip offsets
+    int *d_active = nullptr;     // count flags
+    int *h_active = nullptr;     // pinned mirror
+    double *h_scal = nullptr;    // pinned, 2 per problem
+    int H = 64;
+    int total_strips = 0;
+    int cur = 0;
+    std::vector<int64_t> iters;
+    std::vector<double> res;
+    std::string err;
+    cudaGraphExec_t g_iter = nullptr;
+    int g_len = 0;
+    double g_beta = -1.0;
+    int g_H = 0;
+    cudaGraphExec_t g_res = nullptr;
+};
+
+namespace {
+
+thread_local std::string t_batch_create_err;
+
+int bfail(gabp_batch *b, int code, const std::string &msg) {
+    if (b) b->err = msg;
+    return code;
+}
+
+int bcuda(gabp_batch *b, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    cudaGetLastError();
+    return bfail(b, e == cudaErrorMemoryAllocation ? GABP_ERR_OOM : GABP_ERR_CUDA, m);
+}
+
+#define BK(call, what)                                    \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return bcuda(b, e_, what); \
+    } while (0)
+
+void batch_drop_graphs(gabp_batch *b) {
+    if (b->g_iter) cudaGraphExecDestroy(b->g_iter);
+    if (b->g_res) cudaGraphExecDestroy(b->g_res);
+    b->g_iter = nullptr;
+    b->g_res = nullptr;
+    b->g_len = 0;
+    b->g_beta = -1.0;
+    b->g_H = 0;
+}
+
+int batch_set_height(gabp_batch *b, int H) {
+    const int count = (int)b->inst.size();
+    std::vector<int> pre(count + 1, 0);
+    for (int i = 0; i < count; ++i)
+        pre[i + 1] = pre[i] + gabp::sweep_strips(b->inst[i]->p.nx, b->inst[i]->p.ny, H);
+    BK(cudaMemcpyAsync(b->d_prefix, pre.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, b->stream),
+       "upload strip offsets");
+    BK(cudaStreamSynchronize(b->stream), "sync");
+    b->H = H;
+    b->total_strips = pre[count];
+    return GABP_OK;
+}
+
+cudaError_t batch_launch(gabp_batch *b, int src, double beta, cudaStream_t st) {
+    return gabp::launch_sweep_batch(b->d_table, b->d_prefix, b->d_active, (int)b->inst.size(), b->total_strips,
+                                    src, beta, b->H, st);
+}
+
+int batch_upload_active(gabp_batch *b) {
+    BK(cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int) * b->inst.size(), cudaMemcpyHostToDevice, b->stream),
+       "upload active flags");
+    return GABP_OK;
+}
+
+int batch_ensure_graph(gabp_batch *b, int len, double beta) {
+    if (b->g_iter && b->g_len == len && b->g_beta == beta && b->g_H == b->H) return GABP_OK;
+    if (b->g_iter) cudaGraphExecDestroy(b->g_iter);
+    b->g_iter = nullptr;
+    cudaGraph_t g = nullptr;
+    BK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t le = cudaSuccess;
+    for (int t = 0; t < len && le == cudaSuccess; ++t) le = batch_launch(b, t & 1, beta, b->cap);
+    cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bcuda(b, le, "batch launch during capture");
+    }
+    if (ee != cudaSuccess) return bcuda(b, ee, "end capture");
+    cudaError_t ie = cudaGraphInstantiate(&b->g_iter, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        b->g_iter = nullptr;
+        return bcuda(b, ie, "graph instantiate");
+    }
+    b->g_len = len;
+    b->g_beta = beta;
+    b->g_H = b->H;
+    return GABP_OK;
+}
+
+int batch_run(gabp_batch *b, int64_t count, double beta) {
+    const int G = 20;
+    if (count > 0 && b->cur == 1) {
+        BK(batch_launch(b, 1, beta, b->stream), "batch launch");
+        b->cur = 0;
+        --count;
+        for (size_t i = 0; i < b->inst.size(); ++i)
+            if (b->h_active[i]) ++b->iters[i];
+    }
+    int64_t done = 0;
+    if (count >= G) {
+        int rc = batch_ensure_graph(b, G, beta);
+        if (rc) return rc;
+        while (count - done >= G) {
+            BK(cudaGraphLaunch(b->g_iter, b->stream), "graph launch");
+            done += G;
+        }
+    }
+    while (done < count) {
+        BK(batch_launch(b, b->cur, beta, b->stream), "batch launch");
+        b->cur ^= 1;
+        ++done;
+    }
+    for (size_t i = 0; i < b->inst.size(); ++i)
+        if (b->h_active[i]) b->iters[i] += count;
+    for (gabp_ctx *c : b->inst) c->cur = b->cur;
+    return GABP_OK;
+}
+
+// residuals of every problem at the current parity (graph captured per parity 0 only)
+int batch_residuals(gabp_batch *b) {
+    const int count = (int)b->inst.size();
+    if (b->cur != 0 || !b->g_res) {
+        if (b->g_res) cudaGraphExecDestroy(b->g_res);
+        b->g_res = nullptr;
+        cudaGraph_t g = nullptr;
+        BK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t le = cudaSuccess;
+        for (int i = 0; i < count && le == cudaSuccess; ++i) {
+            le = gabp::launch_residual(b->inst[i]->p, b->cur, b->cap);
+            if (le == cudaSuccess)
+                le = cudaMemcpyAsync(b->h_scal + 2 * i, b->inst[i]->p.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                     b->cap);
+        }
+        cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return bcuda(b, le, "residual capture");
+        }
+        if (ee != cudaSuccess) return bcuda(b, ee, "end capture");
+        cudaError_t ie = cudaGraphInstantiate(&b->g_res, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            b->g_res = nullptr;
+            return bcuda(b, ie, "graph instantiate");
+        }
+    }
+    BK(cudaGraphLaunch(b->g_res, b->stream), "residual graph launch");
+    BK(cudaStreamSynchronize(b->stream), "residual sync");
+    if (b->cur != 0) {   // only the parity-0 graph is kept
+        cudaGraphExecDestroy(b->g_res);
+        b->g_res = nullptr;
+    }
+    for (int i = 0; i < count; ++i) {
+        const double r2 = b->h_scal[2 * i], b2 = b->h_scal[2 * i + 1];
+        b->res[i] = b2 > 0.0 ? std::sqrt(r2) / std::sqrt(b2) : std::sqrt(r2);
+        b->inst[i]->last_res = b->res[i];
+    }
+    return GABP_OK;
+}
+
+std::string autotune_key(const gabp_batch *b) {
+    cudaDeviceProp prop;
+    std::string name = cudaGetDeviceProperties(&prop, b->dev) == cudaSuccess ? prop.name : "unknown";
+    for (char &ch : name)
+        if (ch == ' ') ch = '_';
+    int64_t nodes = 0, obs = 0;
+    for (const gabp_ctx *c : b->inst) {
+        nodes += c->p.n;
+        obs += c->p.m;
+    }
+    return "batch " + name + " " + std::to_string(b->inst.size()) + " " + std::to_string(nodes) + " " +
+           std::to_string(obs);
+}
+
+int autotune_cache_lookup(const std::string &key) {
+    const char *path = std::getenv("GABP_AUTOTUNE_CACHE");
+    if (!path) return 0;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return 0;
+    char line[512];
+    int found = 0;
+    while (std::fgets(line, sizeof line, f)) {
+        std::string s(line);
+        const size_t sp = s.rfind(' ');
+        if (sp != std::string::npos && s.compare(0, sp, key) == 0) found = std::atoi(s.c_str() + sp + 1);
+    }
+    std::fclose(f);
+    return gabp::sweep_shape_supported(found) ? found : 0;
+}
+
+void autotune_cache_store(const std::string &key, int value) {
+    const char *path = std::getenv("GABP_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d\n", key.c_str(), value);
+    std::fclose(f);
+}
+
+// Time each candidate strip height on this batch and keep the fastest; messages are
+// re-initialised afterwards.
+int batch_autotune(gabp_batch *b) {
+    const std::string key = autotune_key(b);
+    int best = autotune_cache_lookup(key);
+    if (!best) {
+        const int cands[4] = {16, 32, 64, 128};
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        BK(cudaEventCreate(&e0), "event");
+        BK(cudaEventCreate(&e1), "event");
+        for (int h : cands) {
+            int rc = batch_set_height(b, h);
+            if (rc) return rc;
+            for (int t = 0; t < 2; ++t) BK(batch_launch(b, t & 1, 0.5, b->stream), "autotune launch");
+            BK(cudaEventRecord(e0, b->stream), "event");
+            for (int t = 0; t < 8; ++t) BK(batch_launch(b, t & 1, 0.5, b->stream), "autotune launch");
+            BK(cudaEventRecord(e1, b->stream), "event");
+            BK(cudaEventSynchronize(e1), "event sync");
+            float ms = 0.f;
+            BK(cudaEventElapsedTime(&ms, e0, e1), "event time");
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = h;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        autotune_cache_store(key, best);
+    }
+    int rc = batch_set_height(b, best);
+    if (rc) return rc;
+    for (gabp_ctx *c : b->inst) {
+        rc = init_messages(c);
+        if (rc) return bfail(b, rc, c->err);
+    }
+    BK(cudaStreamSynchronize(b->stream), "sync");
+    b->cur = 0;
+    return GABP_OK;
+}
+
+void batch_free(gabp_batch *b) {
+    batch_drop_graphs(b);
+    for (gabp_ctx *c : b->inst) gabp_destroy(c);
+    b->inst.clear();
+    if (b->d_table) cudaFree(b->d_table);
+    if (b->d_prefix) cudaFree(b->d_prefix);
+    if (b->d_active) cudaFree(b->d_active);
+    if (b->h_active) cudaFreeHost(b->h_active);
+    if (b->h_scal) cudaFreeHost(b->h_scal);
+    b->d_table = nullptr;
+    b->d_prefix = b->d_active = nullptr;
+    b->h_active = nullptr;
+    b->h_scal = nullptr;
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    b->cap = b->stream = nullptr;
+}
+
+int batch_create_impl(gabp_batch *b, int count, const gabp_problem *problems) {
+    if (count < 1 || !problems) return bfail(b, GABP_ERR_ARG, "count must be >= 1 and problems non-NULL");
+    if (b->opt.precision != GABP_FP32) return bfail(b, GABP_ERR_ARG, "batches use FP32 messages");
+    if (b->opt.tile_y && !gabp::sweep_shape_supported(b->opt.tile_y))
+        return bfail(b, GABP_ERR_ARG, "strip height must be 16, 32, 64 or 128");
+    gabp_options io = b->opt;
+    io.stream = b->stream;
+    io.kernel = GABP_KERNEL_SWEEP;
+    io.tile_x = io.tile_y = 0;
+    io.device = b->dev;
+    for (int i = 0; i < count; ++i) {
+        const gabp_problem &pr = problems[i];
+        gabp_prior prior{pr.gamma > 0.0 ? pr.gamma : 1.0, 0};
+        gabp_ctx *c = nullptr;
+        const int rc = gabp_create(&c, pr.grid, pr.kappa, &prior, pr.m, pr.obs_xy, pr.y, pr.noise_var, &io);
+        if (rc) return bfail(b, rc, "problem " + std::to_string(i) + ": " + gabp_create_error());
+        b->inst.push_back(c);
+    }
+    BK(cudaMalloc((void **)&b->d_table, sizeof(gabp::DevProblem) * count), "alloc table");
+    BK(cudaMalloc((void **)&b->d_prefix, sizeof(int) * (count + 1)), "alloc strip offsets");
+    BK(cudaMalloc((void **)&b->d_active, sizeof(int) * count), "alloc active flags");
+    BK(cudaMallocHost((void **)&b->h_active, sizeof(int) * count), "alloc pinned flags");
+    BK(cudaMallocHost((void **)&b->h_scal, 2 * sizeof(double) * count), "alloc pinned scalars");
+    std::vector<gabp::DevProblem> table(count);
+    for (int i = 0; i < count; ++i) {
+        table[i] = b->inst[i]->p;
+        b->h_active[i] = 1;
+    }
+    BK(cudaMemcpyAsync(b->d_table, table.data(), sizeof(gabp::DevProblem) * count, cudaMemcpyHostToDevice, b->stream),
+       "upload table");
+    int rc = batch_upload_active(b);
+    if (rc) return rc;
+    b->iters.assign(count, 0);
+    b->res.assign(count, NAN);
+    if (b->opt.check_every & 1) b->opt.check_every += 1;
+    if (b->opt.tile_y) {
+        rc = batch_set_height(b, b->opt.tile_y);
+    } else {
+        rc = batch_autotune(b);
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gabp_batch_create(gabp_batch **out, int count, const gabp_problem *problems, const gabp_options *opt) {
+    t_batch_create_err.clear();
+    if (!out) {
+        t_batch_create_err = "out must not be NULL";
+        return GABP_ERR_ARG;
+    }
+    *out = nullptr;
+    gabp_batch *b = new (std::nothrow) gabp_batch();
+    if (!b) return GABP_ERR_OOM;
+    if (opt) b->opt = *opt;
+    else gabp_default_options(&b->opt);
+    int dev = b->opt.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        t_batch_create_err = "no CUDA device";
+        return GABP_ERR_CUDA;
+    }
+    b->dev = dev;
+    int rc = GABP_OK;
+    {
+        DeviceGuard g(dev);
+        cudaError_t e = cudaSuccess;
+        if (b->opt.stream) {
+            b->stream = (cudaStream_t)b->opt.stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+            b->own_stream = e == cudaSuccess;
+        }
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        rc = (!g.ok || e != cudaSuccess) ? bcuda(b, e, "stream create") : batch_create_impl(b, count, problems);
+        if (rc) {
+            t_batch_create_err = b->err;
+            batch_free(b);
+        }
+    }
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return GABP_OK;
+}
+
+int gabp_batch_iterate(gabp_batch *b, int n_iters, double damping) {
+    if (!b) return GABP_ERR_ARG;
+    if (!(damping >= 0.0 && damping < 1.0)) return bfail(b, GABP_ERR_ARG, "damping must be in [0, 1)");
+    DeviceGuard g(b->dev);
+    b->err.clear();
+    const int count = (int)b->inst.size();
+    if (n_iters >= 0) {
+        for (int i = 0; i < count; ++i) b->h_active[i] = 1;
+        int rc = batch_upload_active(b);
+        if (rc) return rc;
+        rc = batch_run(b, n_iters, damping);
+        if (rc) return rc;
+        BK(cudaStreamSynchronize(b->stream), "iterate sync");
+        return GABP_OK;
+    }
+    int rc;
+    if (b->cur == 1) {   // checks run at parity 0
+        for (int i = 0; i < count; ++i) b->h_active[i] = 1;
+        if ((rc = batch_upload_active(b))) return rc;
+        if ((rc = batch_run(b, 1, damping))) return rc;
+    }
+    int64_t done = 0;
+    for (;;) {
+        if ((rc = batch_residuals(b))) return rc;
+        int active = 0;
+        for (int i = 0; i < count; ++i) {
+            if (!std::isfinite(b->res[i]))
+                return bfail(b, GABP_ERR_DIVERGED, "problem " + std::to_string(i) + ": residual is not finite");
+            b->h_active[i] = b->res[i] > b->opt.tol ? 1 : 0;
+            active += b->h_active[i];
+        }
+        if (!active) return GABP_OK;
+        if (done >= b->opt.max_iters) return bfail(b, GABP_ERR_TIMEOUT, std::to_string(active) + " problems above tol at max_iters");
+        if ((rc = batch_upload_active(b))) return rc;
+        if ((rc = batch_run(b, b->opt.check_every, damping))) return rc;
+        done += b->opt.check_every;
+    }
+}
+
+int gabp_batch_residuals(gabp_batch *b, double *rel) {
+    if (!b || !rel) return b ? bfail(b, GABP_ERR_ARG, "rel must not be NULL") : GABP_ERR_ARG;
+    DeviceGuard g(b->dev);
+    int rc = batch_residuals(b);
+    if (rc) return rc;
+    for (size_t i = 0; i < b->inst.size(); ++i) rel[i] = b->res[i];
+    return GABP_OK;
+}
+
+int gabp_batch_marginals(gabp_batch *b, int index, double *mean, double *var) {
+    if (!b) return GABP_ERR_ARG;
+    if (index < 0 || index >= (int)b->inst.size()) return bfail(b, GABP_ERR_ARG, "index out of range");
+    gabp_ctx *c = b->inst[index];
+    c->cur = b->cur;
+    const int rc = gabp_marginals(c, mean, var);
+    if (rc) return bfail(b, rc, c->err);
+    return GABP_OK;
+}
+
+int gabp_batch_get_stats(const gabp_batch *b, int index, gabp_stats *s) {
+    if (!b || !s || index < 0 || index >= (int)b->inst.size()) return GABP_ERR_ARG;
+    const int rc = gabp_get_stats(b->inst[index], s);
+    s->iterations = b->iters[index];
+    s->last_residual = b->res[index];
+    s->kernel = GABP_KERNEL_SWEEP;
+    s->tile_x = 30;
+    s->tile_y = b->H;
+    return rc;
+}
+
+int gabp_batch_strip_height(const gabp_batch *b) { return b ? b->H : 0; }
+
+const char *gabp_batch_last_error(const gabp_batch *b) { return b ? b->err.c_str() : t_batch_create_err.c_str(); }
+
+void gabp_batch_destroy(gabp_batch *b) {
+    if (!b) return;
+    {
+        DeviceGuard g(b->dev);
+        if (b->stream) cudaStreamSynchronize(b->stream);
+        batch_free(b);
+    }
+    delete b;
 }
 
 }  // extern "C"

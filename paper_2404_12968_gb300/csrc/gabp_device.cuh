@@ -72,6 +72,21 @@ template <typename T> struct Belief {
     T ehi, elo, lhi, llo;
 };
 
+// Adds the observation messages into node (x, y) that come from the base cells of one row:
+// base (x-1, row) with corner cl for indices [lo, mid) and base (x, row) with corner cr for
+// [mid, hi).  The two ranges are adjacent in the base-sorted observation array, so the terms
+// are added in increasing observation index; every iteration kernel uses this order (corners
+// 1, 0 from the node's row, then 3, 2 from the row below).
+template <typename T>
+__device__ __forceinline__ void add_obs_pair(CompSum<T> &se, CompSum<T> &sl, const T *O, int lo, int mid,
+                                             int hi, int cl, int cr) {
+    for (int k = lo; k < hi; ++k) {
+        const int c = k < mid ? cl : cr;
+        se.add(O[8 * (int64_t)k + c]);
+        sl.add(O[8 * (int64_t)k + 4 + c]);
+    }
+}
+
 // Cavity of one edge: the belief minus the edge's own incoming message, evaluated as
 // (hi - own) + lo (App. A, variable-to-factor message).
 template <typename T>

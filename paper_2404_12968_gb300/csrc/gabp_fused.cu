@@ -97,13 +97,9 @@ __global__ void __launch_bounds__(FT) k_fused(DevProblem p, int src, T beta) {
         if (gy > 0) { m = sm[(DIR_N * RY + ry - 1) * RX + rx]; se.add(m.x); sl.add(m.y); }
         if (gy < ny - 1) { m = sm[(DIR_S * RY + ry + 1) * RX + rx]; se.add(m.x); sl.add(m.y); }
         if (p.m > 0) {
-            for (int k = optr[v]; k < optr[v + 1]; ++k) { se.add(O[8 * (int64_t)k + 0]); sl.add(O[8 * (int64_t)k + 4]); }
-            if (gx > 0)
-                for (int k = optr[v - 1]; k < optr[v]; ++k) { se.add(O[8 * (int64_t)k + 1]); sl.add(O[8 * (int64_t)k + 5]); }
+            add_obs_pair(se, sl, O, gx > 0 ? optr[v - 1] : optr[v], optr[v], optr[v + 1], 1, 0);
             if (gy > 0)
-                for (int k = optr[v - nx]; k < optr[v - nx + 1]; ++k) { se.add(O[8 * (int64_t)k + 2]); sl.add(O[8 * (int64_t)k + 6]); }
-            if (gx > 0 && gy > 0)
-                for (int k = optr[v - nx - 1]; k < optr[v - nx]; ++k) { se.add(O[8 * (int64_t)k + 3]); sl.add(O[8 * (int64_t)k + 7]); }
+                add_obs_pair(se, sl, O, gx > 0 ? optr[v - nx - 1] : optr[v - nx], optr[v - nx], optr[v - nx + 1], 3, 2);
         }
         se.finish();
         sl.finish();

@@ -1,22 +1,28 @@
-// Fused GaBP iteration, FP32, persistent blocks fed by TMA.
+// Fused GaBP iteration, FP32, persistent blocks fed by TMA, warp-per-row tiles.
 //
-// Same per-tile work as the plain fused kernel (gabp_fused.cu): stage the 5 prior-message
-// planes over the tile plus a 2-cell halo, compute the compensated beliefs of the tile plus a
-// 1-cell halo, update the tile's cell factors and the observation factors based in the tile,
-// write the damped messages to the other ping-pong buffer.  Here each block is persistent and
-// walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ... (row-major tile order, so the tiles in
-// flight at any moment are spatial neighbours and their halos are served by L2).  One thread
-// issues, per tile, two TMA tensor loads into an S-stage shared-memory ring:
-//   * the 5 planes as one 3-D box (2 (TX+4) floats x (TY+4) rows x 5 planes), out-of-grid
-//     positions zero-filled by the TMA unit;
-//   * the window of observation pointers (TX+8) x (TY+3) of the observations-by-base-cell index,
-// and completion is tracked by one mbarrier per stage (complete_tx), so the loads of the next
-// S-1 tiles are in flight while the current tile computes.  Every mbarrier wait is bounded: on
-// timeout the kernel raises the error flag, waits (bounded) for its own outstanding copies and
-// returns.
+// Work unit: a tile of 30 columns x TY rows of cells.  The nodes its factors touch form a
+// 32 x (TY+2) window (the tile plus a one-cell halo), so one warp covers one window row with
+// every lane busy.  Per tile the block
+//   A. computes the compensated beliefs of the window: warp w takes window rows w, w+8, ...,
+//      lane = column; prior messages come from the staged planes, observation messages from
+//      global memory through the staged observation index;
+//   B. updates the tile's cell factors (warp w takes tile rows w, w+8, ..., lanes 0..29) and
+//      the observation factors based in the tile (one per thread), writing the damped messages
+//      to the other ping-pong buffer.
+// Two barriers per tile.  Staging: each block is persistent and walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... in row-major order (tiles in flight are spatial neighbours, so
+// halo re-reads hit L2).  One thread issues, per tile, two TMA tensor loads into an S-stage ring
+// of shared-memory buffers, completion tracked by one mbarrier per stage:
+//   * the 5 message planes over the tile plus a 2-cell halo, one 3-D box of
+//     2 x 34 floats x (TY+4) rows x 5 planes, zero-filled outside the grid;
+//   * the observation index (observations before each base cell) over a 40 x (TY+3) box whose
+//     x origin is rounded down to a multiple of 4 (16-byte aligned start).
+// The zero fill makes the boundary terms of the belief sums exact zeros (adding an exact zero
+// leaves a TwoSum unchanged), so the sums need no boundary tests and match the other kernels
+// bit for bit.  Every mbarrier wait is bounded; on timeout the kernel raises the error flag,
+// waits (bounded) for its own outstanding copies and returns.
 //
-// Requirements (checked on the host): FP32 messages, nx a multiple of 4 (16-byte row pitch of
-// the index, 16-byte aligned box starts).
+// Requirements (checked on the host): FP32 messages, nx a multiple of 4.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -26,6 +32,10 @@
 namespace gabp {
 
 namespace {
+
+constexpr int TTX = 30;   // tile width in cells: window width 32
+constexpr int TNT = 256;  // threads per block (8 warps)
+constexpr int TW = TNT / 32;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -76,50 +86,53 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 
 __host__ __device__ constexpr size_t a128(size_t x) { return (x + 127) & ~size_t(127); }
 
-template <int TX, int TY, int S, int NT> struct TmaLayout {
-    static constexpr int RX = TX + 4, RY = TY + 4;   // staged message window (cells)
-    static constexpr int BX = TX + 2, BY = TY + 2;   // belief window
-    static constexpr int OX = TX + 8, OY = TY + 3;   // observation-pointer window
+template <int TY, int S> struct TileLayout {
+    static constexpr int RX = TTX + 4, RY = TY + 4;   // staged planes (cells), origin (x0-2, y0-2)
+    static constexpr int BX = 32, BY = TY + 2;        // belief window, origin (x0-1, y0-1)
+    static constexpr int OXW = 40, OY = TY + 3;       // observation index window, origin (xs, y0-2)
     static constexpr uint32_t plane_bytes = 5u * RY * RX * 8u;
-    static constexpr uint32_t optr_bytes = (uint32_t)OX * OY * 4u;
+    static constexpr uint32_t optr_bytes = (uint32_t)OXW * OY * 4u;
     static constexpr size_t stage = a128(plane_bytes) + a128(optr_bytes);
     static constexpr size_t bel_off = S * stage;
     static constexpr size_t bar_off = a128(bel_off + sizeof(Belief<float>) * BX * BY);
     static constexpr size_t ints_off = bar_off + 8 * (S + 1);   // S stage barriers + 1 test barrier
-    static constexpr size_t bytes = ints_off + sizeof(int) * (2 * (TY + 1) + 1);
-    static_assert(2 * RX <= 256 && RY <= 256 && OX <= 256, "TMA box dimension above 256");
+    static constexpr size_t bytes = ints_off + sizeof(int) * (2 * TY + 4);
+    static_assert(BY % TW == 0, "window rows must split evenly over the warps");
+    static_assert(2 * RX <= 256 && RY <= 256 && OXW <= 256 && OY <= 256, "TMA box dimension above 256");
 };
 
-template <int TX, int TY, int S, int NT>
-__global__ void __launch_bounds__(NT) k_fused_tma(const __grid_constant__ CUtensorMap mplanes,
-                                                  const __grid_constant__ CUtensorMap moptr, DevProblem p,
-                                                  int src, float beta) {
-    using LY = TmaLayout<TX, TY, S, NT>;
-    constexpr int RX = LY::RX, RY = LY::RY, BX = LY::BX, BY = LY::BY, OX = LY::OX;
+template <int TY, int S>
+__global__ void __launch_bounds__(TNT) k_fused_tma(const __grid_constant__ CUtensorMap mplanes,
+                                                   const __grid_constant__ CUtensorMap moptr, DevProblem p,
+                                                   int src, float beta) {
+    using LY = TileLayout<TY, S>;
+    constexpr int RX = LY::RX, RY = LY::RY, BX = LY::BX, BY = LY::BY, OXW = LY::OXW;
     extern __shared__ __align__(128) unsigned char smem[];
-    Belief<float> *sb = reinterpret_cast<Belief<float> *>(smem + LY::bel_off);
+    Belief<float> *sb = reinterpret_cast<Belief<float> *>(smem + LY::bel_off);   // [BY][32]
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + LY::bar_off);
-    int *rstart = reinterpret_cast<int *>(smem + LY::ints_off);
-    int *rpre = rstart + (TY + 1);
-    int *flag = rpre + (TY + 1);
+    int *rstart = reinterpret_cast<int *>(smem + LY::ints_off);   // [TY]
+    int *rpre = rstart + TY;                                      // [TY + 1] exclusive prefix
+    int *flag = rpre + TY + 1;
 
     const int nx = p.nx, ny = p.ny;
     const int64_t n = p.n;
-    const int ntx = (nx + TX - 1) / TX;
+    const int ntx = (nx + TTX - 1) / TTX;
     const int ntiles = ntx * ((ny + TY - 1) / TY);
     const int G = gridDim.x;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float2 *Q = (float2 *)p.P[src ^ 1];
     const float *O = (const float *)p.O[src];
     float *OQ = (float *)p.O[src ^ 1];
+    const float var_prior = (float)(1.0 / p.gamma);
+    const float aC_in = (float)p.aC[4];
 
     auto issue = [&](int stage, int tile) {
-        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+        const int x0 = (tile % ntx) * TTX, y0 = (tile / ntx) * TY;
         unsigned char *base = smem + stage * LY::stage;
         const uint32_t bar = smem_addr(&bars[stage]);
         mbar_expect_tx(bar, LY::plane_bytes + LY::optr_bytes);
         tma_load_3d(smem_addr(base), &mplanes, 2 * (x0 - 2), y0 - 2, 0, bar);
-        tma_load_2d(smem_addr(base + a128(LY::plane_bytes)), &moptr, x0 - 4, y0 - 2, bar);
+        tma_load_2d(smem_addr(base + a128(LY::plane_bytes)), &moptr, (x0 - 2) & ~3, y0 - 2, bar);
     };
 
     if (tid == 0) {
@@ -146,101 +159,110 @@ __global__ void __launch_bounds__(NT) k_fused_tma(const __grid_constant__ CUtens
         }
 
     int it = 0;
+    bool failed = false;
     for (;; ++it) {
         const int tile = blockIdx.x + it * G;
         if (tile >= ntiles) break;
         const int stage = it % S;
-        const uint32_t parity = (uint32_t)((it / S) & 1);
-        if (!mbar_wait(smem_addr(&bars[stage]), parity)) *flag = 1;
-        __syncthreads();
-        if (*flag) break;
+        const bool ok = mbar_wait(smem_addr(&bars[stage]), (uint32_t)((it / S) & 1));
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        // every thread has finished the previous tile: refill its stage with tile it-1+S
+        if (tid == 0 && it > 0) {
+            const int t2 = blockIdx.x + (it - 1 + S) * G;
+            if (t2 < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue((it - 1) % S, t2);
+            }
+        }
 
-        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+        const int x0 = (tile % ntx) * TTX, y0 = (tile / ntx) * TY;
+        const int xs = (x0 - 2) & ~3;
         const float2 *sm = reinterpret_cast<const float2 *>(smem + stage * LY::stage);   // [5][RY][RX]
         const int *W = reinterpret_cast<const int *>(smem + stage * LY::stage + a128(LY::plane_bytes));
-        // observation pointer of base cell (x, y) from the staged window (origin x0-4, y0-2)
-        auto wptr = [&](int x, int y) { return W[(y - y0 + 2) * OX + (x - x0 + 4)]; };
+        auto wptr = [&](int x, int y) { return W[(y - y0 + 2) * OXW + (x - xs)]; };
 
-        // observation ranges of the tile's own base cells, one per tile row
-        if (tid <= TY) {
-            const int r = tid, gy = y0 + r;
-            int lo = 0, cnt = 0;
-            if (r < TY && gy < ny) {
-                lo = wptr(x0, gy);
-                cnt = wptr(min(x0 + TX, nx - 1), gy) - lo;
+        // ---- A: observation ranges of the tile's rows (last warp), beliefs of the window ----
+        if (p.m > 0 && warp == TW - 1) {
+            int st = 0, cnt = 0;
+            const int gy = y0 + lane;
+            if (lane < TY && gy < ny) {
+                st = wptr(x0, gy);
+                cnt = wptr(min(x0 + TTX, nx - 1), gy) - st;
                 if (cnt < 0) cnt = 0;
             }
-            rstart[r] = lo;
-            rpre[r] = cnt;
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            if (lane < TY) {
+                rstart[lane] = st;
+                rpre[lane] = inc - cnt;
+            }
+            if (lane == TY - 1) rpre[TY] = inc;
         }
-
-        // compensated beliefs over the tile plus a 1-cell halo
-        for (int q = tid; q < BX * BY; q += NT) {
-            const int ly = q / BX, lx = q - ly * BX;
-            const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-            if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) continue;
-            const int rx = lx + 1, ry = ly + 1;
-            float2 m = sm[(DIR_C * RY + ry) * RX + rx];
-            CompSum<float> se(m.x), sl(m.y);
-            if (gx > 0) { m = sm[(DIR_E * RY + ry) * RX + rx - 1]; se.add(m.x); sl.add(m.y); }
-            if (gx < nx - 1) { m = sm[(DIR_W * RY + ry) * RX + rx + 1]; se.add(m.x); sl.add(m.y); }
-            if (gy > 0) { m = sm[(DIR_N * RY + ry - 1) * RX + rx]; se.add(m.x); sl.add(m.y); }
-            if (gy < ny - 1) { m = sm[(DIR_S * RY + ry + 1) * RX + rx]; se.add(m.x); sl.add(m.y); }
-            if (p.m > 0) {
-                // corner 0: base (gx, gy); 1: (gx-1, gy); 2: (gx, gy-1); 3: (gx-1, gy-1).
-                // An end pointer beyond the last column reads the zero fill: the range is empty,
-                // as it must be (no base cell in the last column).
-                const int a0 = wptr(gx, gy), a1 = wptr(gx + 1, gy);
-                for (int k = a0; k < a1; ++k) { se.add(O[8 * (int64_t)k + 0]); sl.add(O[8 * (int64_t)k + 4]); }
-                if (gx > 0) {
-                    const int b0 = wptr(gx - 1, gy);
-                    for (int k = b0; k < a0; ++k) { se.add(O[8 * (int64_t)k + 1]); sl.add(O[8 * (int64_t)k + 5]); }
-                }
-                if (gy > 0) {
-                    const int c0 = wptr(gx, gy - 1), c1 = wptr(gx + 1, gy - 1);
-                    for (int k = c0; k < c1; ++k) { se.add(O[8 * (int64_t)k + 2]); sl.add(O[8 * (int64_t)k + 6]); }
-                    if (gx > 0) {
-                        const int d0 = wptr(gx - 1, gy - 1);
-                        for (int k = d0; k < c0; ++k) { se.add(O[8 * (int64_t)k + 3]); sl.add(O[8 * (int64_t)k + 7]); }
+        for (int ly = warp; ly < BY; ly += TW) {
+            const int gx = x0 - 1 + lane, gy = y0 - 1 + ly;
+            Belief<float> b;
+            if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+                const int rx = lane + 1, ry = ly + 1;
+                float2 m = sm[(DIR_C * RY + ry) * RX + rx];
+                CompSum<float> se(m.x), sl(m.y);
+                // zero-filled outside the grid: the boundary terms add exact zeros
+                m = sm[(DIR_E * RY + ry) * RX + rx - 1]; se.add(m.x); sl.add(m.y);
+                m = sm[(DIR_W * RY + ry) * RX + rx + 1]; se.add(m.x); sl.add(m.y);
+                m = sm[(DIR_N * RY + ry - 1) * RX + rx]; se.add(m.x); sl.add(m.y);
+                m = sm[(DIR_S * RY + ry + 1) * RX + rx]; se.add(m.x); sl.add(m.y);
+                if (p.m > 0) {
+                    const bool last = gx == nx - 1;
+                    const int a0 = wptr(gx, gy);
+                    add_obs_pair(se, sl, O, gx > 0 ? wptr(gx - 1, gy) : a0, a0, last ? a0 : wptr(gx + 1, gy), 1, 0);
+                    if (gy > 0) {
+                        const int c0 = wptr(gx, gy - 1);
+                        add_obs_pair(se, sl, O, gx > 0 ? wptr(gx - 1, gy - 1) : c0, c0, last ? c0 : wptr(gx + 1, gy - 1), 3, 2);
                     }
                 }
+                se.finish();
+                sl.finish();
+                b.ehi = se.hi; b.elo = se.lo; b.lhi = sl.hi; b.llo = sl.lo;
+            } else {
+                b.ehi = b.elo = b.lhi = b.llo = 0.f;
             }
-            se.finish();
-            sl.finish();
-            Belief<float> b;
-            b.ehi = se.hi; b.elo = se.lo; b.lhi = sl.hi; b.llo = sl.lo;
-            sb[q] = b;
+            sb[ly * BX + lane] = b;
         }
         __syncthreads();
-        if (p.m > 0 && tid == 0) {
-            int acc = 0;
-            for (int r = 0; r < TY; ++r) {
-                const int c = rpre[r];
-                rpre[r] = acc;
-                acc += c;
-            }
-            rpre[TY] = acc;
-        }
 
-        // prior cell factors of the tile
-        const float var_prior = (float)(1.0 / p.gamma);
-        for (int q = tid; q < TX * TY; q += NT) {
-            const int ty = q / TX, tx = q - ty * TX;
-            const int gx = x0 + tx, gy = y0 + ty;
-            if (gx >= nx || gy >= ny) continue;
+        // ---- B: cell factors of the tile, then the observation factors based in it ----
+        for (int ty = warp; ty < TY; ty += TW) {
+            const int tx = lane, gx = x0 + tx, gy = y0 + ty;
+            if (tx >= TTX || gx >= nx || gy >= ny) continue;
             const int64_t c = (int64_t)gy * nx + gx;
-            const int deg = grid_degree(gy, gx, nx, ny);
-            const float a[5] = {(float)p.aC[deg], gx > 0 ? -1.f : 0.f, gx < nx - 1 ? -1.f : 0.f,
-                                gy > 0 ? -1.f : 0.f, gy < ny - 1 ? -1.f : 0.f};
-            const int bxs[5] = {tx + 1, tx, tx + 2, tx + 1, tx + 1};
-            const int bys[5] = {ty + 1, ty + 1, ty + 1, ty, ty + 2};
+            const Belief<float> *bs[5] = {&sb[(ty + 1) * BX + tx + 1], &sb[(ty + 1) * BX + tx],
+                                          &sb[(ty + 1) * BX + tx + 2], &sb[ty * BX + tx + 1],
+                                          &sb[(ty + 2) * BX + tx + 1]};
             float2 own[5];
+#pragma unroll
+            for (int u = 0; u < 5; ++u) own[u] = sm[(u * RY + ty + 2) * RX + tx + 2];
+            const bool inner = gx > 0 && gx < nx - 1 && gy > 0 && gy < ny - 1;
+            float a[5];
+            if (inner) {
+                a[0] = aC_in; a[1] = -1.f; a[2] = -1.f; a[3] = -1.f; a[4] = -1.f;
+            } else {
+                a[0] = (float)p.aC[grid_degree(gy, gx, nx, ny)];
+                a[1] = gx > 0 ? -1.f : 0.f;
+                a[2] = gx < nx - 1 ? -1.f : 0.f;
+                a[3] = gy > 0 ? -1.f : 0.f;
+                a[4] = gy < ny - 1 ? -1.f : 0.f;
+            }
             float lam[5], eta[5];
 #pragma unroll
             for (int u = 0; u < 5; ++u) {
-                own[u] = sm[(u * RY + ty + 2) * RX + tx + 2];
                 if (a[u] != 0.f) {
-                    cavity(sb[bys[u] * BX + bxs[u]], own[u].x, own[u].y, eta[u], lam[u]);
+                    cavity(*bs[u], own[u].x, own[u].y, eta[u], lam[u]);
                 } else {
                     lam[u] = 1.f;
                     eta[u] = 0.f;
@@ -258,93 +280,86 @@ __global__ void __launch_bounds__(NT) k_fused_tma(const __grid_constant__ CUtens
                     out.x = 0.f;
                     out.y = 0.f;
                 }
-                Q[u * n + c] = out;
+                __stcs(Q + u * n + c, out);
             }
         }
-        __syncthreads();   // rpre is final; every thread is done with this stage's planes
-
-        // observation factors based in the tile
         if (p.m > 0) {
             const int total = rpre[TY];
             const float *Wt = (const float *)p.ow;
             const float *YV = (const float *)p.ovar;
-            for (int q = tid; q < total; q += NT) {
-                int r = 0;
-                while (r + 1 < TY && rpre[r + 1] <= q) ++r;
+            for (int q = tid; q < total; q += TNT) {
+                int lo = 0, hi = TY - 1;   // last row r with rpre[r] <= q
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (rpre[mid] <= q) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int r = lo;
                 const int64_t k = rstart[r] + (q - rpre[r]);
-                const int b = p.obase[k];
-                const int by = b / nx, bx = b - by * nx;
-                const int lx = bx - x0 + 1, ly = by - y0 + 1;
-                const int bidx[4] = {ly * BX + lx, ly * BX + lx + 1, (ly + 1) * BX + lx, (ly + 1) * BX + lx + 1};
+                const int bx = p.obase[k] - (y0 + r) * nx;
+                const int lx = bx - x0 + 1, ly = r + 1;   // window coordinates of the base node
+                const Belief<float> *ob[4] = {&sb[ly * BX + lx], &sb[ly * BX + lx + 1], &sb[(ly + 1) * BX + lx],
+                                              &sb[(ly + 1) * BX + lx + 1]};
                 const float4 w4 = *reinterpret_cast<const float4 *>(Wt + 4 * k);
-                const float a[4] = {w4.x, w4.y, w4.z, w4.w};
+                const float aw[4] = {w4.x, w4.y, w4.z, w4.w};
                 const float4 oe4 = *reinterpret_cast<const float4 *>(O + 8 * k);
                 const float4 ol4 = *reinterpret_cast<const float4 *>(O + 8 * k + 4);
                 const float oe[4] = {oe4.x, oe4.y, oe4.z, oe4.w};
                 const float ol[4] = {ol4.x, ol4.y, ol4.z, ol4.w};
-                float lam[4], eta[4];
+                float olam[4], oeta[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) cavity(sb[bidx[u]], oe[u], ol[u], eta[u], lam[u]);
-                float L[4], E[4];
-                factor_messages<float, 4>(a, YV[2 * k + 1], YV[2 * k], lam, eta, L, E);
+                for (int u = 0; u < 4; ++u) cavity(*ob[u], oe[u], ol[u], oeta[u], olam[u]);
+                float OL[4], OE[4];
+                const float2 yv = *reinterpret_cast<const float2 *>(YV + 2 * k);
+                factor_messages<float, 4>(aw, yv.y, yv.x, olam, oeta, OL, OE);
                 float4 ne, nl;
-                ne.x = damp(oe[0], E[0], beta); ne.y = damp(oe[1], E[1], beta);
-                ne.z = damp(oe[2], E[2], beta); ne.w = damp(oe[3], E[3], beta);
-                nl.x = damp(ol[0], L[0], beta); nl.y = damp(ol[1], L[1], beta);
-                nl.z = damp(ol[2], L[2], beta); nl.w = damp(ol[3], L[3], beta);
+                ne.x = damp(oe[0], OE[0], beta); ne.y = damp(oe[1], OE[1], beta);
+                ne.z = damp(oe[2], OE[2], beta); ne.w = damp(oe[3], OE[3], beta);
+                nl.x = damp(ol[0], OL[0], beta); nl.y = damp(ol[1], OL[1], beta);
+                nl.z = damp(ol[2], OL[2], beta); nl.w = damp(ol[3], OL[3], beta);
                 *reinterpret_cast<float4 *>(OQ + 8 * k) = ne;
                 *reinterpret_cast<float4 *>(OQ + 8 * k + 4) = nl;
             }
         }
-        __syncthreads();   // beliefs and ranges are reused by the next tile
-
-        if (tid == 0) {
-            const int t2 = blockIdx.x + (it + S) * G;
-            if (t2 < ntiles) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(stage, t2);
-            }
-        }
     }
 
-    if (*flag) {
-        if (tid == 0) {
-            atomicExch(p.err, 1);
-            // drain this block's outstanding copies (bounded)
-            for (int j = it; j < it + S; ++j) {
-                const int t = blockIdx.x + j * G;
-                if (t >= ntiles) break;
-                mbar_wait(smem_addr(&bars[j % S]), (uint32_t)((j / S) & 1));
-            }
+    if (failed && tid == 0) {
+        atomicExch(p.err, 1);
+        // drain this block's outstanding copies (bounded): tiles it .. it+S-1 may be in flight
+        for (int j = it; j < it + S; ++j) {
+            const int t = blockIdx.x + j * G;
+            if (t >= ntiles) break;
+            mbar_wait(smem_addr(&bars[j % S]), (uint32_t)((j / S) & 1));
         }
-        __syncthreads();
     }
 }
 
-template <int TX, int TY, int S, int NT>
+template <int TY, int S>
 cudaError_t launch_cfg(const DevProblem &p, const TmaMaps &maps, int src, double beta, cudaStream_t st) {
-    using LY = TmaLayout<TX, TY, S, NT>;
+    using LY = TileLayout<TY, S>;
     static int grid_cache = 0;
     static int configured_dev = -1;
+    // the tensor maps' boxes must have been encoded for this tile height (the smem layout and
+    // the expected transaction bytes depend on it)
+    if (maps.tx != TTX || maps.ty != TY) return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (configured_dev != dev) {
-        e = cudaFuncSetAttribute(k_fused_tma<TX, TY, S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)LY::bytes);
+        e = cudaFuncSetAttribute(k_fused_tma<TY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::bytes);
         if (e != cudaSuccess) return e;
         int nsm = 0, per_sm = 0;
         e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tma<TX, TY, S, NT>, NT, LY::bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tma<TY, S>, TNT, LY::bytes);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         grid_cache = nsm * per_sm;
         configured_dev = dev;
     }
-    const int ntiles = ((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
+    const int ntiles = ((p.nx + TTX - 1) / TTX) * ((p.ny + TY - 1) / TY);
     const int grid = ntiles < grid_cache ? ntiles : grid_cache;
-    k_fused_tma<TX, TY, S, NT><<<grid, NT, LY::bytes, st>>>(maps.planes[src], maps.optr, p, src, (float)beta);
+    k_fused_tma<TY, S><<<grid, TNT, LY::bytes, st>>>(maps.planes[src], maps.optr, p, src, (float)beta);
     return cudaGetLastError();
 }
 
@@ -365,9 +380,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 
 }  // namespace
 
-bool tma_shape_supported(int tx, int ty) {
-    return (tx == 64 && ty == 16) || (tx == 32 && ty == 16) || (tx == 64 && ty == 8) || (tx == 32 && ty == 32);
-}
+bool tma_shape_supported(int tx, int ty) { return tx == TTX && (ty == 14 || ty == 22 || ty == 30); }
 
 bool tma_problem_supported(const DevProblem &p) { return p.prec == 0 && p.nx % 4 == 0 && p.nx >= 4; }
 
@@ -375,6 +388,7 @@ bool tma_problem_supported(const DevProblem &p) { return p.prec == 0 && p.nx % 4
 // observation index (2-D: nx x ny int32 of optr[0..n)), with boxes for the tile shape.
 cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps) {
     maps.valid = false;
+    if (!tma_shape_supported(tx, ty)) return cudaErrorInvalidValue;
     auto enc = encoder();
     if (!enc) return cudaErrorNotSupported;
     for (int b = 0; b < 2; ++b) {
@@ -389,7 +403,7 @@ cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps) {
     }
     cuuint64_t dims[2] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny};
     cuuint64_t strides[1] = {(cuuint64_t)p.nx * 4};
-    cuuint32_t box[2] = {(cuuint32_t)(tx + 8), (cuuint32_t)(ty + 3)};
+    cuuint32_t box[2] = {40, (cuuint32_t)(ty + 3)};
     cuuint32_t es[2] = {1, 1};
     CUresult r = enc(&maps.optr, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, (void *)p.optr, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -402,20 +416,19 @@ cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps) {
 }
 
 size_t tma_smem_bytes(int tx, int ty) {
-    if (tx == 64 && ty == 16) return TmaLayout<64, 16, 2, 512>::bytes;
-    if (tx == 32 && ty == 16) return TmaLayout<32, 16, 3, 256>::bytes;
-    if (tx == 64 && ty == 8) return TmaLayout<64, 8, 2, 256>::bytes;
-    if (tx == 32 && ty == 32) return TmaLayout<32, 32, 2, 512>::bytes;
+    if (tx != TTX) return 0;
+    if (ty == 14) return TileLayout<14, 2>::bytes;
+    if (ty == 22) return TileLayout<22, 2>::bytes;
+    if (ty == 30) return TileLayout<30, 2>::bytes;
     return 0;
 }
 
 cudaError_t launch_tma_iteration(const DevProblem &p, const TmaMaps &maps, int src, double beta,
                                  cudaStream_t st) {
     if (!maps.valid) return cudaErrorInvalidValue;
-    if (maps.tx == 64 && maps.ty == 16) return launch_cfg<64, 16, 2, 512>(p, maps, src, beta, st);
-    if (maps.tx == 32 && maps.ty == 16) return launch_cfg<32, 16, 3, 256>(p, maps, src, beta, st);
-    if (maps.tx == 64 && maps.ty == 8) return launch_cfg<64, 8, 2, 256>(p, maps, src, beta, st);
-    if (maps.tx == 32 && maps.ty == 32) return launch_cfg<32, 32, 2, 512>(p, maps, src, beta, st);
+    if (maps.ty == 14) return launch_cfg<14, 2>(p, maps, src, beta, st);
+    if (maps.ty == 22) return launch_cfg<22, 2>(p, maps, src, beta, st);
+    if (maps.ty == 30) return launch_cfg<30, 2>(p, maps, src, beta, st);
     return cudaErrorInvalidValue;
 }
 

@@ -60,6 +60,10 @@ size_t fused_smem_bytes(int prec, FusedShape shape);
 // ---- warp-synchronous column sweep, FP32 (gabp_sweep.cu); tile 30 columns x h rows ----
 bool sweep_shape_supported(int h);
 cudaError_t launch_sweep_iteration(const DevProblem &p, int src, double beta, int h, cudaStream_t st);
+int sweep_strips(int nx, int ny, int h);
+// all problems of a batch in one persistent launch (FP32 problems; table/strip_start/active on device)
+cudaError_t launch_sweep_batch(const DevProblem *table, const int *strip_start, const int *active, int count,
+                               int total_strips, int src, double beta, int h, cudaStream_t st);
 
 // ---- TMA-fed persistent fused path, FP32 (gabp_fused_tma.cu) ----
 struct TmaMaps {

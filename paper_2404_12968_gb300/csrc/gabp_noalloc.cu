@@ -20,7 +20,7 @@
 #include <cstdio>
 #include <mutex>
 
-#include "../../include/gabp.h"
+#include "gabp.h"
 #include "gabp_device.cuh"
 #include "gabp_internal.h"
 

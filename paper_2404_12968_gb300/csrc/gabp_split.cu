@@ -36,14 +36,9 @@ template <typename T> __global__ void k_beliefs(DevProblem p, int src) {
     if (i < ny - 1) { q = P[DIR_S * n + v + nx]; se.add(q.x); sl.add(q.y); }
     if (p.m > 0) {
         const int *optr = p.optr;
-        // corner 0: base v; corner 1: base v-1; corner 2: base v-nx; corner 3: base v-nx-1
-        for (int k = optr[v]; k < optr[v + 1]; ++k) { se.add(O[8 * (int64_t)k + 0]); sl.add(O[8 * (int64_t)k + 4]); }
-        if (j > 0)
-            for (int k = optr[v - 1]; k < optr[v]; ++k) { se.add(O[8 * (int64_t)k + 1]); sl.add(O[8 * (int64_t)k + 5]); }
-        if (i > 0)
-            for (int k = optr[v - nx]; k < optr[v - nx + 1]; ++k) { se.add(O[8 * (int64_t)k + 2]); sl.add(O[8 * (int64_t)k + 6]); }
-        if (i > 0 && j > 0)
-            for (int k = optr[v - nx - 1]; k < optr[v - nx]; ++k) { se.add(O[8 * (int64_t)k + 3]); sl.add(O[8 * (int64_t)k + 7]); }
+        // bases (j-1, i), (j, i) then (j-1, i-1), (j, i-1): corners 1, 0, 3, 2
+        add_obs_pair(se, sl, O, j > 0 ? optr[v - 1] : optr[v], optr[v], optr[v + 1], 1, 0);
+        if (i > 0) add_obs_pair(se, sl, O, j > 0 ? optr[v - nx - 1] : optr[v - nx], optr[v - nx], optr[v - nx + 1], 3, 2);
     }
     se.finish();
     sl.finish();

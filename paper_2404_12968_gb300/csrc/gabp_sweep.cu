@@ -140,17 +140,12 @@ __device__ __forceinline__ Belief<float> belief_at(const DevProblem &p, const fl
     if (y > 0) { m = below.msg.m[DIR_N]; se.add(m.x); sl.add(m.y); }
     if (y < p.ny - 1) { se.add(above_s.x); sl.add(above_s.y); }
     if (p.m > 0) {
-        // corner 0: base (x, y); 1: (x-1, y); 2: (x, y-1); 3: (x-1, y-1).  Base cells exist only
-        // in columns <= nx-2 and rows <= ny-2; an end pointer outside the grid reads 0, which
-        // leaves the (necessarily empty) range of the last column empty.
-        for (int k = at.o0; k < at.o1; ++k) { se.add(O[8 * (int64_t)k + 0]); sl.add(O[8 * (int64_t)k + 4]); }
-        if (x > 0)
-            for (int k = at.om; k < at.o0; ++k) { se.add(O[8 * (int64_t)k + 1]); sl.add(O[8 * (int64_t)k + 5]); }
-        if (y > 0) {
-            for (int k = below.o0; k < below.o1; ++k) { se.add(O[8 * (int64_t)k + 2]); sl.add(O[8 * (int64_t)k + 6]); }
-            if (x > 0)
-                for (int k = below.om; k < below.o0; ++k) { se.add(O[8 * (int64_t)k + 3]); sl.add(O[8 * (int64_t)k + 7]); }
-        }
+        // bases (x-1, y), (x, y) then (x-1, y-1), (x, y-1): corners 1, 0, 3, 2.  Base cells exist
+        // only in columns <= nx-2 and rows <= ny-2 (an index read outside the grid is 0, so the
+        // last column's empty range is closed explicitly).
+        const bool last = x == p.nx - 1;   // no base cell in the last column: corner-0 range empty
+        add_obs_pair(se, sl, O, x > 0 ? at.om : at.o0, at.o0, last ? at.o0 : at.o1, 1, 0);
+        if (y > 0) add_obs_pair(se, sl, O, x > 0 ? below.om : below.o0, below.o0, last ? below.o0 : below.o1, 3, 2);
     }
     se.finish();
     sl.finish();
@@ -262,15 +257,13 @@ __device__ __forceinline__ void obs_batch(const DevProblem &p, const WarpRing &r
     }
 }
 
+// One strip (30 columns x H rows) of one problem, processed by one warp.
 template <int H>
-__global__ void __launch_bounds__(SWEEP_WARPS * 32) k_sweep(DevProblem p, int src, float beta) {
-    __shared__ WarpRing rings[SWEEP_WARPS];
-    const int lane = threadIdx.x & 31;
-    WarpRing &ring = rings[threadIdx.x >> 5];
+__device__ __forceinline__ void sweep_strip(const DevProblem &p, WarpRing &ring, int lane, int strip, int src,
+                                            float beta) {
     const int nx = p.nx, ny = p.ny;
     const int64_t n = p.n;
     const int ncs = (nx + SW - 1) / SW;
-    const int nstrips = ncs * ((ny + H - 1) / H);
     const float2 *P = (const float2 *)p.P[src];
     float2 *Q = (float2 *)p.P[src ^ 1];
     const float *O = (const float *)p.O[src];
@@ -278,67 +271,99 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) k_sweep(DevProblem p, int sr
     const float var_prior = (float)(1.0 / p.gamma);
     const float aC_in = (float)p.aC[4];
 
-    for (int strip = blockIdx.x * SWEEP_WARPS + (threadIdx.x >> 5); strip < nstrips;
-         strip += gridDim.x * SWEEP_WARPS) {
-        const int cs = strip % ncs, rs = strip / ncs;
-        const int x0 = cs * SW;
-        const int x = x0 - 1 + lane;
-        const bool owned = lane >= 1 && lane <= SW && x < nx;
-        const bool x_inner = x > 0 && x < nx - 1;
-        const int y0 = rs * H, y1 = min(y0 + H, ny);
-        const int end_lane = min(31, nx - x0);   // lane holding column min(x0 + 30, nx - 1)
+    const int cs = strip % ncs, rs = strip / ncs;
+    const int x0 = cs * SW;
+    const int x = x0 - 1 + lane;
+    const bool owned = lane >= 1 && lane <= SW && x < nx;
+    const bool x_inner = x > 0 && x < nx - 1;
+    const int y0 = rs * H, y1 = min(y0 + H, ny);
+    const int end_lane = min(31, nx - x0);   // lane holding column min(x0 + 30, nx - 1)
 
-        // prologue: beliefs of rows y0-1 and y0; raw rows y0+1 .. y0+3 in flight
-        const RowState s_m2 = finalize(load_raw(p, P, lane, x, y0 - 2), lane);
-        const RowState s_m1 = finalize(load_raw(p, P, lane, x, y0 - 1), lane);
-        RowState s_0 = finalize(load_raw(p, P, lane, x, y0), lane);
-        RowRaw r1 = load_raw(p, P, lane, x, y0 + 1);
-        RowRaw r2 = load_raw(p, P, lane, x, y0 + 2);
-        RowRaw r3 = load_raw(p, P, lane, x, y0 + 3);
-        Belief<float> b_prev = belief_at(p, O, x, y0 - 1, s_m2, s_m1, s_0.msg.m[DIR_S]);
-        Belief<float> b_cur = belief_at(p, O, x, y0, s_m1, s_0, r1.msg.m[DIR_S]);
-        __syncwarp();   // the ring may still be read by the previous strip's last batch
-        ring.bel[y0 & (RING - 1)][lane] = b_cur;
+    // prologue: beliefs of rows y0-1 and y0; raw rows y0+1 .. y0+3 in flight
+    const RowState s_m2 = finalize(load_raw(p, P, lane, x, y0 - 2), lane);
+    const RowState s_m1 = finalize(load_raw(p, P, lane, x, y0 - 1), lane);
+    RowState s_0 = finalize(load_raw(p, P, lane, x, y0), lane);
+    RowRaw r1 = load_raw(p, P, lane, x, y0 + 1);
+    RowRaw r2 = load_raw(p, P, lane, x, y0 + 2);
+    RowRaw r3 = load_raw(p, P, lane, x, y0 + 3);
+    Belief<float> b_prev = belief_at(p, O, x, y0 - 1, s_m2, s_m1, s_0.msg.m[DIR_S]);
+    Belief<float> b_cur = belief_at(p, O, x, y0, s_m1, s_0, r1.msg.m[DIR_S]);
+    __syncwarp();   // the ring may still be read by the previous strip's last batch
+    ring.bel[y0 & (RING - 1)][lane] = b_cur;
 
-        for (int r = y0; r < y1; ++r) {
-            const RowRaw r4 = load_raw(p, P, lane, x, r + 4);   // in flight for three rows
-            const RowState s_1 = finalize(r1, lane);
-            const Belief<float> b_next = belief_at(p, O, x, r + 1, s_0, s_1, r2.msg.m[DIR_S]);
-            ring.bel[(r + 1) & (RING - 1)][lane] = b_next;
-            if (p.m > 0) {
-                const int st = __shfl_sync(FULL, s_0.o0, 1);
-                const int en = __shfl_sync(FULL, s_0.o0, end_lane);
-                if (lane == 0) ring.range[r & (RING - 1)] = make_int2(st, en > st ? en : st);
-            }
-
-            const Belief<float> b_w = shfl_up_b(b_cur);
-            const Belief<float> b_e = shfl_down_b(b_cur);
-            if (owned) {
-                const Belief<float> *const bs[5] = {&b_cur, &b_w, &b_e, &b_prev, &b_next};
-                const int64_t c = (int64_t)r * nx + x;
-                if (x_inner && r > 0 && r < ny - 1) {
-                    const float a[5] = {aC_in, -1.f, -1.f, -1.f, -1.f};
-                    cell_factor(a, var_prior, beta, s_0.msg, bs, Q, n, c);
-                } else {
-                    const int deg = grid_degree(r, x, nx, ny);
-                    const float a[5] = {(float)p.aC[deg], x > 0 ? -1.f : 0.f, x < nx - 1 ? -1.f : 0.f,
-                                        r > 0 ? -1.f : 0.f, r < ny - 1 ? -1.f : 0.f};
-                    cell_factor(a, var_prior, beta, s_0.msg, bs, Q, n, c);
-                }
-            }
-            if (p.m > 0 && ((r - y0) % OBS_BATCH == OBS_BATCH - 1 || r == y1 - 1)) {
-                __syncwarp();
-                const int rb = r - (r - y0) % OBS_BATCH;
-                obs_batch(p, ring, lane, x0, rb, r, O, OQ, beta);
-                __syncwarp();
-            }
-            b_prev = b_cur;
-            b_cur = b_next;
-            s_0 = s_1;
-            r1 = r2;
-            r2 = r3;
-            r3 = r4;
+    for (int r = y0; r < y1; ++r) {
+        const RowRaw r4 = load_raw(p, P, lane, x, r + 4);   // in flight for three rows
+        const RowState s_1 = finalize(r1, lane);
+        const Belief<float> b_next = belief_at(p, O, x, r + 1, s_0, s_1, r2.msg.m[DIR_S]);
+        ring.bel[(r + 1) & (RING - 1)][lane] = b_next;
+        if (p.m > 0) {
+            const int st = __shfl_sync(FULL, s_0.o0, 1);
+            const int en = __shfl_sync(FULL, s_0.o0, end_lane);
+            if (lane == 0) ring.range[r & (RING - 1)] = make_int2(st, en > st ? en : st);
         }
+
+        const Belief<float> b_w = shfl_up_b(b_cur);
+        const Belief<float> b_e = shfl_down_b(b_cur);
+        if (owned) {
+            const Belief<float> *const bs[5] = {&b_cur, &b_w, &b_e, &b_prev, &b_next};
+            const int64_t c = (int64_t)r * nx + x;
+            if (x_inner && r > 0 && r < ny - 1) {
+                const float a[5] = {aC_in, -1.f, -1.f, -1.f, -1.f};
+                cell_factor(a, var_prior, beta, s_0.msg, bs, Q, n, c);
+            } else {
+                const int deg = grid_degree(r, x, nx, ny);
+                const float a[5] = {(float)p.aC[deg], x > 0 ? -1.f : 0.f, x < nx - 1 ? -1.f : 0.f,
+                                    r > 0 ? -1.f : 0.f, r < ny - 1 ? -1.f : 0.f};
+                cell_factor(a, var_prior, beta, s_0.msg, bs, Q, n, c);
+            }
+        }
+        if (p.m > 0 && ((r - y0) % OBS_BATCH == OBS_BATCH - 1 || r == y1 - 1)) {
+            __syncwarp();
+            const int rb = r - (r - y0) % OBS_BATCH;
+            obs_batch(p, ring, lane, x0, rb, r, O, OQ, beta);
+            __syncwarp();
+        }
+        b_prev = b_cur;
+        b_cur = b_next;
+        s_0 = s_1;
+        r1 = r2;
+        r2 = r3;
+        r3 = r4;
+    }
+}
+
+template <int H>
+__global__ void __launch_bounds__(SWEEP_WARPS * 32) k_sweep(DevProblem p, int src, float beta) {
+    __shared__ WarpRing rings[SWEEP_WARPS];
+    const int lane = threadIdx.x & 31;
+    WarpRing &ring = rings[threadIdx.x >> 5];
+    const int nstrips = ((p.nx + SW - 1) / SW) * ((p.ny + H - 1) / H);
+    for (int strip = blockIdx.x * SWEEP_WARPS + (threadIdx.x >> 5); strip < nstrips;
+         strip += gridDim.x * SWEEP_WARPS)
+        sweep_strip<H>(p, ring, lane, strip, src, beta);
+}
+
+// Many independent problems in one persistent launch: the strips of all problems form one work
+// list (strip_start[i] = first strip of problem i, prefix over the problems), taken by the warps
+// of a grid sized to fill the GPU.  Problems whose active flag is 0 are skipped (their messages
+// stay as they are).  All problems share the ping-pong parity `src`.
+template <int H>
+__global__ void __launch_bounds__(SWEEP_WARPS * 32)
+    k_sweep_batch(const DevProblem *__restrict__ table, const int *__restrict__ strip_start,
+                  const int *__restrict__ active, int count, int src, float beta) {
+    __shared__ WarpRing rings[SWEEP_WARPS];
+    const int lane = threadIdx.x & 31;
+    WarpRing &ring = rings[threadIdx.x >> 5];
+    const int total = strip_start[count];
+    for (int g = blockIdx.x * SWEEP_WARPS + (threadIdx.x >> 5); g < total; g += gridDim.x * SWEEP_WARPS) {
+        int lo = 0, hi = count - 1;   // last problem whose first strip is <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (strip_start[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        if (!active[lo]) continue;
+        sweep_strip<H>(table[lo], ring, lane, g - strip_start[lo], src, beta);
     }
 }
 
@@ -366,6 +391,44 @@ template <int H> cudaError_t launch_h(const DevProblem &p, int src, double beta,
 }  // namespace
 
 bool sweep_shape_supported(int h) { return h == 16 || h == 32 || h == 64 || h == 128; }
+
+int sweep_strips(int nx, int ny, int h) { return ((nx + SW - 1) / SW) * ((ny + h - 1) / h); }
+
+namespace {
+template <int H>
+cudaError_t launch_batch_h(const DevProblem *table, const int *strip_start, const int *active, int count,
+                           int total_strips, int src, double beta, cudaStream_t st) {
+    static int grid_cache = 0, configured_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured_dev != dev) {
+        int nsm = 0, per_sm = 0;
+        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_batch<H>, SWEEP_WARPS * 32, 0);
+        if (e != cudaSuccess) return e;
+        grid_cache = nsm * (per_sm > 0 ? per_sm : 1);
+        configured_dev = dev;
+    }
+    const int blocks = (total_strips + SWEEP_WARPS - 1) / SWEEP_WARPS;
+    const int grid = blocks < grid_cache ? blocks : grid_cache;
+    if (grid < 1) return cudaSuccess;
+    k_sweep_batch<H><<<grid, SWEEP_WARPS * 32, 0, st>>>(table, strip_start, active, count, src, (float)beta);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_sweep_batch(const DevProblem *table, const int *strip_start, const int *active, int count,
+                               int total_strips, int src, double beta, int h, cudaStream_t st) {
+    switch (h) {
+        case 16: return launch_batch_h<16>(table, strip_start, active, count, total_strips, src, beta, st);
+        case 32: return launch_batch_h<32>(table, strip_start, active, count, total_strips, src, beta, st);
+        case 64: return launch_batch_h<64>(table, strip_start, active, count, total_strips, src, beta, st);
+        case 128: return launch_batch_h<128>(table, strip_start, active, count, total_strips, src, beta, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_sweep_iteration(const DevProblem &p, int src, double beta, int h, cudaStream_t st) {
     if (p.prec != 0) return cudaErrorInvalidValue;

@@ -112,7 +112,7 @@ def test_split_and_fused_bit_identical(prec, shape):
                                 sigma=(0.02, 0.1))
     variants = [(2, (0, 0)), (1, (32, 8)), (1, (64, 16)), (1, (128, 8)), (1, (32, 32))]
     if prec == "fp32" and nx % 4 == 0:
-        variants += [(3, (64, 16)), (3, (32, 16)), (3, (64, 8)), (3, (32, 32))]
+        variants += [(3, (30, 14)), (3, (30, 22)), (3, (30, 30))]
     if prec == "fp32":
         variants += [(4, (30, 16)), (4, (30, 32)), (4, (30, 64)), (4, (30, 128))]
     bufs = []
