@@ -66,7 +66,8 @@ extern "C" {
 #define GABP_INIT_PAPER 1    /* Lambda = 1e-8, eta = 0 (Alg. 1 / Alg. 2 initialisation) */
 
 /* iteration kernel (gabp_options.kernel) */
-#define GABP_KERNEL_AUTO 0   /* GABP_KERNEL_SWEEP for FP32 messages, GABP_KERNEL_FUSED for FP64 */
+#define GABP_KERNEL_AUTO 0   /* FP32: GABP_KERNEL_TMA if nx is a multiple of 4, else
+                                GABP_KERNEL_SWEEP; FP64: GABP_KERNEL_FUSED */
 #define GABP_KERNEL_FUSED 1  /* one fused kernel per iteration (beliefs + all factors) */
 #define GABP_KERNEL_SPLIT 2  /* three kernels per iteration: beliefs, prior factors, obs factors */
 #define GABP_KERNEL_TMA 3    /* the fused kernel as persistent blocks fed by TMA tensor loads;
@@ -267,6 +268,50 @@ int gabp_batch_strip_height(const gabp_batch *b);
 
 const char *gabp_batch_last_error(const gabp_batch *b);
 void gabp_batch_destroy(gabp_batch *b);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned warm start.  A small convolutional encoder-decoder (4 levels, 32 -> 256 channels,
+ * BF16 weights and activations, FP32 accumulation) maps the gridded observations to initial
+ * beliefs (mean, log precision); gabp_wsnet_warm_start() seeds a context's messages with them
+ * (as gabp_warm_start).  The paper has no learned component; its own accelerator of
+ * convergence is the multigrid warm start (Sec. 3.2 "Multigrid", App. B "Upscale Messages").
+ * Network input per node (grid padded to multiples of 8): the mean of y / scale over the
+ * observations whose nearest node it is, that mask, log(kappa) + 3 (13 zero channels follow);
+ * scale = standard deviation of the problem's observed values.  Output: mean / scale, log
+ * precision.
+ * --------------------------------------------------------------------------------------- */
+typedef struct gabp_wsnet gabp_wsnet;
+
+/* Create a network with seeded He-normal weights on `device` (-1 = current). */
+int gabp_wsnet_create(gabp_wsnet **out, uint64_t seed, int device);
+int64_t gabp_wsnet_param_count(const gabp_wsnet *net);
+/* FP32 parameter vector (host or device, gabp_wsnet_param_count floats). */
+int gabp_wsnet_get_params(gabp_wsnet *net, float *params);
+int gabp_wsnet_set_params(gabp_wsnet *net, const float *params);
+/* Forward pass: x [B][H][W][16] BF16, out [B][H][W][2] FP32 (host or device); H, W multiples of 8. */
+int gabp_wsnet_forward(gabp_wsnet *net, const void *x, int B, int H, int W, float *out);
+/* Loss (mean over pixels of the squared errors of both outputs) and its gradient w.r.t. every
+ * parameter (FP32, host or device; NULL = do not copy) for B samples given as device pointers
+ * to [H][W][16] BF16 inputs and [H][W][2] FP32 targets. */
+int gabp_wsnet_gradients(gabp_wsnet *net, const void *const *xs, const float *const *ts, int B, int H, int W,
+                         float *grads, float *loss);
+/* One Adam step (beta 0.9 / 0.999) on B samples; loss before the step into *loss. */
+int gabp_wsnet_train_step(gabp_wsnet *net, const void *const *xs, const float *const *ts, int B, int H, int W,
+                          float lr, float *loss);
+const char *gabp_wsnet_last_error(const gabp_wsnet *net);
+const char *gabp_wsnet_create_error(void);
+void gabp_wsnet_destroy(gabp_wsnet *net);
+
+/* Padded network grid of a context (H, W multiples of 8) and its input scale. */
+int gabp_wsnet_input_shape(const gabp_ctx *ctx, int *H, int *W, double *scale);
+/* A training sample of a context: network input (DEVICE, [H][W][16] BF16, may be NULL) and target
+ * from its current beliefs (DEVICE, [H][W][2] FP32: mean / scale, log precision; may be NULL). */
+int gabp_wsnet_sample(gabp_ctx *ctx, void *x_out, float *t_out);
+int gabp_batch_input_shape(const gabp_batch *b, int index, int *H, int *W, double *scale);
+int gabp_batch_wsnet_sample(gabp_batch *b, int index, void *x_out, float *t_out);
+/* Scatter the observations, run the network and seed the messages from its prediction
+ * (all on the GPU, on the context's stream). */
+int gabp_wsnet_warm_start(gabp_ctx *ctx, gabp_wsnet *net);
 
 /*
  * Allocation-free residual.  The paper has no counterpart: this entry point exists for callers

@@ -25,8 +25,11 @@ __all__ = [
     "gabp_warm_start", "gabp_reset", "gabp_message_bytes", "gabp_get_messages",
     "gabp_set_messages", "gabp_get_stats", "gabp_destroy", "gabp_residual_noalloc",
     "gabp_batch_create", "gabp_batch_iterate", "gabp_batch_residuals", "gabp_batch_marginals",
-    "gabp_batch_get_stats", "gabp_batch_strip_height", "gabp_batch_destroy", "Solver", "Batch",
-    "GabpError",
+    "gabp_batch_get_stats", "gabp_batch_strip_height", "gabp_batch_destroy",
+    "gabp_wsnet_create", "gabp_wsnet_param_count", "gabp_wsnet_get_params", "gabp_wsnet_set_params",
+    "gabp_wsnet_forward", "gabp_wsnet_gradients", "gabp_wsnet_train_step", "gabp_wsnet_destroy",
+    "gabp_wsnet_input_shape", "gabp_wsnet_sample", "gabp_batch_input_shape", "gabp_batch_wsnet_sample",
+    "gabp_wsnet_warm_start", "Solver", "Batch", "WarmStartNet", "GabpError",
 ]
 
 
@@ -249,6 +252,118 @@ class Batch:
         self.close()
 
 
+def _wcheck(rc: int, net):
+    if rc != GABP_OK:
+        L = _lib.load()
+        msg = L.gabp_wsnet_last_error(net) if net else L.gabp_wsnet_create_error()
+        raise GabpError(rc, (msg or b"").decode(errors="replace"))
+
+
+def gabp_wsnet_create(seed: int = 0, device: int = -1) -> int:
+    h = ctypes.c_void_p()
+    _wcheck(_lib.load().gabp_wsnet_create(ctypes.byref(h), int(seed), int(device)), None)
+    return h.value
+
+
+def gabp_wsnet_param_count(net: int) -> int:
+    return int(_lib.load().gabp_wsnet_param_count(net))
+
+
+def gabp_wsnet_get_params(net: int, out) -> None:
+    _wcheck(_lib.load().gabp_wsnet_get_params(net, _ptr(out)), net)
+
+
+def gabp_wsnet_set_params(net: int, params) -> None:
+    _wcheck(_lib.load().gabp_wsnet_set_params(net, _ptr(params)), net)
+
+
+def gabp_wsnet_forward(net: int, x, B: int, H: int, W: int, out) -> None:
+    _wcheck(_lib.load().gabp_wsnet_forward(net, _ptr(x), B, H, W, _ptr(out)), net)
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, t in enumerate(items):
+        arr[i] = _ptr(t)
+    return arr
+
+
+def gabp_wsnet_gradients(net: int, xs, ts, H: int, W: int, grads=None) -> float:
+    loss = ctypes.c_float()
+    _wcheck(_lib.load().gabp_wsnet_gradients(net, _ptr_array(xs), _ptr_array(ts), len(xs), H, W, _ptr(grads),
+                                             ctypes.byref(loss)), net)
+    return loss.value
+
+
+def gabp_wsnet_train_step(net: int, xs, ts, H: int, W: int, lr: float) -> float:
+    loss = ctypes.c_float()
+    _wcheck(_lib.load().gabp_wsnet_train_step(net, _ptr_array(xs), _ptr_array(ts), len(xs), H, W, float(lr),
+                                              ctypes.byref(loss)), net)
+    return loss.value
+
+
+def gabp_wsnet_destroy(net: int) -> None:
+    if net:
+        _lib.load().gabp_wsnet_destroy(net)
+
+
+def gabp_wsnet_input_shape(ctx: int):
+    H, W, sc = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(_lib.load().gabp_wsnet_input_shape(ctx, ctypes.byref(H), ctypes.byref(W), ctypes.byref(sc)), ctx)
+    return H.value, W.value, sc.value
+
+
+def gabp_wsnet_sample(ctx: int, x_out=None, t_out=None) -> None:
+    _check(_lib.load().gabp_wsnet_sample(ctx, _ptr(x_out), _ptr(t_out)), ctx)
+
+
+def gabp_batch_input_shape(b: int, index: int):
+    H, W, sc = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _bcheck(_lib.load().gabp_batch_input_shape(b, int(index), ctypes.byref(H), ctypes.byref(W), ctypes.byref(sc)), b)
+    return H.value, W.value, sc.value
+
+
+def gabp_batch_wsnet_sample(b: int, index: int, x_out=None, t_out=None) -> None:
+    _bcheck(_lib.load().gabp_batch_wsnet_sample(b, int(index), _ptr(x_out), _ptr(t_out)), b)
+
+
+def gabp_wsnet_warm_start(ctx: int, net: int) -> None:
+    _check(_lib.load().gabp_wsnet_warm_start(ctx, net), ctx)
+
+
+class WarmStartNet:
+    """Owns a warm-start network (weights on the GPU)."""
+
+    def __init__(self, seed: int = 0, device: int = -1):
+        self.handle = gabp_wsnet_create(seed, device)
+        self.nparam = gabp_wsnet_param_count(self.handle)
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.nparam, np.float32)
+        gabp_wsnet_get_params(self.handle, out)
+        return out
+
+    def set_params(self, params) -> None:
+        gabp_wsnet_set_params(self.handle, np.ascontiguousarray(params, np.float32))
+
+    def save(self, path: str) -> None:
+        np.save(path, self.params())
+
+    def load(self, path: str) -> None:
+        self.set_params(np.load(path))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gabp_wsnet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Solver:
     """Owns one context.  ``Solver(problem, precision='fp32')`` with a ``gabp_synth.Problem``-like
     object (fields nx, ny, kappa, obs_x, obs_y, y, noise_var)."""
@@ -279,6 +394,9 @@ class Solver:
         var = out_var if out_var is not None else (np.empty(self.n) if want_var else None)
         gabp_marginals(self.ctx, mean, var)
         return mean, var
+
+    def learned_warm_start(self, net: "WarmStartNet") -> None:
+        gabp_wsnet_warm_start(self.ctx, net.handle)
 
     def warm_start(self, mu0, lam0) -> None:
         gabp_warm_start(self.ctx, np.ascontiguousarray(mu0, np.float64).reshape(-1)

@@ -126,6 +126,40 @@ def load():
     L.gabp_batch_last_error.restype = ctypes.c_char_p
     L.gabp_batch_destroy.argtypes = [_vp]
     L.gabp_batch_destroy.restype = None
+    _fp = ctypes.POINTER(ctypes.c_float)
+    L.gabp_wsnet_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_uint64, ctypes.c_int]
+    L.gabp_wsnet_create.restype = ctypes.c_int
+    L.gabp_wsnet_param_count.argtypes = [_vp]
+    L.gabp_wsnet_param_count.restype = ctypes.c_int64
+    L.gabp_wsnet_get_params.argtypes = [_vp, _vp]
+    L.gabp_wsnet_get_params.restype = ctypes.c_int
+    L.gabp_wsnet_set_params.argtypes = [_vp, _vp]
+    L.gabp_wsnet_set_params.restype = ctypes.c_int
+    L.gabp_wsnet_forward.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]
+    L.gabp_wsnet_forward.restype = ctypes.c_int
+    L.gabp_wsnet_gradients.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, _vp, _fp]
+    L.gabp_wsnet_gradients.restype = ctypes.c_int
+    L.gabp_wsnet_train_step.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_float, _fp]
+    L.gabp_wsnet_train_step.restype = ctypes.c_int
+    L.gabp_wsnet_last_error.argtypes = [_vp]
+    L.gabp_wsnet_last_error.restype = ctypes.c_char_p
+    L.gabp_wsnet_create_error.argtypes = []
+    L.gabp_wsnet_create_error.restype = ctypes.c_char_p
+    L.gabp_wsnet_destroy.argtypes = [_vp]
+    L.gabp_wsnet_destroy.restype = None
+    L.gabp_wsnet_input_shape.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]
+    L.gabp_wsnet_input_shape.restype = ctypes.c_int
+    L.gabp_wsnet_sample.argtypes = [_vp, _vp, _vp]
+    L.gabp_wsnet_sample.restype = ctypes.c_int
+    L.gabp_batch_input_shape.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), _dp]
+    L.gabp_batch_input_shape.restype = ctypes.c_int
+    L.gabp_batch_wsnet_sample.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+    L.gabp_batch_wsnet_sample.restype = ctypes.c_int
+    L.gabp_wsnet_warm_start.argtypes = [_vp, _vp]
+    L.gabp_wsnet_warm_start.restype = ctypes.c_int
     L.gabp_residual_noalloc.argtypes = [gabp_grid, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                         _vp, _vp, _vp, _vp, _dp, _vp]
     L.gabp_residual_noalloc.restype = ctypes.c_int

@@ -38,6 +38,9 @@ struct gabp_ctx {
     int g_len = 0;
     double g_beta = -1.0;
     int g_kernel = -1;
+    double kappa = 0.0;
+    double yscale = 1.0;          // spread of the observed values (network input scale)
+    void *ws_x = nullptr;         // network input buffer (allocated on first use)
 };
 
 namespace {
@@ -193,6 +196,8 @@ int init_messages(gabp_ctx *c) {
 
 void free_all(gabp_ctx *c) {
     drop_graph(c);
+    if (c->ws_x) cudaFree(c->ws_x);
+    c->ws_x = nullptr;
     for (void *q : c->allocs) cudaFree(q);
     c->allocs.clear();
     if (c->hscal) cudaFreeHost(c->hscal);
@@ -225,8 +230,10 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     if (!(o.tol > 0.0) || o.check_every < 1 || o.max_iters < 1) return fail(c, GABP_ERR_ARG, "bad tol/check_every/max_iters");
     {
         // the kernel AUTO resolves to: the sweep for FP32, the plain fused kernel for FP64
-        const int k = o.kernel != GABP_KERNEL_AUTO ? o.kernel
-                                                   : (o.precision == GABP_FP32 ? GABP_KERNEL_SWEEP : GABP_KERNEL_FUSED);
+        const int k = o.kernel != GABP_KERNEL_AUTO
+                          ? o.kernel
+                          : (o.precision == GABP_FP32 ? (nx % 4 == 0 && nx >= 4 ? GABP_KERNEL_TMA : GABP_KERNEL_SWEEP)
+                                                      : GABP_KERNEL_FUSED);
         const bool tiled = o.tile_x || o.tile_y;
         if (tiled && (k == GABP_KERNEL_FUSED || k == GABP_KERNEL_SPLIT) && !gabp::fused_shape_supported(o.tile_x, o.tile_y))
             return fail(c, GABP_ERR_ARG, "unsupported tile shape");
@@ -266,6 +273,15 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
         svar[(size_t)dst] = noise_var[k];
     }
 
+    c->kappa = kappa;
+    if (m >= 2) {
+        double mean = 0.0, sq = 0.0;
+        for (int64_t k = 0; k < m; ++k) mean += y[k];
+        mean /= (double)m;
+        for (int64_t k = 0; k < m; ++k) sq += (y[k] - mean) * (y[k] - mean);
+        const double sd = std::sqrt(sq / (double)(m - 1));
+        c->yscale = sd > 0.0 ? sd : 1.0;
+    }
     DevProblem &p = c->p;
     p.nx = nx;
     p.ny = ny;
@@ -339,13 +355,13 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     if (o.kernel == GABP_KERNEL_SWEEP && p.prec != 0)
         return fail(c, GABP_ERR_ARG, "the sweep kernel needs FP32 messages");
     if (o.kernel == GABP_KERNEL_SPLIT) c->kernel = GABP_KERNEL_SPLIT;
-    else if (o.kernel == GABP_KERNEL_TMA) c->kernel = GABP_KERNEL_TMA;
+    else if (o.kernel == GABP_KERNEL_TMA || (o.kernel == GABP_KERNEL_AUTO && tma_ok)) c->kernel = GABP_KERNEL_TMA;
     else if (o.kernel == GABP_KERNEL_SWEEP || (o.kernel == GABP_KERNEL_AUTO && p.prec == 0)) c->kernel = GABP_KERNEL_SWEEP;
     else c->kernel = GABP_KERNEL_FUSED;
     if (c->kernel == GABP_KERNEL_SWEEP) {
         c->shape = o.tile_y ? gabp::FusedShape{30, o.tile_y} : gabp::FusedShape{30, 64};
     } else if (c->kernel == GABP_KERNEL_TMA) {
-        c->shape = o.tile_x ? gabp::FusedShape{o.tile_x, o.tile_y} : gabp::FusedShape{30, 22};
+        c->shape = o.tile_x ? gabp::FusedShape{o.tile_x, o.tile_y} : gabp::FusedShape{30, 14};
         CK(gabp::make_tma_maps(p, c->shape.tx, c->shape.ty, c->maps), "tensor map encode");
     } else if (o.tile_x) {
         c->shape = {o.tile_x, o.tile_y};
@@ -1035,6 +1051,87 @@ void gabp_batch_destroy(gabp_batch *b) {
         batch_free(b);
     }
     delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Learned warm start glue
+// ---------------------------------------------------------------------------------------
+
+namespace {
+
+inline int pad8(int v) { return (v + 7) / 8 * 8; }
+
+int ws_ensure_input(gabp_ctx *c) {
+    if (c->ws_x) return GABP_OK;
+    const size_t bytes = sizeof(uint16_t) * 16 * (size_t)pad8(c->p.nx) * pad8(c->p.ny);
+    CK(cudaMalloc(&c->ws_x, bytes), "alloc network input");
+    return GABP_OK;
+}
+
+int ws_sample(gabp_ctx *c, void *x_out, float *t_out) {
+    const int Hp = pad8(c->p.ny), Wp = pad8(c->p.nx);
+    if (x_out) CK(gabp::launch_ws_input(c->p, c->yscale, c->kappa, Hp, Wp, x_out, c->stream), "network input");
+    if (t_out) CK(gabp::launch_ws_target(c->p, c->cur, c->yscale, Hp, Wp, t_out, c->stream), "network target");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    return GABP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gabp_wsnet_input_shape(const gabp_ctx *c, int *H, int *W, double *scale) {
+    if (!c) return GABP_ERR_ARG;
+    if (H) *H = pad8(c->p.ny);
+    if (W) *W = pad8(c->p.nx);
+    if (scale) *scale = c->yscale;
+    return GABP_OK;
+}
+
+int gabp_wsnet_sample(gabp_ctx *c, void *x_out, float *t_out) {
+    if (!c) return GABP_ERR_ARG;
+    DeviceGuard g(c->dev);
+    return ws_sample(c, x_out, t_out);
+}
+
+int gabp_batch_wsnet_sample(gabp_batch *b, int index, void *x_out, float *t_out) {
+    if (!b) return GABP_ERR_ARG;
+    if (index < 0 || index >= (int)b->inst.size()) return bfail(b, GABP_ERR_ARG, "index out of range");
+    DeviceGuard g(b->dev);
+    gabp_ctx *c = b->inst[index];
+    c->cur = b->cur;
+    const int rc = ws_sample(c, x_out, t_out);
+    if (rc) return bfail(b, rc, c->err);
+    return GABP_OK;
+}
+
+int gabp_batch_input_shape(const gabp_batch *b, int index, int *H, int *W, double *scale) {
+    if (!b || index < 0 || index >= (int)b->inst.size()) return GABP_ERR_ARG;
+    return gabp_wsnet_input_shape(b->inst[index], H, W, scale);
+}
+
+int gabp_wsnet_warm_start(gabp_ctx *c, gabp_wsnet *net) {
+    if (!c || !net) return c ? fail(c, GABP_ERR_ARG, "net must not be NULL") : GABP_ERR_ARG;
+    if (gabp::wsnet_device(net) != c->dev) return fail(c, GABP_ERR_ARG, "network and context on different devices");
+    DeviceGuard g(c->dev);
+    int rc = ws_ensure_input(c);
+    if (rc) return rc;
+    const int Hp = pad8(c->p.ny), Wp = pad8(c->p.nx);
+    CK(gabp::launch_ws_input(c->p, c->yscale, c->kappa, Hp, Wp, c->ws_x, c->stream), "network input");
+    float *out = nullptr;
+    std::string err;
+    rc = gabp::wsnet_forward_device(net, c->ws_x, 1, Hp, Wp, &out, c->stream, err);
+    if (rc) return fail(c, rc, "network forward: " + err);
+    const int64_t n = c->p.n;
+    CK(gabp::launch_ws_decode(c->p, c->yscale, Wp, out, c->stage, c->stage + n, c->stream), "decode");
+    CK(gabp::launch_init_warm(c->p, 0, c->stage, c->stage + n, c->stream), "warm init kernels");
+    CK(cudaStreamSynchronize(c->stream), "warm start sync");
+    c->cur = 0;
+    c->iters = 0;
+    c->last_res = NAN;
+    return GABP_OK;
 }
 
 }  // extern "C"

@@ -3,10 +3,10 @@
 // Work unit: a tile of 30 columns x TY rows of cells.  The nodes its factors touch form a
 // 32 x (TY+2) window (the tile plus a one-cell halo), so one warp covers one window row with
 // every lane busy.  Per tile the block
-//   A. computes the compensated beliefs of the window: warp w takes window rows w, w+8, ...,
+//   A. computes the compensated beliefs of the window: one warp per window row (TY + 2 warps),
 //      lane = column; prior messages come from the staged planes, observation messages from
 //      global memory through the staged observation index;
-//   B. updates the tile's cell factors (warp w takes tile rows w, w+8, ..., lanes 0..29) and
+//   B. updates the tile's cell factors (warp w takes tile row w, lanes 0..29) and
 //      the observation factors based in the tile (one per thread), writing the damped messages
 //      to the other ping-pong buffer.
 // Two barriers per tile.  Staging: each block is persistent and walks the tiles blockIdx.x,
@@ -34,8 +34,6 @@ namespace gabp {
 namespace {
 
 constexpr int TTX = 30;   // tile width in cells: window width 32
-constexpr int TNT = 256;  // threads per block (8 warps)
-constexpr int TW = TNT / 32;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -86,7 +84,9 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 
 __host__ __device__ constexpr size_t a128(size_t x) { return (x + 127) & ~size_t(127); }
 
+// One warp per belief-window row: TY + 2 warps per block.
 template <int TY, int S> struct TileLayout {
+    static constexpr int TW = TY + 2, TNT = 32 * TW;   // warps, threads
     static constexpr int RX = TTX + 4, RY = TY + 4;   // staged planes (cells), origin (x0-2, y0-2)
     static constexpr int BX = 32, BY = TY + 2;        // belief window, origin (x0-1, y0-1)
     static constexpr int OXW = 40, OY = TY + 3;       // observation index window, origin (xs, y0-2)
@@ -102,11 +102,12 @@ template <int TY, int S> struct TileLayout {
 };
 
 template <int TY, int S>
-__global__ void __launch_bounds__(TNT) k_fused_tma(const __grid_constant__ CUtensorMap mplanes,
+__global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __grid_constant__ CUtensorMap mplanes,
                                                    const __grid_constant__ CUtensorMap moptr, DevProblem p,
                                                    int src, float beta) {
     using LY = TileLayout<TY, S>;
     constexpr int RX = LY::RX, RY = LY::RY, BX = LY::BX, BY = LY::BY, OXW = LY::OXW;
+    constexpr int TW = LY::TW, TNT = LY::TNT;
     extern __shared__ __align__(128) unsigned char smem[];
     Belief<float> *sb = reinterpret_cast<Belief<float> *>(smem + LY::bel_off);   // [BY][32]
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + LY::bar_off);
@@ -351,7 +352,7 @@ cudaError_t launch_cfg(const DevProblem &p, const TmaMaps &maps, int src, double
         int nsm = 0, per_sm = 0;
         e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tma<TY, S>, TNT, LY::bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tma<TY, S>, LY::TNT, LY::bytes);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         grid_cache = nsm * per_sm;
@@ -359,7 +360,7 @@ cudaError_t launch_cfg(const DevProblem &p, const TmaMaps &maps, int src, double
     }
     const int ntiles = ((p.nx + TTX - 1) / TTX) * ((p.ny + TY - 1) / TY);
     const int grid = ntiles < grid_cache ? ntiles : grid_cache;
-    k_fused_tma<TY, S><<<grid, TNT, LY::bytes, st>>>(maps.planes[src], maps.optr, p, src, (float)beta);
+    k_fused_tma<TY, S><<<grid, LY::TNT, LY::bytes, st>>>(maps.planes[src], maps.optr, p, src, (float)beta);
     return cudaGetLastError();
 }
 

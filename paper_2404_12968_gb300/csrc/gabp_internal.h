@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace gabp {
 
 // Device-resident description of one problem instance.  All pointers are device pointers.
@@ -48,6 +50,12 @@ cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st);
 cudaError_t launch_marginals(const DevProblem &p, int src, double *mean, double *var,
                              cudaStream_t st);
 
+// ---- learned warm start (gabp_split.cu kernels, network in gabp_wsnet.cu) ----
+cudaError_t launch_ws_input(const DevProblem &p, double scale, double kappa, int Hp, int Wp, void *x, cudaStream_t st);
+cudaError_t launch_ws_target(const DevProblem &p, int src, double scale, int Hp, int Wp, float *t, cudaStream_t st);
+cudaError_t launch_ws_decode(const DevProblem &p, double scale, int Wp, const float *out, double *mu0, double *lam0,
+                             cudaStream_t st);
+
 // ---- fused path (gabp_fused.cu) ----
 struct FusedShape {
     int tx, ty;   // tile in cells
@@ -79,4 +87,11 @@ size_t tma_smem_bytes(int tx, int ty);
 cudaError_t launch_tma_iteration(const DevProblem &p, const TmaMaps &maps, int src, double beta,
                                  cudaStream_t st);
 
+}  // namespace gabp
+
+struct gabp_wsnet;
+namespace gabp {
+int wsnet_forward_device(gabp_wsnet *net, const void *x, int B, int H, int W, float **out, cudaStream_t st,
+                         std::string &err);
+int wsnet_device(const gabp_wsnet *net);
 }  // namespace gabp

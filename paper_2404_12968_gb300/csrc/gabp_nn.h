@@ -1,0 +1,55 @@
+// Internal interface of the warm-start network kernels (gabp_nn_kernels.cu).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gabp {
+namespace nn {
+
+// out = act(conv(in, w) + bias (+ skip)); NHWC BF16, weights [Cout][T][Cin], T = 9 or 1.
+// Cout a multiple of 32, Cin a multiple of 16.
+struct ConvArgs {
+    const __nv_bfloat16 *in;
+    const __nv_bfloat16 *w;
+    const float *bias;          // may be NULL
+    const __nv_bfloat16 *skip;  // may be NULL; [B][H][W][Cout]
+    __nv_bfloat16 *out;
+    int B, H, W, Cin, Cout, T, relu;
+};
+
+// dw[co][t][ci] = sum_p g[p][co] in[p + d_t][ci]; `part` holds chunk partials
+// (wgrad_chunks(args) * Cout * T * Cin floats).
+struct WgradArgs {
+    const __nv_bfloat16 *g;     // [B][H][W][Cout]
+    const __nv_bfloat16 *in;    // [B][H][W][Cin]
+    float *part;
+    int B, H, W, Cin, Cout, T;
+    int64_t chunk_pixels;       // set by conv_wgrad
+};
+
+cudaError_t conv(const ConvArgs &a, cudaStream_t st);
+int64_t wgrad_chunks(const WgradArgs &a);
+cudaError_t conv_wgrad(WgradArgs a, float *dw, cudaStream_t st);
+cudaError_t bias_grad(const __nv_bfloat16 *g, int64_t P, int C, float *db, cudaStream_t st);
+cudaError_t flip_transpose(const __nv_bfloat16 *w, int Cout, int T, int Cin, __nv_bfloat16 *wt, cudaStream_t st);
+cudaError_t relu_bwd(const __nv_bfloat16 *y, const __nv_bfloat16 *dy, __nv_bfloat16 *dx, int64_t n, cudaStream_t st);
+cudaError_t pool(const __nv_bfloat16 *x, int B, int H, int W, int C, __nv_bfloat16 *y, cudaStream_t st);
+cudaError_t pool_bwd_add(const __nv_bfloat16 *dy, int B, int H, int W, int C, __nv_bfloat16 *dx, cudaStream_t st);
+cudaError_t up_add(const __nv_bfloat16 *r, const __nv_bfloat16 *s, int B, int H, int W, int C, __nv_bfloat16 *y,
+                   cudaStream_t st);
+cudaError_t down_sum(const __nv_bfloat16 *dy, int B, int H, int W, int C, __nv_bfloat16 *dr, cudaStream_t st);
+cudaError_t add_into(const __nv_bfloat16 *a, __nv_bfloat16 *b, int64_t n, cudaStream_t st);
+cudaError_t head(const __nv_bfloat16 *x, int64_t P, int C, const float *w, const float *b, float *out,
+                 cudaStream_t st);
+cudaError_t loss(const float *out, const float *target, int64_t P, float *dout, float *part, int parts,
+                 cudaStream_t st);
+// dx (BF16) and the head's weight/bias gradients dwb[2C + 2] (part: ceil(P/1024) * (2C+2) floats)
+cudaError_t head_bwd(const float *dout, const __nv_bfloat16 *x, int64_t P, int C, const float *w,
+                     __nv_bfloat16 *dx, float *part, float *dwb, cudaStream_t st);
+cudaError_t adam(float *w, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2, float eps,
+                 int step, __nv_bfloat16 *w16, cudaStream_t st);
+cudaError_t to_bf16(const float *x, __nv_bfloat16 *y, int64_t n, cudaStream_t st);
+
+}  // namespace nn
+}  // namespace gabp

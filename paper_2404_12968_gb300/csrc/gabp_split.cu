@@ -2,6 +2,10 @@
 // auxiliary kernels: message initialisation, FP64 observation precompute, FP64 residual and
 // marginals.  The split iteration is the plain form of one synchronous iteration; the fused
 // kernel (gabp_fused.cu) computes the same messages in one pass.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
 #include "gabp_device.cuh"
 #include "gabp_internal.h"
 
@@ -351,6 +355,72 @@ template <typename T> __global__ void k_marg(DevProblem p, double *mean, double 
     if (var) var[v] = 1.0 / L;
 }
 
+// ---- learned warm start: network inputs, training targets, decoded initial beliefs ----
+// Grid padded to Hp x Wp (multiples of 8); node (i, j) -> pixel (i, j).
+
+// x[i][j][0..15]: mean of y / scale over the observations whose nearest node is (i, j), the
+// mask of such nodes, log(kappa) + 3, zeros.  The nearest node of an observation is the corner
+// of its base cell that carries the largest bilinear weight (ties to the lower index), found from
+// fu = w1 + w3 and fv = w2 + w3.
+__global__ void k_ws_input(DevProblem p, double inv_scale, float kfeat, int Hp, int Wp, __nv_bfloat16 *x) {
+    const int64_t q = gtid();
+    if (q >= (int64_t)Hp * Wp) return;
+    const int i = (int)(q / Wp), j = (int)(q - (int64_t)i * Wp);
+    double sum = 0.0;
+    int cnt = 0;
+    if (i < p.ny && j < p.nx && p.m > 0) {
+        const int nx = p.nx;
+        const int64_t v = (int64_t)i * nx + j;
+        const int64_t bases[4] = {v, v - 1, v - nx, v - nx - 1};
+        const bool ok[4] = {true, j > 0, i > 0, i > 0 && j > 0};
+        for (int c = 0; c < 4; ++c) {
+            if (!ok[c]) continue;
+            for (int k = p.optr[bases[c]]; k < p.optr[bases[c] + 1]; ++k) {
+                const double *w = p.ow64 + 4 * (int64_t)k;
+                const int near = (w[1] + w[3] >= 0.5 ? 1 : 0) + (w[2] + w[3] >= 0.5 ? 2 : 0);
+                if (near == c) {
+                    sum += p.oys64[2 * (int64_t)k];
+                    ++cnt;
+                }
+            }
+        }
+    }
+    __nv_bfloat16 *o = x + q * 16;
+    o[0] = __float2bfloat16(cnt ? (float)(sum / cnt * inv_scale) : 0.f);
+    o[1] = __float2bfloat16(cnt ? 1.f : 0.f);
+    o[2] = __float2bfloat16(kfeat);
+#pragma unroll
+    for (int c = 3; c < 16; ++c) o[c] = __float2bfloat16(0.f);
+}
+
+// t[i][j] = (mu / scale, log Lambda) of the current beliefs (after k_beliefs); zeros in the pad
+template <typename T> __global__ void k_ws_target(DevProblem p, double inv_scale, int Hp, int Wp, float *t) {
+    const int64_t q = gtid();
+    if (q >= (int64_t)Hp * Wp) return;
+    const int i = (int)(q / Wp), j = (int)(q - (int64_t)i * Wp);
+    float a = 0.f, b = 0.f;
+    if (i < p.ny && j < p.nx) {
+        const BeliefStore<T> s = ((const BeliefStore<T> *)p.belief)[(int64_t)i * p.nx + j];
+        const double L = (double)s.lhi + (double)s.llo;
+        a = (float)(((double)s.ehi + (double)s.elo) / L * inv_scale);
+        b = (float)log(L);
+    }
+    t[2 * q] = a;
+    t[2 * q + 1] = b;
+}
+
+// initial beliefs from the network output: mu0 = scale * out0, lam0 = exp(out1) clamped
+__global__ void k_ws_decode(DevProblem p, double scale, int Wp, const float *out, double *mu0, double *lam0) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+    const int64_t q = (int64_t)i * Wp + j;
+    double lg = (double)out[2 * q + 1];
+    lg = lg < -10.0 ? -10.0 : (lg > 15.0 ? 15.0 : lg);
+    mu0[v] = scale * (double)out[2 * q];
+    lam0[v] = exp(lg);
+}
+
 template <typename T> cudaError_t split_iteration(const DevProblem &p, int src, double beta, cudaStream_t st) {
     k_beliefs<T><<<nblocks(p.n), TPB, 0, st>>>(p, src);
     k_prior<T><<<nblocks(p.n), TPB, 0, st>>>(p, src, (T)beta);
@@ -416,6 +486,27 @@ cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st) {
     k_Lmu<<<nblocks(p.n), TPB, 0, st>>>(p);
     k_res<<<RES_BLOCKS, TPB, 0, st>>>(p);
     k_final_sum<<<1, TPB, 0, st>>>(p.part, RES_BLOCKS, p.scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ws_input(const DevProblem &p, double scale, double kappa, int Hp, int Wp, void *x,
+                            cudaStream_t st) {
+    k_ws_input<<<nblocks((int64_t)Hp * Wp), TPB, 0, st>>>(p, 1.0 / scale, (float)(std::log(kappa) + 3.0), Hp, Wp,
+                                                          (__nv_bfloat16 *)x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ws_target(const DevProblem &p, int src, double scale, int Hp, int Wp, float *t, cudaStream_t st) {
+    cudaError_t e = launch_beliefs(p, src, st);
+    if (e != cudaSuccess) return e;
+    if (p.prec) k_ws_target<double><<<nblocks((int64_t)Hp * Wp), TPB, 0, st>>>(p, 1.0 / scale, Hp, Wp, t);
+    else k_ws_target<float><<<nblocks((int64_t)Hp * Wp), TPB, 0, st>>>(p, 1.0 / scale, Hp, Wp, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ws_decode(const DevProblem &p, double scale, int Wp, const float *out, double *mu0, double *lam0,
+                             cudaStream_t st) {
+    k_ws_decode<<<nblocks(p.n), TPB, 0, st>>>(p, scale, Wp, out, mu0, lam0);
     return cudaGetLastError();
 }
 

@@ -287,8 +287,8 @@ def test_argument_errors():
 
 
 def test_auto_kernel_selection():
-    from paper_2404_12968_gb300 import GABP_KERNEL_FUSED, GABP_KERNEL_SWEEP
-    for (nx, prec, expect) in [(64, "fp32", GABP_KERNEL_SWEEP), (66, "fp32", GABP_KERNEL_SWEEP),
+    from paper_2404_12968_gb300 import GABP_KERNEL_FUSED, GABP_KERNEL_SWEEP, GABP_KERNEL_TMA
+    for (nx, prec, expect) in [(64, "fp32", GABP_KERNEL_TMA), (66, "fp32", GABP_KERNEL_SWEEP),
                                (64, "fp64", GABP_KERNEL_FUSED)]:
         p = gabp_synth.make_problem(nx, 40, 0.3, 0, n_uniform=50)
         with solver(p, prec) as s:
