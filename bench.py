@@ -277,12 +277,32 @@ def own_arm(args):
                      "kernel": KERNEL_NAMES[st["kernel"]], "algorithmic_bytes_per_launch": st["bytes_per_iter"],
                      "launch_ms": iter_ms},
     }
+    if rank == 0 and not args.no_e2e:
+        line["time_to_1e-5"] = warm_vs_cold(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def warm_vs_cold(device: int):
+    """Time to relative residual 1e-5 on the 2048^2 warm-start evaluation problem (kappa 0.03,
+    48 tracks), cold start vs the learned warm start with the committed trained weights
+    (network inference included)."""
+    from paper_2404_12968_gb300 import WarmStartNet
+    from paper_2404_12968_gb300.warmstart import evaluate
+    import gabp_synth
+    wpath = os.path.join(ROOT, "paper_2404_12968_gb300", "weights", "wsnet_512.npy")
+    if not os.path.exists(wpath):
+        return {"unavailable": "no trained weights"}
+    net = WarmStartNet(seed=0, device=device)
+    net.load(wpath)
+    r = evaluate(net, gabp_synth.config_warm_eval(0), device=device)
+    net.close()
+    r["workload"] = "warm-start evaluation 2048x2048, kappa 0.03, 48 tracks, sigma 0.05"
+    return r
 
 
 def _oracle_rate(p, iters: int):
