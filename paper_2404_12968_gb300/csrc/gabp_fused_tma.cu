@@ -93,10 +93,14 @@ template <int TY, int S> struct TileLayout {
     static constexpr uint32_t plane_bytes = 5u * RY * RX * 8u;
     static constexpr uint32_t optr_bytes = (uint32_t)OXW * OY * 4u;
     static constexpr size_t stage = a128(plane_bytes) + a128(optr_bytes);
+    // beliefs and observation row ranges are double-buffered (tile parity), so one block-wide
+    // barrier per tile separates their writers (phase A) from their readers (phase B)
+    static constexpr size_t bel_bytes = sizeof(Belief<float>) * BX * BY;
     static constexpr size_t bel_off = S * stage;
-    static constexpr size_t bar_off = a128(bel_off + sizeof(Belief<float>) * BX * BY);
+    static constexpr size_t bar_off = a128(bel_off + 2 * bel_bytes);
     static constexpr size_t ints_off = bar_off + 8 * (S + 1);   // S stage barriers + 1 test barrier
-    static constexpr size_t bytes = ints_off + sizeof(int) * (2 * TY + 4);
+    static constexpr int NI = 2 * TY + 2;                         // row starts [TY], prefix [TY + 1], pad
+    static constexpr size_t bytes = ints_off + sizeof(int) * (2 * NI + 2);
     static_assert(BY % TW == 0, "window rows must split evenly over the warps");
     static_assert(2 * RX <= 256 && RY <= 256 && OXW <= 256 && OY <= 256, "TMA box dimension above 256");
 };
@@ -109,11 +113,8 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
     constexpr int RX = LY::RX, RY = LY::RY, BX = LY::BX, BY = LY::BY, OXW = LY::OXW;
     constexpr int TW = LY::TW, TNT = LY::TNT;
     extern __shared__ __align__(128) unsigned char smem[];
-    Belief<float> *sb = reinterpret_cast<Belief<float> *>(smem + LY::bel_off);   // [BY][32]
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + LY::bar_off);
-    int *rstart = reinterpret_cast<int *>(smem + LY::ints_off);   // [TY]
-    int *rpre = rstart + TY;                                      // [TY + 1] exclusive prefix
-    int *flag = rpre + TY + 1;
+    int *flag = reinterpret_cast<int *>(smem + LY::ints_off) + 2 * LY::NI;
 
     const int nx = p.nx, ny = p.ny;
     const int64_t n = p.n;
@@ -165,19 +166,12 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
         const int tile = blockIdx.x + it * G;
         if (tile >= ntiles) break;
         const int stage = it % S;
+        // a thread whose wait ran out skips phase A (its staged indices may be stale) and the
+        // barrier after phase A stops the whole block
         const bool ok = mbar_wait(smem_addr(&bars[stage]), (uint32_t)((it / S) & 1));
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        // every thread has finished the previous tile: refill its stage with tile it-1+S
-        if (tid == 0 && it > 0) {
-            const int t2 = blockIdx.x + (it - 1 + S) * G;
-            if (t2 < ntiles) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue((it - 1) % S, t2);
-            }
-        }
+        Belief<float> *sb = reinterpret_cast<Belief<float> *>(smem + LY::bel_off + (it & 1) * LY::bel_bytes);
+        int *rstart = reinterpret_cast<int *>(smem + LY::ints_off) + (it & 1) * LY::NI;   // [TY]
+        int *rpre = rstart + TY;                                                          // [TY + 1]
 
         const int x0 = (tile % ntx) * TTX, y0 = (tile / ntx) * TY;
         const int xs = (x0 - 2) & ~3;
@@ -186,7 +180,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
         auto wptr = [&](int x, int y) { return W[(y - y0 + 2) * OXW + (x - xs)]; };
 
         // ---- A: observation ranges of the tile's rows (last warp), beliefs of the window ----
-        if (p.m > 0 && warp == TW - 1) {
+        if (ok && p.m > 0 && warp == TW - 1) {
             int st = 0, cnt = 0;
             const int gy = y0 + lane;
             if (lane < TY && gy < ny) {
@@ -209,7 +203,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
         for (int ly = warp; ly < BY; ly += TW) {
             const int gx = x0 - 1 + lane, gy = y0 - 1 + ly;
             Belief<float> b;
-            if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+            if (ok && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
                 const int rx = lane + 1, ry = ly + 1;
                 float2 m = sm[(DIR_C * RY + ry) * RX + rx];
                 CompSum<float> se(m.x), sl(m.y);
@@ -235,7 +229,18 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
             }
             sb[ly * BX + lane] = b;
         }
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        // every thread has finished tile it-1: refill its stage with tile it-1+S
+        if (tid == 0 && it > 0) {
+            const int t2 = blockIdx.x + (it - 1 + S) * G;
+            if (t2 < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue((it - 1) % S, t2);
+            }
+        }
 
         // ---- B: cell factors of the tile, then the observation factors based in it ----
         for (int ty = warp; ty < TY; ty += TW) {
@@ -288,7 +293,8 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
             const int total = rpre[TY];
             const float *Wt = (const float *)p.ow;
             const float *YV = (const float *)p.ovar;
-            for (int q = tid; q < total; q += TNT) {
+            // observation factors go first to the warps without a cell row
+            for (int q = (tid + TNT - 32 * TY) % TNT; q < total; q += TNT) {
                 int lo = 0, hi = TY - 1;   // last row r with rpre[r] <= q
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
@@ -326,8 +332,10 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
 
     if (failed && tid == 0) {
         atomicExch(p.err, 1);
-        // drain this block's outstanding copies (bounded): tiles it .. it+S-1 may be in flight
-        for (int j = it; j < it + S; ++j) {
+        // drain this block's outstanding copies (bounded): the prologue issued tiles 0 .. S-1 and
+        // the barrier of tile i >= 1 tile i-1+S, so tiles it .. jmax may be in flight
+        const int jmax = it == 0 ? S - 1 : it + S - 2;
+        for (int j = it; j <= jmax; ++j) {
             const int t = blockIdx.x + j * G;
             if (t >= ntiles) break;
             mbar_wait(smem_addr(&bars[j % S]), (uint32_t)((j / S) & 1));
