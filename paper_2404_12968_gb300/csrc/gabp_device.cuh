@@ -43,6 +43,16 @@ template <> __device__ __forceinline__ float recip<float>(float x) {
 }
 template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
 
+// Explicitly rounded arithmetic for the message formulas: no multiply is contracted into a
+// fused multiply-add unless written as one, so every kernel (scalar or packed two-lane FP32)
+// evaluates them with the same roundings and produces the same bits.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Two-term compensated sum (TwoSum accumulation, Knuth TAOCP vol. 2 4.2.2): hi + lo carries
 // the running sum to about twice the working precision.  Used for the belief sums so that
 // the cavity (belief minus one message) keeps its relative accuracy even when that message
@@ -117,8 +127,8 @@ __device__ __forceinline__ void factor_messages(const T (&a)[K], T var, T r, con
             p[u] = T(0);
         } else {
             T rl = recip(lam[u]);
-            t[u] = a[u] * a[u] * rl;
-            p[u] = a[u] * (eta[u] * rl);
+            t[u] = mul_rn(mul_rn(a[u], a[u]), rl);
+            p[u] = mul_rn(a[u], mul_rn(eta[u], rl));
         }
     }
     T preV[K], preM[K];
@@ -126,27 +136,28 @@ __device__ __forceinline__ void factor_messages(const T (&a)[K], T var, T r, con
     preM[0] = T(0);
 #pragma unroll
     for (int v = 1; v < K; ++v) {
-        preV[v] = preV[v - 1] + t[v - 1];
-        preM[v] = preM[v - 1] + p[v - 1];
+        preV[v] = add_rn(preV[v - 1], t[v - 1]);
+        preM[v] = add_rn(preM[v - 1], p[v - 1]);
     }
     T sufV = T(0), sufM = T(0);
 #pragma unroll
     for (int v = K - 1; v >= 0; --v) {
-        T V = preV[v] + sufV;
-        T M = preM[v] + sufM;
+        T V = add_rn(preV[v], sufV);
+        T M = add_rn(preM[v], sufM);
         // V >= var > 0; an infinite V (a slot without information) gives the message (0, 0)
         const bool inf_v = V == pos_inf<T>();
         const T rV = inf_v ? T(0) : recip(V);
-        L[v] = a[v] * a[v] * rV;
-        E[v] = inf_v ? T(0) : a[v] * (r - M) * rV;
-        sufV += t[v];
-        sufM += p[v];
+        L[v] = mul_rn(mul_rn(a[v], a[v]), rV);
+        E[v] = inf_v ? T(0) : mul_rn(mul_rn(a[v], add_rn(r, -M)), rV);
+        sufV = add_rn(sufV, t[v]);
+        sufM = add_rn(sufM, p[v]);
     }
 }
 
-// Damped update m_t = beta m_{t-1} + (1 - beta) m_new, evaluated as m_new + beta (m_{t-1} - m_new).
+// Damped update m_t = beta m_{t-1} + (1 - beta) m_new, evaluated as the fused multiply-add
+// m_new + beta (m_{t-1} - m_new).
 template <typename T> __device__ __forceinline__ T damp(T old, T fresh, T beta) {
-    return fresh + beta * (old - fresh);
+    return fma_rn(beta, add_rn(old, -fresh), fresh);
 }
 
 // Number of existing 4-neighbours of node (i, j).

@@ -84,9 +84,109 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 
 __host__ __device__ constexpr size_t a128(size_t x) { return (x + 127) & ~size_t(127); }
 
-// One warp per belief-window row: TY + 2 warps per block.
-template <int TY, int S> struct TileLayout {
-    static constexpr int TW = TY + 2, TNT = 32 * TW;   // warps, threads
+// ---- packed two-lane FP32 arithmetic on (eta, Lambda) pairs ----
+// Every (eta, Lambda) pair goes through the same sequence of roundings as the scalar formulas
+// in gabp_device.cuh (add_rn, mul_rn, fma_rn per component), so the results are bit-identical
+// to the other kernels; one packed instruction issues both components.
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, f2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Compensated (eta, Lambda) belief sums: TwoSum accumulation of both components at once.
+struct CompSum2 {
+    float2 hi, lo;
+    __device__ __forceinline__ explicit CompSum2(float2 first) : hi(first), lo(f2(0.f, 0.f)) {}
+    __device__ __forceinline__ void add(float2 x) {
+        const float2 t = add2(hi, x);
+        const float2 z = sub2(t, hi);
+        const float2 e = add2(sub2(hi, sub2(t, z)), sub2(x, z));
+        hi = t;
+        lo = add2(lo, e);
+    }
+    __device__ __forceinline__ void finish() {
+        const float2 t = add2(hi, lo);
+        lo = sub2(lo, sub2(t, hi));
+        hi = t;
+    }
+};
+
+// A compensated belief: hi = (eta_hi, Lambda_hi), lo = (eta_lo, Lambda_lo).
+struct Belief2 {
+    float2 hi, lo;
+};
+
+// Cavity (belief minus the edge's own message), (hi - own) + lo per component.
+__device__ __forceinline__ float2 cavity2(const Belief2 &b, float2 own) { return add2(sub2(b.hi, own), b.lo); }
+
+// Observation messages into one node from the base cells of one row, in increasing
+// observation index (the order every kernel uses): corner cl for [lo, mid), cr for [mid, hi).
+__device__ __forceinline__ void add_obs_pair2(CompSum2 &s, const float *O, int lo, int mid, int hi, int cl, int cr) {
+    for (int k = lo; k < hi; ++k) {
+        const int c = k < mid ? cl : cr;
+        s.add(f2(O[8 * (int64_t)k + c], O[8 * (int64_t)k + 4 + c]));
+    }
+}
+
+// Factor-to-variable messages of a rank-1 factor with K slots on (eta, Lambda) pairs: the
+// arithmetic of factor_messages (App. A) with the (M, V) sums and the (eta, Lambda) outputs
+// carried as pairs.  cav[u] = cavity (eta, Lambda) of slot u; out[u] = message (eta, Lambda).
+template <int K>
+__device__ __forceinline__ void factor_messages2(const float (&a)[K], float var, float r, const float2 (&cav)[K],
+                                                 float2 (&out)[K]) {
+    float2 tp[K];   // (a eta / lam, a^2 / lam)
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+        if (a[u] == 0.f) {
+            tp[u] = f2(0.f, 0.f);
+        } else if (!(cav[u].y >= tiny_normal<float>())) {
+            tp[u] = f2(0.f, pos_inf<float>());
+        } else {
+            const float rl = recip(cav[u].y);
+            tp[u] = mul2(f2(a[u], mul_rn(a[u], a[u])), f2(mul_rn(cav[u].x, rl), rl));
+        }
+    }
+    float2 pre[K];   // prefix sums (M, V), V starting from var
+    pre[0] = f2(0.f, var);
+#pragma unroll
+    for (int v = 1; v < K; ++v) pre[v] = add2(pre[v - 1], tp[v - 1]);
+    float2 suf = f2(0.f, 0.f);
+#pragma unroll
+    for (int v = K - 1; v >= 0; --v) {
+        const float2 MV = add2(pre[v], suf);
+        const bool inf_v = MV.y == pos_inf<float>();
+        const float rV = inf_v ? 0.f : recip(MV.y);
+        float2 o = mul2(f2(mul_rn(a[v], add_rn(r, -MV.x)), mul_rn(a[v], a[v])), f2(rV, rV));
+        if (inf_v) o.x = 0.f;
+        out[v] = o;
+        suf = add2(suf, tp[v]);
+    }
+}
+
+// Damped update of an (eta, Lambda) pair: fresh + beta (old - fresh) as one fused multiply-add.
+__device__ __forceinline__ float2 damp2(float2 old, float2 fresh, float2 beta2) {
+    return fma2(beta2, sub2(old, fresh), fresh);
+}
+
+// Update of the rank-1 factor of one cell (row of L, Eq. 5 / App. A): cavities of its five
+// slots from the compensated beliefs, the factor-to-variable messages, damping, and a
+// streaming store of the five outgoing messages (planes n apart).  Slots with a = 0 (missing
+// neighbours at the grid border) send (0, 0).
+__device__ __forceinline__ void cell_factor(const float (&a)[5], const Belief2 *const (&bs)[5], const float2 (&own)[5],
+                                            float var, float2 beta2, float2 *q, int64_t n) {
+    float2 cav[5];
+#pragma unroll
+    for (int u = 0; u < 5; ++u) cav[u] = a[u] != 0.f ? cavity2(*bs[u], own[u]) : f2(0.f, 1.f);
+    float2 msg[5];
+    factor_messages2<5>(a, var, 0.f, cav, msg);
+#pragma unroll
+    for (int u = 0; u < 5; ++u) __stcs(q + u * n, a[u] != 0.f ? damp2(own[u], msg[u], beta2) : f2(0.f, 0.f));
+}
+
+// RW belief-window rows (and up to RW cell rows) per warp: (TY + 2) / RW warps per block.
+template <int TY, int S, int RW> struct TileLayout {
+    static constexpr int TW = (TY + 2) / RW, TNT = 32 * TW;   // warps, threads
     static constexpr int RX = TTX + 4, RY = TY + 4;   // staged planes (cells), origin (x0-2, y0-2)
     static constexpr int BX = 32, BY = TY + 2;        // belief window, origin (x0-1, y0-1)
     static constexpr int OXW = 40, OY = TY + 3;       // observation index window, origin (xs, y0-2)
@@ -95,21 +195,25 @@ template <int TY, int S> struct TileLayout {
     static constexpr size_t stage = a128(plane_bytes) + a128(optr_bytes);
     // beliefs and observation row ranges are double-buffered (tile parity), so one block-wide
     // barrier per tile separates their writers (phase A) from their readers (phase B)
-    static constexpr size_t bel_bytes = sizeof(Belief<float>) * BX * BY;
+    static constexpr size_t bel_bytes = sizeof(Belief2) * BX * BY;
     static constexpr size_t bel_off = S * stage;
     static constexpr size_t bar_off = a128(bel_off + 2 * bel_bytes);
     static constexpr size_t ints_off = bar_off + 8 * (S + 1);   // S stage barriers + 1 test barrier
     static constexpr int NI = 2 * TY + 2;                         // row starts [TY], prefix [TY + 1], pad
     static constexpr size_t bytes = ints_off + sizeof(int) * (2 * NI + 2);
-    static_assert(BY % TW == 0, "window rows must split evenly over the warps");
+    // resident blocks per SM that threads and shared memory (228 KB, 1 KB reserved per block)
+    // allow; the register budget is sized for it
+    static constexpr int MINB_T = 2048 / TNT, MINB_S = (int)((228 * 1024) / (bytes + 1024));
+    static constexpr int MINB = MINB_T < MINB_S ? MINB_T : MINB_S;
+    static_assert(BY == RW * TW, "window rows must split evenly over the warps");
     static_assert(2 * RX <= 256 && RY <= 256 && OXW <= 256 && OY <= 256, "TMA box dimension above 256");
 };
 
-template <int TY, int S>
-__global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __grid_constant__ CUtensorMap mplanes,
+template <int TY, int S, int RW>
+__global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, RW>::MINB) k_fused_tma(const __grid_constant__ CUtensorMap mplanes,
                                                    const __grid_constant__ CUtensorMap moptr, DevProblem p,
                                                    int src, float beta) {
-    using LY = TileLayout<TY, S>;
+    using LY = TileLayout<TY, S, RW>;
     constexpr int RX = LY::RX, RY = LY::RY, BX = LY::BX, BY = LY::BY, OXW = LY::OXW;
     constexpr int TW = LY::TW, TNT = LY::TNT;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -127,6 +231,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
     float *OQ = (float *)p.O[src ^ 1];
     const float var_prior = (float)(1.0 / p.gamma);
     const float aC_in = (float)p.aC[4];
+    const float2 beta2 = f2(beta, beta);
 
     auto issue = [&](int stage, int tile) {
         const int x0 = (tile % ntx) * TTX, y0 = (tile / ntx) * TY;
@@ -160,20 +265,31 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
             if (t < ntiles) issue(s, t);
         }
 
+    // tile coordinates advance by G tiles per step without a division
+    const int step_x = G % ntx, step_y = G / ntx;
+    int tcx = (int)blockIdx.x % ntx, tcy = (int)blockIdx.x / ntx;
     int it = 0;
     bool failed = false;
     for (;; ++it) {
+        if (it > 0) {
+            tcx += step_x;
+            tcy += step_y;
+            if (tcx >= ntx) {
+                tcx -= ntx;
+                ++tcy;
+            }
+        }
         const int tile = blockIdx.x + it * G;
         if (tile >= ntiles) break;
         const int stage = it % S;
         // a thread whose wait ran out skips phase A (its staged indices may be stale) and the
         // barrier after phase A stops the whole block
         const bool ok = mbar_wait(smem_addr(&bars[stage]), (uint32_t)((it / S) & 1));
-        Belief<float> *sb = reinterpret_cast<Belief<float> *>(smem + LY::bel_off + (it & 1) * LY::bel_bytes);
+        Belief2 *sb = reinterpret_cast<Belief2 *>(smem + LY::bel_off + (it & 1) * LY::bel_bytes);
         int *rstart = reinterpret_cast<int *>(smem + LY::ints_off) + (it & 1) * LY::NI;   // [TY]
         int *rpre = rstart + TY;                                                          // [TY + 1]
 
-        const int x0 = (tile % ntx) * TTX, y0 = (tile / ntx) * TY;
+        const int x0 = tcx * TTX, y0 = tcy * TY;
         const int xs = (x0 - 2) & ~3;
         const float2 *sm = reinterpret_cast<const float2 *>(smem + stage * LY::stage);   // [5][RY][RX]
         const int *W = reinterpret_cast<const int *>(smem + stage * LY::stage + a128(LY::plane_bytes));
@@ -202,30 +318,29 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
         }
         for (int ly = warp; ly < BY; ly += TW) {
             const int gx = x0 - 1 + lane, gy = y0 - 1 + ly;
-            Belief<float> b;
+            Belief2 b;
             if (ok && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
                 const int rx = lane + 1, ry = ly + 1;
-                float2 m = sm[(DIR_C * RY + ry) * RX + rx];
-                CompSum<float> se(m.x), sl(m.y);
+                CompSum2 s(sm[(DIR_C * RY + ry) * RX + rx]);
                 // zero-filled outside the grid: the boundary terms add exact zeros
-                m = sm[(DIR_E * RY + ry) * RX + rx - 1]; se.add(m.x); sl.add(m.y);
-                m = sm[(DIR_W * RY + ry) * RX + rx + 1]; se.add(m.x); sl.add(m.y);
-                m = sm[(DIR_N * RY + ry - 1) * RX + rx]; se.add(m.x); sl.add(m.y);
-                m = sm[(DIR_S * RY + ry + 1) * RX + rx]; se.add(m.x); sl.add(m.y);
+                s.add(sm[(DIR_E * RY + ry) * RX + rx - 1]);
+                s.add(sm[(DIR_W * RY + ry) * RX + rx + 1]);
+                s.add(sm[(DIR_N * RY + ry - 1) * RX + rx]);
+                s.add(sm[(DIR_S * RY + ry + 1) * RX + rx]);
                 if (p.m > 0) {
                     const bool last = gx == nx - 1;
                     const int a0 = wptr(gx, gy);
-                    add_obs_pair(se, sl, O, gx > 0 ? wptr(gx - 1, gy) : a0, a0, last ? a0 : wptr(gx + 1, gy), 1, 0);
+                    add_obs_pair2(s, O, gx > 0 ? wptr(gx - 1, gy) : a0, a0, last ? a0 : wptr(gx + 1, gy), 1, 0);
                     if (gy > 0) {
                         const int c0 = wptr(gx, gy - 1);
-                        add_obs_pair(se, sl, O, gx > 0 ? wptr(gx - 1, gy - 1) : c0, c0, last ? c0 : wptr(gx + 1, gy - 1), 3, 2);
+                        add_obs_pair2(s, O, gx > 0 ? wptr(gx - 1, gy - 1) : c0, c0, last ? c0 : wptr(gx + 1, gy - 1), 3, 2);
                     }
                 }
-                se.finish();
-                sl.finish();
-                b.ehi = se.hi; b.elo = se.lo; b.lhi = sl.hi; b.llo = sl.lo;
+                s.finish();
+                b.hi = s.hi;
+                b.lo = s.lo;
             } else {
-                b.ehi = b.elo = b.lhi = b.llo = 0.f;
+                b.hi = b.lo = f2(0.f, 0.f);
             }
             sb[ly * BX + lane] = b;
         }
@@ -247,54 +362,28 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
             const int tx = lane, gx = x0 + tx, gy = y0 + ty;
             if (tx >= TTX || gx >= nx || gy >= ny) continue;
             const int64_t c = (int64_t)gy * nx + gx;
-            const Belief<float> *bs[5] = {&sb[(ty + 1) * BX + tx + 1], &sb[(ty + 1) * BX + tx],
+            const Belief2 *bs[5] = {&sb[(ty + 1) * BX + tx + 1], &sb[(ty + 1) * BX + tx],
                                           &sb[(ty + 1) * BX + tx + 2], &sb[ty * BX + tx + 1],
                                           &sb[(ty + 2) * BX + tx + 1]};
             float2 own[5];
 #pragma unroll
             for (int u = 0; u < 5; ++u) own[u] = sm[(u * RY + ty + 2) * RX + tx + 2];
-            const bool inner = gx > 0 && gx < nx - 1 && gy > 0 && gy < ny - 1;
-            float a[5];
-            if (inner) {
-                a[0] = aC_in; a[1] = -1.f; a[2] = -1.f; a[3] = -1.f; a[4] = -1.f;
+            if (gx > 0 && gx < nx - 1 && gy > 0 && gy < ny - 1) {
+                // interior cell: literal coefficients, so the compiler folds the -1 factors
+                const float a[5] = {aC_in, -1.f, -1.f, -1.f, -1.f};
+                cell_factor(a, bs, own, var_prior, beta2, Q + c, n);
             } else {
-                a[0] = (float)p.aC[grid_degree(gy, gx, nx, ny)];
-                a[1] = gx > 0 ? -1.f : 0.f;
-                a[2] = gx < nx - 1 ? -1.f : 0.f;
-                a[3] = gy > 0 ? -1.f : 0.f;
-                a[4] = gy < ny - 1 ? -1.f : 0.f;
-            }
-            float lam[5], eta[5];
-#pragma unroll
-            for (int u = 0; u < 5; ++u) {
-                if (a[u] != 0.f) {
-                    cavity(*bs[u], own[u].x, own[u].y, eta[u], lam[u]);
-                } else {
-                    lam[u] = 1.f;
-                    eta[u] = 0.f;
-                }
-            }
-            float L[5], E[5];
-            factor_messages<float, 5>(a, var_prior, 0.f, lam, eta, L, E);
-#pragma unroll
-            for (int u = 0; u < 5; ++u) {
-                float2 out;
-                if (a[u] != 0.f) {
-                    out.x = damp(own[u].x, E[u], beta);
-                    out.y = damp(own[u].y, L[u], beta);
-                } else {
-                    out.x = 0.f;
-                    out.y = 0.f;
-                }
-                __stcs(Q + u * n + c, out);
+                const float a[5] = {(float)p.aC[grid_degree(gy, gx, nx, ny)], gx > 0 ? -1.f : 0.f,
+                                    gx < nx - 1 ? -1.f : 0.f, gy > 0 ? -1.f : 0.f, gy < ny - 1 ? -1.f : 0.f};
+                cell_factor(a, bs, own, var_prior, beta2, Q + c, n);
             }
         }
         if (p.m > 0) {
             const int total = rpre[TY];
             const float *Wt = (const float *)p.ow;
             const float *YV = (const float *)p.ovar;
-            // observation factors go first to the warps without a cell row
-            for (int q = (tid + TNT - 32 * TY) % TNT; q < total; q += TNT) {
+            // observation factors go first to the two warps with one cell row fewer
+            for (int q = (tid + TNT - 32 * (TW - 2)) % TNT; q < total; q += TNT) {
                 int lo = 0, hi = TY - 1;   // last row r with rpre[r] <= q
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
@@ -305,7 +394,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
                 const int64_t k = rstart[r] + (q - rpre[r]);
                 const int bx = p.obase[k] - (y0 + r) * nx;
                 const int lx = bx - x0 + 1, ly = r + 1;   // window coordinates of the base node
-                const Belief<float> *ob[4] = {&sb[ly * BX + lx], &sb[ly * BX + lx + 1], &sb[(ly + 1) * BX + lx],
+                const Belief2 *ob[4] = {&sb[ly * BX + lx], &sb[ly * BX + lx + 1], &sb[(ly + 1) * BX + lx],
                                               &sb[(ly + 1) * BX + lx + 1]};
                 const float4 w4 = *reinterpret_cast<const float4 *>(Wt + 4 * k);
                 const float aw[4] = {w4.x, w4.y, w4.z, w4.w};
@@ -313,17 +402,19 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
                 const float4 ol4 = *reinterpret_cast<const float4 *>(O + 8 * k + 4);
                 const float oe[4] = {oe4.x, oe4.y, oe4.z, oe4.w};
                 const float ol[4] = {ol4.x, ol4.y, ol4.z, ol4.w};
-                float olam[4], oeta[4];
+                float2 own4[4], cav[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) cavity(*ob[u], oe[u], ol[u], oeta[u], olam[u]);
-                float OL[4], OE[4];
+                for (int u = 0; u < 4; ++u) {
+                    own4[u] = f2(oe[u], ol[u]);
+                    cav[u] = cavity2(*ob[u], own4[u]);
+                }
                 const float2 yv = *reinterpret_cast<const float2 *>(YV + 2 * k);
-                factor_messages<float, 4>(aw, yv.y, yv.x, olam, oeta, OL, OE);
-                float4 ne, nl;
-                ne.x = damp(oe[0], OE[0], beta); ne.y = damp(oe[1], OE[1], beta);
-                ne.z = damp(oe[2], OE[2], beta); ne.w = damp(oe[3], OE[3], beta);
-                nl.x = damp(ol[0], OL[0], beta); nl.y = damp(ol[1], OL[1], beta);
-                nl.z = damp(ol[2], OL[2], beta); nl.w = damp(ol[3], OL[3], beta);
+                float2 msg[4];
+                factor_messages2<4>(aw, yv.y, yv.x, cav, msg);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) msg[u] = damp2(own4[u], msg[u], beta2);
+                const float4 ne = make_float4(msg[0].x, msg[1].x, msg[2].x, msg[3].x);
+                const float4 nl = make_float4(msg[0].y, msg[1].y, msg[2].y, msg[3].y);
                 *reinterpret_cast<float4 *>(OQ + 8 * k) = ne;
                 *reinterpret_cast<float4 *>(OQ + 8 * k + 4) = nl;
             }
@@ -343,9 +434,9 @@ __global__ void __launch_bounds__(TileLayout<TY, S>::TNT) k_fused_tma(const __gr
     }
 }
 
-template <int TY, int S>
+template <int TY, int S, int RW>
 cudaError_t launch_cfg(const DevProblem &p, const TmaMaps &maps, int src, double beta, cudaStream_t st) {
-    using LY = TileLayout<TY, S>;
+    using LY = TileLayout<TY, S, RW>;
     static int grid_cache = 0;
     static int configured_dev = -1;
     // the tensor maps' boxes must have been encoded for this tile height (the smem layout and
@@ -355,12 +446,12 @@ cudaError_t launch_cfg(const DevProblem &p, const TmaMaps &maps, int src, double
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (configured_dev != dev) {
-        e = cudaFuncSetAttribute(k_fused_tma<TY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::bytes);
+        e = cudaFuncSetAttribute(k_fused_tma<TY, S, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::bytes);
         if (e != cudaSuccess) return e;
         int nsm = 0, per_sm = 0;
         e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tma<TY, S>, LY::TNT, LY::bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tma<TY, S, RW>, LY::TNT, LY::bytes);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         grid_cache = nsm * per_sm;
@@ -368,7 +459,7 @@ cudaError_t launch_cfg(const DevProblem &p, const TmaMaps &maps, int src, double
     }
     const int ntiles = ((p.nx + TTX - 1) / TTX) * ((p.ny + TY - 1) / TY);
     const int grid = ntiles < grid_cache ? ntiles : grid_cache;
-    k_fused_tma<TY, S><<<grid, LY::TNT, LY::bytes, st>>>(maps.planes[src], maps.optr, p, src, (float)beta);
+    k_fused_tma<TY, S, RW><<<grid, LY::TNT, LY::bytes, st>>>(maps.planes[src], maps.optr, p, src, (float)beta);
     return cudaGetLastError();
 }
 
@@ -426,18 +517,18 @@ cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps) {
 
 size_t tma_smem_bytes(int tx, int ty) {
     if (tx != TTX) return 0;
-    if (ty == 14) return TileLayout<14, 2>::bytes;
-    if (ty == 22) return TileLayout<22, 2>::bytes;
-    if (ty == 30) return TileLayout<30, 2>::bytes;
+    if (ty == 14) return TileLayout<14, 2, 1>::bytes;
+    if (ty == 22) return TileLayout<22, 2, 1>::bytes;
+    if (ty == 30) return TileLayout<30, 2, 1>::bytes;
     return 0;
 }
 
 cudaError_t launch_tma_iteration(const DevProblem &p, const TmaMaps &maps, int src, double beta,
                                  cudaStream_t st) {
     if (!maps.valid) return cudaErrorInvalidValue;
-    if (maps.ty == 14) return launch_cfg<14, 2>(p, maps, src, beta, st);
-    if (maps.ty == 22) return launch_cfg<22, 2>(p, maps, src, beta, st);
-    if (maps.ty == 30) return launch_cfg<30, 2>(p, maps, src, beta, st);
+    if (maps.ty == 14) return launch_cfg<14, 2, 1>(p, maps, src, beta, st);
+    if (maps.ty == 22) return launch_cfg<22, 2, 1>(p, maps, src, beta, st);
+    if (maps.ty == 30) return launch_cfg<30, 2, 1>(p, maps, src, beta, st);
     return cudaErrorInvalidValue;
 }
 
