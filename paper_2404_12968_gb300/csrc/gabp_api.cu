@@ -291,6 +291,8 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     p.gamma = gamma;
     p.debug_stall = (o.debug_flags & 1) ? 1 : 0;
     for (int d = 0; d <= 4; ++d) p.aC[d] = kappa * kappa + (double)d;
+    p.var_f = (float)(1.0 / gamma);
+    for (int d = 0; d <= 4; ++d) p.aC_f[d] = (float)p.aC[d];
     const size_t T = tsize(c);
     int rc;
     void *q;

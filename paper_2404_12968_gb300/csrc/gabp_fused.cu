@@ -110,14 +110,14 @@ __global__ void __launch_bounds__(FT) k_fused(DevProblem p, int src, T beta) {
     __syncthreads();
 
     // 3a. prior cell factors of the tile
-    const T var_prior = T(1.0 / p.gamma);
+    const T var_prior = prior_var<T>(p);
     for (int q = threadIdx.x; q < TX * TY; q += FT) {
         const int ty = q / TX, tx = q - ty * TX;
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx >= nx || gy >= ny) continue;
         const int64_t c = (int64_t)gy * nx + gx;
         const int deg = grid_degree(gy, gx, nx, ny);
-        const T a[5] = {T(p.aC[deg]), gx > 0 ? T(-1) : T(0), gx < nx - 1 ? T(-1) : T(0),
+        const T a[5] = {cell_coef<T>(p, deg), gx > 0 ? T(-1) : T(0), gx < nx - 1 ? T(-1) : T(0),
                         gy > 0 ? T(-1) : T(0), gy < ny - 1 ? T(-1) : T(0)};
         // belief-window coordinates of the 5 nodes (C, W, E, S, N)
         const int bxs[5] = {tx + 1, tx, tx + 2, tx + 1, tx + 1};

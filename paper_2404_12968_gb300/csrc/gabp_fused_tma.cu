@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
     float2 *Q = (float2 *)p.P[src ^ 1];
     const float *O = (const float *)p.O[src];
     float *OQ = (float *)p.O[src ^ 1];
-    const float var_prior = (float)(1.0 / p.gamma);
-    const float aC_in = (float)p.aC[4];
+    const float var_prior = p.var_f;
+    const float aC_in = p.aC_f[4];
     const float2 beta2 = f2(beta, beta);
 
     auto issue = [&](int stage, int tile) {
@@ -321,20 +321,43 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
             Belief2 b;
             if (ok && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
                 const int rx = lane + 1, ry = ly + 1;
+                // observation ranges of the node: base row gy (corners 1, 0) and base row gy-1
+                // (corners 3, 2); the first message of each range is loaded before the prior
+                // sums, so that its latency overlaps them (the order of the sum is unchanged)
+                int lo1 = 0, mid1 = 0, hi1 = 0, lo2 = 0, mid2 = 0, hi2 = 0;
+                float2 first1 = f2(0.f, 0.f), first2 = f2(0.f, 0.f);
+                if (p.m > 0) {
+                    const bool last = gx == nx - 1;
+                    mid1 = wptr(gx, gy);
+                    lo1 = gx > 0 ? wptr(gx - 1, gy) : mid1;
+                    hi1 = last ? mid1 : wptr(gx + 1, gy);
+                    if (gy > 0) {
+                        mid2 = wptr(gx, gy - 1);
+                        lo2 = gx > 0 ? wptr(gx - 1, gy - 1) : mid2;
+                        hi2 = last ? mid2 : wptr(gx + 1, gy - 1);
+                    }
+                    if (lo1 < hi1) {
+                        const int c = lo1 < mid1 ? 1 : 0;
+                        first1 = f2(O[8 * (int64_t)lo1 + c], O[8 * (int64_t)lo1 + 4 + c]);
+                    }
+                    if (lo2 < hi2) {
+                        const int c = lo2 < mid2 ? 3 : 2;
+                        first2 = f2(O[8 * (int64_t)lo2 + c], O[8 * (int64_t)lo2 + 4 + c]);
+                    }
+                }
                 CompSum2 s(sm[(DIR_C * RY + ry) * RX + rx]);
                 // zero-filled outside the grid: the boundary terms add exact zeros
                 s.add(sm[(DIR_E * RY + ry) * RX + rx - 1]);
                 s.add(sm[(DIR_W * RY + ry) * RX + rx + 1]);
                 s.add(sm[(DIR_N * RY + ry - 1) * RX + rx]);
                 s.add(sm[(DIR_S * RY + ry + 1) * RX + rx]);
-                if (p.m > 0) {
-                    const bool last = gx == nx - 1;
-                    const int a0 = wptr(gx, gy);
-                    add_obs_pair2(s, O, gx > 0 ? wptr(gx - 1, gy) : a0, a0, last ? a0 : wptr(gx + 1, gy), 1, 0);
-                    if (gy > 0) {
-                        const int c0 = wptr(gx, gy - 1);
-                        add_obs_pair2(s, O, gx > 0 ? wptr(gx - 1, gy - 1) : c0, c0, last ? c0 : wptr(gx + 1, gy - 1), 3, 2);
-                    }
+                if (lo1 < hi1) {
+                    s.add(first1);
+                    add_obs_pair2(s, O, lo1 + 1, mid1, hi1, 1, 0);
+                }
+                if (lo2 < hi2) {
+                    s.add(first2);
+                    add_obs_pair2(s, O, lo2 + 1, mid2, hi2, 3, 2);
                 }
                 s.finish();
                 b.hi = s.hi;
@@ -373,7 +396,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                 const float a[5] = {aC_in, -1.f, -1.f, -1.f, -1.f};
                 cell_factor(a, bs, own, var_prior, beta2, Q + c, n);
             } else {
-                const float a[5] = {(float)p.aC[grid_degree(gy, gx, nx, ny)], gx > 0 ? -1.f : 0.f,
+                const float a[5] = {p.aC_f[grid_degree(gy, gx, nx, ny)], gx > 0 ? -1.f : 0.f,
                                     gx < nx - 1 ? -1.f : 0.f, gy > 0 ? -1.f : 0.f, gy < ny - 1 ? -1.f : 0.f};
                 cell_factor(a, bs, own, var_prior, beta2, Q + c, n);
             }

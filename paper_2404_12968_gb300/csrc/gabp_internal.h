@@ -15,7 +15,9 @@ struct DevProblem {
     int64_t n, m;
     int prec;            // 0 = FP32, 1 = FP64
     double gamma;        // prior scale (factor precision of every cell factor)
-    double aC[5];        // kappa^2 + deg for deg = 0..4 (FP64; kernels round to T)
+    double aC[5];        // kappa^2 + deg for deg = 0..4 (FP64)
+    float var_f;         // (float)(1 / gamma), rounded once on the host
+    float aC_f[5];       // (float)aC[d]
     void *P[2];          // prior messages, ping-pong: 5 * n (eta, Lambda) pairs
     void *O[2];          // observation messages, ping-pong: 8 * m values
     const int *obase;    // m base-cell indices (sorted ascending)
@@ -33,6 +35,16 @@ struct DevProblem {
     int *err;            // device error flag (a bounded wait in a kernel gave up)
     int debug_stall;     // test hook: the TMA kernel first waits on a barrier nothing completes
 };
+
+// Prior constants in the kernel's precision.  FP32 kernels read the values rounded once on the
+// host (the same roundings as converting the FP64 values on the device, without FP64
+// instructions in the FP32 kernels); FP64 kernels read the FP64 values.
+template <typename T> __device__ __forceinline__ T prior_var(const DevProblem &p);
+template <> __device__ __forceinline__ float prior_var<float>(const DevProblem &p) { return p.var_f; }
+template <> __device__ __forceinline__ double prior_var<double>(const DevProblem &p) { return 1.0 / p.gamma; }
+template <typename T> __device__ __forceinline__ T cell_coef(const DevProblem &p, int deg);
+template <> __device__ __forceinline__ float cell_coef<float>(const DevProblem &p, int deg) { return p.aC_f[deg]; }
+template <> __device__ __forceinline__ double cell_coef<double>(const DevProblem &p, int deg) { return p.aC[deg]; }
 
 constexpr int RES_BLOCKS = 1024;   // fixed partition of the deterministic residual reduction
 

@@ -68,7 +68,7 @@ template <typename T> __global__ void k_prior(DevProblem p, int src, T beta) {
     const T2<T> *P = (const T2<T> *)p.P[src];
     T2<T> *Q = (T2<T> *)p.P[src ^ 1];
     const int deg = grid_degree(i, j, nx, ny);
-    const T a[5] = {T(p.aC[deg]), j > 0 ? T(-1) : T(0), j < nx - 1 ? T(-1) : T(0),
+    const T a[5] = {cell_coef<T>(p, deg), j > 0 ? T(-1) : T(0), j < nx - 1 ? T(-1) : T(0),
                     i > 0 ? T(-1) : T(0), i < ny - 1 ? T(-1) : T(0)};
     const int64_t node[5] = {c, c - 1, c + 1, c - nx, c + nx};
     T2<T> own[5];
@@ -84,7 +84,7 @@ template <typename T> __global__ void k_prior(DevProblem p, int src, T beta) {
         }
     }
     T L[5], E[5];
-    factor_messages<T, 5>(a, T(1.0 / p.gamma), T(0), lam, eta, L, E);
+    factor_messages<T, 5>(a, prior_var<T>(p), T(0), lam, eta, L, E);
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
         T2<T> out;

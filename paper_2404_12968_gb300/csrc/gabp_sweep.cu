@@ -268,8 +268,8 @@ __device__ __forceinline__ void sweep_strip(const DevProblem &p, WarpRing &ring,
     float2 *Q = (float2 *)p.P[src ^ 1];
     const float *O = (const float *)p.O[src];
     float *OQ = (float *)p.O[src ^ 1];
-    const float var_prior = (float)(1.0 / p.gamma);
-    const float aC_in = (float)p.aC[4];
+    const float var_prior = p.var_f;
+    const float aC_in = p.aC_f[4];
 
     const int cs = strip % ncs, rs = strip / ncs;
     const int x0 = cs * SW;
@@ -312,7 +312,7 @@ __device__ __forceinline__ void sweep_strip(const DevProblem &p, WarpRing &ring,
                 cell_factor(a, var_prior, beta, s_0.msg, bs, Q, n, c);
             } else {
                 const int deg = grid_degree(r, x, nx, ny);
-                const float a[5] = {(float)p.aC[deg], x > 0 ? -1.f : 0.f, x < nx - 1 ? -1.f : 0.f,
+                const float a[5] = {p.aC_f[deg], x > 0 ? -1.f : 0.f, x < nx - 1 ? -1.f : 0.f,
                                     r > 0 ? -1.f : 0.f, r < ny - 1 ? -1.f : 0.f};
                 cell_factor(a, var_prior, beta, s_0.msg, bs, Q, n, c);
             }
