@@ -50,6 +50,21 @@ def dist_info():
     return rank, world, local
 
 
+def reduce_over_ranks(units: float, ms: float, device=None):
+    """Whole-job totals under torch.distributed: the units all ranks processed (sum) and the
+    slowest rank's time (max).  Without an initialised process group (one rank) the local
+    values are returned unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(units), float(ms)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def measured_peak_gbs():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -211,10 +226,8 @@ def own_arm(args):
         dist.barrier()
     ms = t0.elapsed_time(t1)
     iter_ms = sum(a.elapsed_time(b) for a, b in evs) / (args.steps * ITERS_PER_STEP)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    node_updates = n * ITERS_PER_STEP
+    job_units, ms = reduce_over_ranks(node_updates * args.steps, ms, dev)
     s.close()
 
     # end to end through the public API from host buffers
@@ -236,6 +249,7 @@ def own_arm(args):
 
     e_steps = max(1, min(args.steps, 5))
     e_ms = float("nan")
+    e_units = 0.0
     if not args.no_e2e:
         e2e_step()
         torch.cuda.synchronize()
@@ -246,13 +260,10 @@ def own_arm(args):
             e2e_step()
         torch.cuda.synchronize()
         e_ms = (time.perf_counter() - tt) * 1e3 / e_steps
-    if world > 1:
-        t = torch.tensor([e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
+        e_units = node_updates
+    e_units, e_ms = reduce_over_ranks(e_units, e_ms, dev)
 
-    node_updates = n * ITERS_PER_STEP
-    value = world * node_updates * args.steps / (ms / 1e3)
+    value = job_units / (ms / 1e3)
     peak, peak_kind = measured_peak_gbs()
     achieved = st["bytes_per_iter"] / (iter_ms / 1e3) / 1e9
     traffic = profiled_traffic(KERNEL_NAMES[st["kernel"]])
@@ -269,7 +280,7 @@ def own_arm(args):
                    "l2": "inputs larger than L2 (message planes 1.3 GB ping-pong)"},
         "hbm_gbs": achieved, "rel_residual_last_step": residuals[-1],
         "clocks": clocks,
-        "e2e": {"value": world * node_updates / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": e_units / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e_ms},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -360,8 +360,8 @@ template <typename T> __global__ void k_marg(DevProblem p, double *mean, double 
 
 // x[i][j][0..15]: mean of y / scale over the observations whose nearest node is (i, j), the
 // mask of such nodes, log(kappa) + 3, zeros.  The nearest node of an observation is the corner
-// of its base cell that carries the largest bilinear weight (ties to the lower index), found from
-// fu = w1 + w3 and fv = w2 + w3.
+// of its base cell nearest to it along each axis, found from the fractions fu = w1 + w3 and
+// fv = w2 + w3 (a fraction of exactly 0.5 goes to the higher index).
 __global__ void k_ws_input(DevProblem p, double inv_scale, float kfeat, int Hp, int Wp, __nv_bfloat16 *x) {
     const int64_t q = gtid();
     if (q >= (int64_t)Hp * Wp) return;
