@@ -288,6 +288,14 @@ int64_t gabp_wsnet_param_count(const gabp_wsnet *net);
 /* FP32 parameter vector (host or device, gabp_wsnet_param_count floats). */
 int gabp_wsnet_get_params(gabp_wsnet *net, float *params);
 int gabp_wsnet_set_params(gabp_wsnet *net, const float *params);
+/* Kernel family of the forward pass: GABP_WSNET_TCGEN05 (default) runs every convolution on the
+ * tcgen05 tensor cores (TMA-fed implicit GEMM, accumulators in tensor memory) with pooling,
+ * upsampling additions and the head fused into the convolutions; GABP_WSNET_MMA_SYNC runs the
+ * mma.sync kernels that the backward pass uses.  Both compute the same network in BF16 with FP32
+ * accumulation (results differ by rounding order only).  GABP_ERR_ARG for another value. */
+#define GABP_WSNET_TCGEN05 0
+#define GABP_WSNET_MMA_SYNC 1
+int gabp_wsnet_set_kernels(gabp_wsnet *net, int kernels);
 /* Forward pass: x [B][H][W][16] BF16, out [B][H][W][2] FP32 (host or device); H, W multiples of 8. */
 int gabp_wsnet_forward(gabp_wsnet *net, const void *x, int B, int H, int W, float *out);
 /* Loss (mean over pixels of the squared errors of both outputs) and its gradient w.r.t. every

@@ -28,6 +28,7 @@ __all__ = [
     "gabp_batch_get_stats", "gabp_batch_strip_height", "gabp_batch_destroy",
     "gabp_wsnet_create", "gabp_wsnet_param_count", "gabp_wsnet_get_params", "gabp_wsnet_set_params",
     "gabp_wsnet_forward", "gabp_wsnet_gradients", "gabp_wsnet_train_step", "gabp_wsnet_destroy",
+    "gabp_wsnet_set_kernels", "GABP_WSNET_TCGEN05", "GABP_WSNET_MMA_SYNC",
     "gabp_wsnet_input_shape", "gabp_wsnet_sample", "gabp_batch_input_shape", "gabp_batch_wsnet_sample",
     "gabp_wsnet_warm_start", "Solver", "Batch", "WarmStartNet", "GabpError",
 ]
@@ -275,6 +276,14 @@ def gabp_wsnet_get_params(net: int, out) -> None:
 
 def gabp_wsnet_set_params(net: int, params) -> None:
     _wcheck(_lib.load().gabp_wsnet_set_params(net, _ptr(params)), net)
+
+
+GABP_WSNET_TCGEN05 = 0
+GABP_WSNET_MMA_SYNC = 1
+
+
+def gabp_wsnet_set_kernels(net: int, kernels: int) -> None:
+    _wcheck(_lib.load().gabp_wsnet_set_kernels(net, kernels), net)
 
 
 def gabp_wsnet_forward(net: int, x, B: int, H: int, W: int, out) -> None:

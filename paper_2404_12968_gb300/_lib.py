@@ -135,6 +135,8 @@ def load():
     L.gabp_wsnet_get_params.restype = ctypes.c_int
     L.gabp_wsnet_set_params.argtypes = [_vp, _vp]
     L.gabp_wsnet_set_params.restype = ctypes.c_int
+    L.gabp_wsnet_set_kernels.argtypes = [_vp, ctypes.c_int]
+    L.gabp_wsnet_set_kernels.restype = ctypes.c_int
     L.gabp_wsnet_forward.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]
     L.gabp_wsnet_forward.restype = ctypes.c_int
     L.gabp_wsnet_gradients.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int,

@@ -1127,9 +1127,14 @@ int gabp_wsnet_warm_start(gabp_ctx *c, gabp_wsnet *net) {
     rc = gabp::wsnet_forward_device(net, c->ws_x, 1, Hp, Wp, &out, c->stream, err);
     if (rc) return fail(c, rc, "network forward: " + err);
     const int64_t n = c->p.n;
-    CK(gabp::launch_ws_decode(c->p, c->yscale, Wp, out, c->stage, c->stage + n, c->stream), "decode");
-    CK(gabp::launch_init_warm(c->p, 0, c->stage, c->stage + n, c->stream), "warm init kernels");
+    if (c->p.prec == 0) {   // FP32 messages: decode and initialise in FP32 (stage holds n float2)
+        CK(gabp::launch_ws_init_f32(c->p, 0, c->yscale, Wp, out, (float2 *)c->stage, c->stream), "warm init kernels");
+    } else {
+        CK(gabp::launch_ws_decode(c->p, c->yscale, Wp, out, c->stage, c->stage + n, c->stream), "decode");
+        CK(gabp::launch_init_warm(c->p, 0, c->stage, c->stage + n, c->stream), "warm init kernels");
+    }
     CK(cudaStreamSynchronize(c->stream), "warm start sync");
+    if (gabp::wsnet_take_device_error(net)) return fail(c, GABP_ERR_TIMEOUT, "network kernel wait ran out");
     c->cur = 0;
     c->iters = 0;
     c->last_res = NAN;

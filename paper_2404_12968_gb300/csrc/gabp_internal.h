@@ -65,6 +65,10 @@ cudaError_t launch_marginals(const DevProblem &p, int src, double *mean, double 
 // ---- learned warm start (gabp_split.cu kernels, network in gabp_wsnet.cu) ----
 cudaError_t launch_ws_input(const DevProblem &p, double scale, double kappa, int Hp, int Wp, void *x, cudaStream_t st);
 cudaError_t launch_ws_target(const DevProblem &p, int src, double scale, int Hp, int Wp, float *t, cudaStream_t st);
+// FP32 contexts: decode the network output and initialise the messages (dst buffer) in FP32;
+// nm: n float2 scratch
+cudaError_t launch_ws_init_f32(const DevProblem &p, int dst, double scale, int Wp, const float *out, float2 *nm,
+                               cudaStream_t st);
 cudaError_t launch_ws_decode(const DevProblem &p, double scale, int Wp, const float *out, double *mu0, double *lam0,
                              cudaStream_t st);
 
@@ -106,4 +110,5 @@ namespace gabp {
 int wsnet_forward_device(gabp_wsnet *net, const void *x, int B, int H, int W, float **out, cudaStream_t st,
                          std::string &err);
 int wsnet_device(const gabp_wsnet *net);
+int wsnet_take_device_error(gabp_wsnet *net);
 }  // namespace gabp

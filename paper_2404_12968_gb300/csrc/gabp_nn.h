@@ -29,6 +29,32 @@ struct WgradArgs {
 };
 
 cudaError_t conv(const ConvArgs &a, cudaStream_t st);
+
+// Forward convolution on the tcgen05 tensor cores (gabp_nn_tc.cu): out = act(conv(in, w) + bias)
+// with optional fused 2x2 average pooling, nearest upsampling plus skip, and 1x1 FP32 head.
+// Input [B][H][W][Cin] BF16 (given separately, read through a TMA tensor map); Cin a multiple
+// of 16, Cout 32, 64, 128 or 256; H and W even when pooling.  The weights are prepacked by
+// tc_pack_weights.
+struct TcConvArgs {
+    const __nv_bfloat16 *wpk;     // packed weights (tc_pack_weights)
+    const float *bias;            // [Cout]
+    __nv_bfloat16 *out;           // [B][H][W][Cout], or NULL
+    __nv_bfloat16 *pool_out;      // 2x2 average of out, [B][H/2][W/2][Cout], or NULL
+    const __nv_bfloat16 *up_skip; // [B][2H][2W][Cout] (with up_out)
+    __nv_bfloat16 *up_out;        // nearest-upsampled out + up_skip, [B][2H][2W][Cout], or NULL
+    const float *head_w;          // [2][Cout] FP32 head (Cout = 32), or NULL
+    const float *head_b;          // [2]
+    float *head_out;              // [B][H][W][2] FP32
+    int *err;                     // device flag, set if a bounded wait ran out
+    int B, H, W, Cin, Cout, T, relu;
+    // set by tc_conv
+    int stages, nblocks, tiles_x, tiles_y, resident;
+    int64_t ntiles;
+};
+int tc_block_n(int Cout);
+// packed[nb][kb][t][h][n][e] = w[nb * N + n][t][16 kb + 8 h + e], N = tc_block_n(Cout)
+cudaError_t tc_pack_weights(const __nv_bfloat16 *w, int Cout, int T, int Cin, __nv_bfloat16 *out, cudaStream_t st);
+cudaError_t tc_conv(const __nv_bfloat16 *in, TcConvArgs a, cudaStream_t st);
 int64_t wgrad_chunks(const WgradArgs &a);
 cudaError_t conv_wgrad(WgradArgs a, float *dw, cudaStream_t st);
 cudaError_t bias_grad(const __nv_bfloat16 *g, int64_t P, int C, float *db, cudaStream_t st);

@@ -362,11 +362,14 @@ template <typename T> __global__ void k_marg(DevProblem p, double *mean, double 
 // mask of such nodes, log(kappa) + 3, zeros.  The nearest node of an observation is the corner
 // of its base cell nearest to it along each axis, found from the fractions fu = w1 + w3 and
 // fv = w2 + w3 (a fraction of exactly 0.5 goes to the higher index).
-__global__ void k_ws_input(DevProblem p, double inv_scale, float kfeat, int Hp, int Wp, __nv_bfloat16 *x) {
+template <typename T>
+__global__ void k_ws_input(DevProblem p, T inv_scale, float kfeat, int Hp, int Wp, __nv_bfloat16 *x) {
     const int64_t q = gtid();
     if (q >= (int64_t)Hp * Wp) return;
     const int i = (int)(q / Wp), j = (int)(q - (int64_t)i * Wp);
-    double sum = 0.0;
+    const T *ow = (const T *)p.ow;    // 4 weights per observation
+    const T *oyv = (const T *)p.ovar; // (y, variance) per observation
+    T sum = T(0);
     int cnt = 0;
     if (i < p.ny && j < p.nx && p.m > 0) {
         const int nx = p.nx;
@@ -376,21 +379,24 @@ __global__ void k_ws_input(DevProblem p, double inv_scale, float kfeat, int Hp, 
         for (int c = 0; c < 4; ++c) {
             if (!ok[c]) continue;
             for (int k = p.optr[bases[c]]; k < p.optr[bases[c] + 1]; ++k) {
-                const double *w = p.ow64 + 4 * (int64_t)k;
-                const int near = (w[1] + w[3] >= 0.5 ? 1 : 0) + (w[2] + w[3] >= 0.5 ? 2 : 0);
+                const T *w = ow + 4 * (int64_t)k;
+                const int near = (w[1] + w[3] >= T(0.5) ? 1 : 0) + (w[2] + w[3] >= T(0.5) ? 2 : 0);
                 if (near == c) {
-                    sum += p.oys64[2 * (int64_t)k];
+                    sum += oyv[2 * (int64_t)k];
                     ++cnt;
                 }
             }
         }
     }
-    __nv_bfloat16 *o = x + q * 16;
-    o[0] = __float2bfloat16(cnt ? (float)(sum / cnt * inv_scale) : 0.f);
+    __align__(16) __nv_bfloat16 o[16];
+    o[0] = __float2bfloat16(cnt ? (float)(sum / T(cnt) * inv_scale) : 0.f);
     o[1] = __float2bfloat16(cnt ? 1.f : 0.f);
     o[2] = __float2bfloat16(kfeat);
 #pragma unroll
     for (int c = 3; c < 16; ++c) o[c] = __float2bfloat16(0.f);
+    uint4 *dst = reinterpret_cast<uint4 *>(x + q * 16);
+    dst[0] = reinterpret_cast<const uint4 *>(o)[0];
+    dst[1] = reinterpret_cast<const uint4 *>(o)[1];
 }
 
 // t[i][j] = (mu / scale, log Lambda) of the current beliefs (after k_beliefs); zeros in the pad
@@ -410,6 +416,39 @@ template <typename T> __global__ void k_ws_target(DevProblem p, double inv_scale
 }
 
 // initial beliefs from the network output: mu0 = scale * out0, lam0 = exp(out1) clamped
+// FP32 contexts: per node, the initial message pair (mu0 L, L) with L = lam0 / (number of factor
+// slots at the node), decoded from the network output (mu0 = scale * out0, lam0 = exp(out1)
+// with out1 clamped to [-10, 15]); the message planes are then gathered from it.
+__global__ void k_ws_node_msg(DevProblem p, float scale, int Wp, const float *out, float2 *nm) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+    const int64_t q = (int64_t)i * Wp + j;
+    const float lg = fminf(fmaxf(out[2 * q + 1], -10.f), 15.f);
+    const float L = expf(lg) / (float)node_slots(p, v);
+    nm[v] = make_float2(scale * out[2 * q] * L, L);
+}
+__global__ void k_init_nodes_prior(DevProblem p, int dst, const float2 *nm) {
+    const int64_t c = gtid();
+    if (c >= p.n) return;
+    const int nx = p.nx, ny = p.ny;
+    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    const bool exists[5] = {true, j > 0, j < nx - 1, i > 0, i < ny - 1};
+    const int64_t node[5] = {c, c - 1, c + 1, c - nx, c + nx};
+    float2 *Q = (float2 *)p.P[dst];
+#pragma unroll
+    for (int u = 0; u < 5; ++u) Q[u * p.n + c] = exists[u] ? nm[node[u]] : make_float2(0.f, 0.f);
+}
+__global__ void k_init_nodes_obs(DevProblem p, int dst, const float2 *nm) {
+    const int64_t k = gtid();
+    if (k >= p.m) return;
+    const int64_t b = p.obase[k];
+    const float2 m0 = nm[b], m1 = nm[b + 1], m2 = nm[b + p.nx], m3 = nm[b + p.nx + 1];
+    float4 *Q = (float4 *)((float *)p.O[dst] + 8 * k);
+    Q[0] = make_float4(m0.x, m1.x, m2.x, m3.x);
+    Q[1] = make_float4(m0.y, m1.y, m2.y, m3.y);
+}
+
 __global__ void k_ws_decode(DevProblem p, double scale, int Wp, const float *out, double *mu0, double *lam0) {
     const int64_t v = gtid();
     if (v >= p.n) return;
@@ -491,8 +530,12 @@ cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st) {
 
 cudaError_t launch_ws_input(const DevProblem &p, double scale, double kappa, int Hp, int Wp, void *x,
                             cudaStream_t st) {
-    k_ws_input<<<nblocks((int64_t)Hp * Wp), TPB, 0, st>>>(p, 1.0 / scale, (float)(std::log(kappa) + 3.0), Hp, Wp,
-                                                          (__nv_bfloat16 *)x);
+    const float kf = (float)(std::log(kappa) + 3.0);
+    if (p.prec)
+        k_ws_input<double><<<nblocks((int64_t)Hp * Wp), TPB, 0, st>>>(p, 1.0 / scale, kf, Hp, Wp, (__nv_bfloat16 *)x);
+    else
+        k_ws_input<float><<<nblocks((int64_t)Hp * Wp), TPB, 0, st>>>(p, (float)(1.0 / scale), kf, Hp, Wp,
+                                                                     (__nv_bfloat16 *)x);
     return cudaGetLastError();
 }
 
@@ -501,6 +544,15 @@ cudaError_t launch_ws_target(const DevProblem &p, int src, double scale, int Hp,
     if (e != cudaSuccess) return e;
     if (p.prec) k_ws_target<double><<<nblocks((int64_t)Hp * Wp), TPB, 0, st>>>(p, 1.0 / scale, Hp, Wp, t);
     else k_ws_target<float><<<nblocks((int64_t)Hp * Wp), TPB, 0, st>>>(p, 1.0 / scale, Hp, Wp, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ws_init_f32(const DevProblem &p, int dst, double scale, int Wp, const float *out, float2 *nm,
+                               cudaStream_t st) {
+    if (p.prec) return cudaErrorInvalidValue;
+    k_ws_node_msg<<<nblocks(p.n), TPB, 0, st>>>(p, (float)scale, Wp, out, nm);
+    k_init_nodes_prior<<<nblocks(p.n), TPB, 0, st>>>(p, dst, nm);
+    if (p.m > 0) k_init_nodes_obs<<<nblocks(p.m), TPB, 0, st>>>(p, dst, nm);
     return cudaGetLastError();
 }
 

@@ -53,6 +53,11 @@ struct gabp_wsnet {
     float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;   // FP32 master, Adam, grads
     __nv_bfloat16 *w16 = nullptr;    // BF16 copy (the flat vector, converted)
     __nv_bfloat16 *wt = nullptr;     // flipped/transposed weights scratch (largest layer)
+    __nv_bfloat16 *wpk = nullptr;    // weights packed for the tensor-core forward (same offsets)
+    bool packed = false;             // wpk matches w16
+    int *derr = nullptr;             // device flag of the tensor-core kernels (a bounded wait ran out)
+    int kernels = GABP_WSNET_TCGEN05;
+    const __nv_bfloat16 *xin = nullptr;   // caller's input, read in place by the tensor-core forward
     int step = 0;
     // activation buffers for the current shape
     int B = 0, H = 0, W = 0;
@@ -182,7 +187,71 @@ int conv_fwd(gabp_wsnet *net, int l, const Buf &in, const Buf *skip, Buf &out, i
     return GABP_OK;
 }
 
+// Forward on the tcgen05 tensor-core convolutions, with the pooling, the upsampling additions
+// and the head fused into the convolutions' epilogues.  Buffers that only the backward pass
+// reads (r2, r1, r0, d0) are written when gradients are wanted.
+int forward_tc(gabp_wsnet *net) {
+    const int B = net->B, H = net->H, W = net->W;
+    cudaStream_t st = net->stream;
+    if (!net->packed) {
+        for (int l = 0; l < NLAYER; ++l)
+            WK(gabp::nn::tc_pack_weights(net->w16 + net->woff[l], SPECS[l].cout, SPECS[l].taps, SPECS[l].cin,
+                                         net->wpk + net->woff[l], st),
+               "pack weights");
+        net->packed = true;
+    }
+    const bool keep = net->grads;
+    auto L = [&](int l, const Buf &in, int h, int w, Buf *out, Buf *pool, const Buf *up_skip, Buf *up,
+                 bool head) -> int {
+        gabp::nn::TcConvArgs a{};
+        a.wpk = net->wpk + net->woff[l];
+        a.bias = net->w + net->boff[l];
+        a.out = out ? out->p : nullptr;
+        a.pool_out = pool ? pool->p : nullptr;
+        a.up_skip = up_skip ? up_skip->p : nullptr;
+        a.up_out = up ? up->p : nullptr;
+        if (head) {
+            a.head_w = net->w + net->head_off;
+            a.head_b = net->w + net->head_off + 2 * HEAD_C;
+            a.head_out = net->out;
+        }
+        a.err = net->derr;
+        a.B = B;
+        a.H = h;
+        a.W = w;
+        a.Cin = SPECS[l].cin;
+        a.Cout = SPECS[l].cout;
+        a.T = SPECS[l].taps;
+        a.relu = SPECS[l].relu;
+        WK(gabp::nn::tc_conv(in.p, a, st), "tensor-core convolution");
+        return GABP_OK;
+    };
+    int rc;
+#define F(...) \
+    if ((rc = L(__VA_ARGS__))) return rc
+    Buf xin;
+    xin.p = const_cast<__nv_bfloat16 *>(net->xin ? net->xin : net->x.p);
+    xin.n = net->x.n;
+    F(0, xin, H, W, &net->a0, nullptr, nullptr, nullptr, false);
+    F(1, net->a0, H, W, &net->s0, &net->p0, nullptr, nullptr, false);
+    F(2, net->p0, H / 2, W / 2, &net->a1, nullptr, nullptr, nullptr, false);
+    F(3, net->a1, H / 2, W / 2, &net->s1, &net->p1, nullptr, nullptr, false);
+    F(4, net->p1, H / 4, W / 4, &net->a2, nullptr, nullptr, nullptr, false);
+    F(5, net->a2, H / 4, W / 4, &net->s2, &net->p2, nullptr, nullptr, false);
+    F(6, net->p2, H / 8, W / 8, &net->a3, nullptr, nullptr, nullptr, false);
+    F(7, net->a3, H / 8, W / 8, &net->b3, nullptr, nullptr, nullptr, false);
+    F(8, net->b3, H / 8, W / 8, keep ? &net->r2 : nullptr, nullptr, &net->s2, &net->u2, false);
+    F(9, net->u2, H / 4, W / 4, &net->d2, nullptr, nullptr, nullptr, false);
+    F(10, net->d2, H / 4, W / 4, keep ? &net->r1 : nullptr, nullptr, &net->s1, &net->u1, false);
+    F(11, net->u1, H / 2, W / 2, &net->d1, nullptr, nullptr, nullptr, false);
+    F(12, net->d1, H / 2, W / 2, keep ? &net->r0 : nullptr, nullptr, &net->s0, &net->u0, false);
+    F(13, net->u0, H, W, keep ? &net->d0 : nullptr, nullptr, nullptr, nullptr, true);
+#undef F
+    return GABP_OK;
+}
+
 int forward(gabp_wsnet *net) {
+    if (net->kernels == GABP_WSNET_TCGEN05) return forward_tc(net);
     const int B = net->B, H = net->H, W = net->W;
     cudaStream_t st = net->stream;
     int rc;
@@ -321,13 +390,18 @@ int wsnet_forward_device(gabp_wsnet *net, const void *x, int B, int H, int W, fl
     }
     cudaStream_t keep = net->stream;
     net->stream = st;
-    cudaError_t e = cudaMemcpyAsync(net->x.p, x, sizeof(__nv_bfloat16) * net->x.n, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) {
-        net->stream = keep;
-        err = cudaGetErrorString(e);
-        return GABP_ERR_CUDA;
+    if (net->kernels == GABP_WSNET_TCGEN05) {
+        net->xin = (const __nv_bfloat16 *)x;   // the first convolution reads the input in place
+    } else {
+        cudaError_t e = cudaMemcpyAsync(net->x.p, x, sizeof(__nv_bfloat16) * net->x.n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) {
+            net->stream = keep;
+            err = cudaGetErrorString(e);
+            return GABP_ERR_CUDA;
+        }
     }
     rc = forward(net);
+    net->xin = nullptr;
     net->stream = keep;
     if (rc) err = net->err;
     *out = net->out;
@@ -335,6 +409,14 @@ int wsnet_forward_device(gabp_wsnet *net, const void *x, int B, int H, int W, fl
 }
 
 int wsnet_device(const gabp_wsnet *net) { return net->dev; }
+
+// After a synchronisation: 1 if a tensor-core kernel's bounded wait ran out (flag cleared).
+int wsnet_take_device_error(gabp_wsnet *net) {
+    int h = 0;
+    if (cudaMemcpy(&h, net->derr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return 1;
+    if (h) cudaMemset(net->derr, 0, sizeof(int));
+    return h ? 1 : 0;
+}
 
 }  // namespace gabp
 
@@ -393,6 +475,9 @@ int gabp_wsnet_create(gabp_wsnet **out, uint64_t seed, int device) {
     if (e == cudaSuccess) e = cudaMalloc((void **)&net->g, sizeof(float) * off);
     if (e == cudaSuccess) e = cudaMalloc((void **)&net->w16, sizeof(__nv_bfloat16) * off);
     if (e == cudaSuccess) e = cudaMalloc((void **)&net->wt, sizeof(__nv_bfloat16) * maxw);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&net->wpk, sizeof(__nv_bfloat16) * off);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&net->derr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(net->derr, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(net->w, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(net->m, 0, sizeof(float) * off);
     if (e == cudaSuccess) e = cudaMemset(net->v, 0, sizeof(float) * off);
@@ -420,7 +505,14 @@ int gabp_wsnet_set_params(gabp_wsnet *net, const float *params) {
     if (!net || !params) return GABP_ERR_ARG;
     WK(cudaMemcpy(net->w, params, sizeof(float) * net->nparam, cudaMemcpyDefault), "copy params");
     WK(gabp::nn::to_bf16(net->w, net->w16, net->nparam, net->stream), "to bf16");
+    net->packed = false;
     WK(cudaStreamSynchronize(net->stream), "sync");
+    return GABP_OK;
+}
+
+int gabp_wsnet_set_kernels(gabp_wsnet *net, int kernels) {
+    if (!net || (kernels != GABP_WSNET_TCGEN05 && kernels != GABP_WSNET_MMA_SYNC)) return GABP_ERR_ARG;
+    net->kernels = kernels;
     return GABP_OK;
 }
 
@@ -433,6 +525,7 @@ int gabp_wsnet_forward(gabp_wsnet *net, const void *x, int B, int H, int W, floa
     if ((rc = forward(net))) return rc;
     WK(cudaMemcpyAsync(out, net->out, sizeof(float) * 2 * B * H * W, cudaMemcpyDefault, net->stream), "copy output");
     WK(cudaStreamSynchronize(net->stream), "sync");
+    if (gabp::wsnet_take_device_error(net)) return wfail(net, GABP_ERR_TIMEOUT, "a tensor-core kernel wait ran out");
     return GABP_OK;
 }
 
@@ -485,6 +578,7 @@ int gabp_wsnet_train_step(gabp_wsnet *net, const void *const *xs, const float *c
     WK(gabp::nn::adam(net->w, net->m, net->v, net->g, net->nparam, lr, 0.9f, 0.999f, 1e-8f, net->step, net->w16,
                       net->stream),
        "adam");
+    net->packed = false;
     WK(cudaStreamSynchronize(net->stream), "sync");
     return GABP_OK;
 }
@@ -504,6 +598,8 @@ void gabp_wsnet_destroy(gabp_wsnet *net) {
     cudaFree(net->g);
     cudaFree(net->w16);
     cudaFree(net->wt);
+    cudaFree(net->wpk);
+    cudaFree(net->derr);
     if (net->stream) cudaStreamDestroy(net->stream);
     if (prev >= 0) cudaSetDevice(prev);
     delete net;

@@ -90,6 +90,35 @@ def test_network_forward_and_gradients_match_reference():
     net.close()
 
 
+@pytest.mark.parametrize("B,H,W", [(2, 40, 72), (1, 64, 64), (3, 16, 24)])
+def test_tensor_core_forward_matches_mma_sync_forward(B, H, W):
+    """The tcgen05 forward (fused pooling, upsampling additions and head) against the mma.sync
+    forward of the same network: the same BF16 arithmetic up to the accumulation order.  The
+    shapes give partial 16 x 8 tiles at every level, several output-channel blocks (Cout 256),
+    and batches."""
+    torch = pytest.importorskip("torch")
+    from oracle import unet
+    from paper_2404_12968_gb300 import (GABP_WSNET_MMA_SYNC, GABP_WSNET_TCGEN05, WarmStartNet, gabp_wsnet_forward,
+                                        gabp_wsnet_set_kernels)
+    net = WarmStartNet(seed=5, device=0)
+    rng = np.random.default_rng(6)
+    _, _, total = unet.layout()
+    net.set_params((net.params() + rng.normal(size=total) * 0.02).astype(np.float32))
+    _, _, xs, _ = _case(torch, H, W, B, seed=9)
+    xb = torch.stack(xs).contiguous()
+    outs = {}
+    for k in (GABP_WSNET_TCGEN05, GABP_WSNET_MMA_SYNC):
+        gabp_wsnet_set_kernels(net.handle, k)
+        o = np.empty((B, H, W, 2), np.float32)
+        gabp_wsnet_forward(net.handle, xb, B, H, W, o)
+        outs[k] = o
+    a, b = outs[GABP_WSNET_TCGEN05], outs[GABP_WSNET_MMA_SYNC]
+    assert np.all(np.isfinite(a))
+    rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel < 1e-2, rel
+    net.close()
+
+
 def test_training_reduces_loss():
     torch = pytest.importorskip("torch")
     from paper_2404_12968_gb300 import WarmStartNet, gabp_wsnet_train_step
