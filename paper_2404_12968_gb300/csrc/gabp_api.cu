@@ -292,7 +292,14 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     p.debug_stall = (o.debug_flags & 1) ? 1 : 0;
     for (int d = 0; d <= 4; ++d) p.aC[d] = kappa * kappa + (double)d;
     p.var_f = (float)(1.0 / gamma);
-    for (int d = 0; d <= 4; ++d) p.aC_f[d] = (float)p.aC[d];
+    for (int d = 0; d <= 4; ++d) {
+        p.aC_f[d] = (float)p.aC[d];
+        p.aC_lo[d] = (float)(p.aC[d] - (double)p.aC_f[d]);
+    }
+    p.gam_hi = (float)gamma;
+    p.gam_lo = (float)(gamma - (double)p.gam_hi);
+    p.owdf = nullptr;
+    p.oysdf = nullptr;
     const size_t T = tsize(c);
     int rc;
     void *q;
@@ -310,6 +317,12 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     p.ow64 = (const double *)q;
     if ((rc = dalloc(c, &q, 2 * (size_t)m * sizeof(double), "alloc obs values fp64"))) return rc;
     p.oys64 = (const double *)q;
+    if (p.prec == 0) {   // double-float copies for the FP32 contexts' residual
+        if ((rc = dalloc(c, &q, 4 * (size_t)m * sizeof(float2), "alloc obs weights double-float"))) return rc;
+        p.owdf = (const float2 *)q;
+        if ((rc = dalloc(c, &q, 2 * (size_t)m * sizeof(float2), "alloc obs values double-float"))) return rc;
+        p.oysdf = (const float2 *)q;
+    }
     if ((rc = dalloc(c, &q, ((size_t)n + 1) * sizeof(int), "alloc obs pointers"))) return rc;
     p.optr = (const int *)q;
     if ((rc = dalloc(c, &p.belief, (size_t)n * 4 * T, "alloc beliefs"))) return rc;
@@ -340,6 +353,7 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
         if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 3 * m, svar.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync((void *)p.obase, sbase.data(), (size_t)m * sizeof(int), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = gabp::launch_obs_precompute(p, raw, raw + 2 * m, raw + 3 * m, c->stream);
+        if (e == cudaSuccess && p.prec == 0) e = gabp::launch_df_precompute(p, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         cudaFree(raw);
         if (e != cudaSuccess) return cuda_fail(c, e, "observation upload/precompute");

@@ -18,6 +18,10 @@ struct DevProblem {
     double aC[5];        // kappa^2 + deg for deg = 0..4 (FP64)
     float var_f;         // (float)(1 / gamma), rounded once on the host
     float aC_f[5];       // (float)aC[d]
+    float aC_lo[5];      // aC[d] - aC_f[d] rounded: aC[d] as a double-float pair (aC_f, aC_lo)
+    float gam_hi, gam_lo;   // gamma as a double-float pair
+    const float2 *owdf;  // FP32 contexts: 4 * m observation weights as double-float (hi, lo) pairs
+    const float2 *oysdf; // FP32 contexts: 2 * m (y, 1/sigma^2) as double-float pairs
     void *P[2];          // prior messages, ping-pong: 5 * n (eta, Lambda) pairs
     void *O[2];          // observation messages, ping-pong: 8 * m values
     const int *obase;    // m base-cell indices (sorted ascending)
@@ -69,6 +73,8 @@ cudaError_t launch_ws_target(const DevProblem &p, int src, double scale, int Hp,
 // nm: n float2 scratch
 cudaError_t launch_ws_init_f32(const DevProblem &p, int dst, double scale, int Wp, const float *out, float2 *nm,
                                cudaStream_t st);
+// FP32 contexts: double-float (hi, lo) copies of the FP64 observation weights and (y, 1/sigma^2)
+cudaError_t launch_df_precompute(const DevProblem &p, cudaStream_t st);
 cudaError_t launch_ws_decode(const DevProblem &p, double scale, int Wp, const float *out, double *mu0, double *lam0,
                              cudaStream_t st);
 

@@ -297,6 +297,128 @@ __global__ void k_rhs_norm(DevProblem p) {
     if (threadIdx.x == 0) p.part[blockIdx.x] = s;
 }
 
+// ---- the residual of FP32 contexts in double-float arithmetic ----
+// A value is an unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2), about 48 significant
+// bits.  Error-free transformations: TwoSum (Knuth), Fast2Sum (Dekker, |a| >= |b|) and the
+// product error by fused multiply-add; every operation is explicitly rounded.  It replaces FP64
+// arithmetic, whose throughput on this GPU is a small fraction of FP32's.
+struct dfl {
+    float hi, lo;
+};
+__device__ __forceinline__ dfl df_fast2sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+    const float s = __fadd_rn(x.hi, y.hi);
+    const float bb = __fsub_rn(s, x.hi);
+    const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+    return df_fast2sum(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dfl df_neg(dfl x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return df_fast2sum(p, e);
+}
+__device__ __forceinline__ dfl df_ld(const float2 *a, int64_t i) {
+    const float2 v = a[i];
+    return {v.x, v.y};
+}
+__device__ __forceinline__ void df_st(float2 *a, int64_t i, dfl x) { a[i] = make_float2(x.hi, x.lo); }
+__device__ __forceinline__ dfl df_split(double d) {
+    const float h = __double2float_rn(d);
+    return {h, __double2float_rn(d - (double)h)};
+}
+
+__global__ void k_df_precompute(DevProblem p) {
+    const int64_t k = gtid();
+    if (k >= p.m) return;
+    float2 *w = (float2 *)p.owdf;
+    float2 *ys = (float2 *)p.oysdf;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) df_st(w, 4 * k + c, df_split(p.ow64[4 * k + c]));
+    df_st(ys, 2 * k, df_split(p.oys64[2 * k]));
+    df_st(ys, 2 * k + 1, df_split(p.oys64[2 * k + 1]));
+}
+
+// mu = eta / Lambda from the compensated FP32 belief (hi + lo pairs): quotient of the leading
+// parts, one correction with the exact remainder eta - Lambda q1
+__global__ void k_mu_df(DevProblem p) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const BeliefStore<float> b = ((const BeliefStore<float> *)p.belief)[v];
+    const dfl eta = {b.ehi, b.elo}, lam = {b.lhi, b.llo};
+    const float q1 = __fdiv_rn(eta.hi, lam.hi);
+    const dfl r = df_add(eta, df_neg(df_mul(lam, {q1, 0.f})));
+    const float q2 = __fdiv_rn(r.hi, lam.hi);
+    df_st((float2 *)p.mu64, v, df_fast2sum(q1, q2));
+}
+
+// e_k = s_k (h_k . mu - y_k)
+__global__ void k_obs_err_df(DevProblem p) {
+    const int64_t k = gtid();
+    if (k >= p.m) return;
+    const int64_t b = p.obase[k];
+    const float2 *mu = (const float2 *)p.mu64;
+    const int64_t nodes[4] = {b, b + 1, b + p.nx, b + p.nx + 1};
+    dfl hm = df_mul(df_ld(p.owdf, 4 * k), df_ld(mu, nodes[0]));
+#pragma unroll
+    for (int c = 1; c < 4; ++c) hm = df_add(hm, df_mul(df_ld(p.owdf, 4 * k + c), df_ld(mu, nodes[c])));
+    const dfl e = df_mul(df_ld(p.oysdf, 2 * k + 1), df_add(hm, df_neg(df_ld(p.oysdf, 2 * k))));
+    df_st((float2 *)p.e64, k, e);
+}
+
+// (L x)_v with the zero-Neumann stencil: (kappa^2 + deg) x_v - sum of the existing neighbours
+__device__ __forceinline__ dfl apply_L_df(const DevProblem &p, const float2 *x, int64_t v, int i, int j) {
+    const int nx = p.nx, ny = p.ny;
+    const int d = grid_degree(i, j, nx, ny);
+    dfl s = df_mul({p.aC_f[d], p.aC_lo[d]}, df_ld(x, v));
+    if (j > 0) s = df_add(s, df_neg(df_ld(x, v - 1)));
+    if (j < nx - 1) s = df_add(s, df_neg(df_ld(x, v + 1)));
+    if (i > 0) s = df_add(s, df_neg(df_ld(x, v - nx)));
+    if (i < ny - 1) s = df_add(s, df_neg(df_ld(x, v + nx)));
+    return s;
+}
+
+__global__ void k_Lmu_df(DevProblem p) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+    df_st((float2 *)p.z64, v, apply_L_df(p, (const float2 *)p.mu64, v, i, j));
+}
+
+// partial sums of r_v^2, r = b - A mu = -gamma L (L mu) - H^T (s (H mu - y)); per-thread sums in
+// double-float, then the same fixed-order FP64 block reduction as the FP64 path
+__global__ void k_res_df(DevProblem p) {
+    dfl acc = {0.f, 0.f};
+    const int64_t stride = (int64_t)gridDim.x * TPB;
+    const float2 *e = (const float2 *)p.e64;
+    const int *o = p.optr;
+    const int nx = p.nx;
+    for (int64_t v = gtid(); v < p.n; v += stride) {
+        const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
+        dfl r = df_neg(df_mul({p.gam_hi, p.gam_lo}, apply_L_df(p, (const float2 *)p.z64, v, i, j)));
+        if (p.m > 0) {
+            for (int k = o[v]; k < o[v + 1]; ++k) r = df_add(r, df_neg(df_mul(df_ld(p.owdf, 4 * (int64_t)k), df_ld(e, k))));
+            if (j > 0)
+                for (int k = o[v - 1]; k < o[v]; ++k)
+                    r = df_add(r, df_neg(df_mul(df_ld(p.owdf, 4 * (int64_t)k + 1), df_ld(e, k))));
+            if (i > 0)
+                for (int k = o[v - nx]; k < o[v - nx + 1]; ++k)
+                    r = df_add(r, df_neg(df_mul(df_ld(p.owdf, 4 * (int64_t)k + 2), df_ld(e, k))));
+            if (i > 0 && j > 0)
+                for (int k = o[v - nx - 1]; k < o[v - nx]; ++k)
+                    r = df_add(r, df_neg(df_mul(df_ld(p.owdf, 4 * (int64_t)k + 3), df_ld(e, k))));
+        }
+        acc = df_add(acc, df_mul(r, r));
+    }
+    double s = block_sum((double)acc.hi + (double)acc.lo);
+    if (threadIdx.x == 0) p.part[blockIdx.x] = s;
+}
+
 template <typename T> __global__ void k_mu(DevProblem p) {
     const int64_t v = gtid();
     if (v >= p.n) return;
@@ -516,9 +638,24 @@ cudaError_t launch_rhs_norm(const DevProblem &p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_df_precompute(const DevProblem &p, cudaStream_t st) {
+    if (p.m == 0 || p.prec) return cudaSuccess;
+    k_df_precompute<<<nblocks(p.m), TPB, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st) {
     cudaError_t e = launch_beliefs(p, src, st);
     if (e != cudaSuccess) return e;
+    if (p.prec == 0) {
+        // FP32 messages: the residual in double-float arithmetic (FP32 pipes, ~48-bit significands)
+        k_mu_df<<<nblocks(p.n), TPB, 0, st>>>(p);
+        if (p.m > 0) k_obs_err_df<<<nblocks(p.m), TPB, 0, st>>>(p);
+        k_Lmu_df<<<nblocks(p.n), TPB, 0, st>>>(p);
+        k_res_df<<<RES_BLOCKS, TPB, 0, st>>>(p);
+        k_final_sum<<<1, TPB, 0, st>>>(p.part, RES_BLOCKS, p.scal);
+        return cudaGetLastError();
+    }
     if (p.prec) k_mu<double><<<nblocks(p.n), TPB, 0, st>>>(p);
     else k_mu<float><<<nblocks(p.n), TPB, 0, st>>>(p);
     if (p.m > 0) k_obs_err<<<nblocks(p.m), TPB, 0, st>>>(p);
