@@ -270,6 +270,44 @@ const char *gabp_batch_last_error(const gabp_batch *b);
 void gabp_batch_destroy(gabp_batch *b);
 
 /* ---------------------------------------------------------------------------------------
+ * Multigrid warm start (Sec. 3.2 "Multigrid"; Alg. 2 "Multigrid MP" and "Upscale Messages").
+ * Level k = 1 .. levels-1 is the context's problem on a grid of spacing 2^k target cells:
+ * ceil(nx / 2^k) x ceil(ny / 2^k) nodes, kappa_k = 2^k kappa and gamma_k = gamma / 4^k (the
+ * same SPDE discretised at that spacing), every observation at (x / 2^k, y / 2^k) clamped to
+ * the level's last node, with its own value and noise variance.  From the coarsest level
+ * (cold start) up, each level runs GaBP; every node of the next finer level then takes the
+ * marginal (mean, precision) of its parent node (floor(i/2), floor(j/2)) and its messages are
+ * set as by gabp_warm_start.  Finally the target context is warm-started from level 1.  A level
+ * whose final relative residual is not finite or not below 1 is re-run from the same start
+ * with damping (1 + damping) / 2, up to three times; a level that still fails passes its own
+ * start on (or a cold start).
+ * --------------------------------------------------------------------------------------- */
+#define GABP_MG_MAX_LEVELS 16
+typedef struct gabp_mg gabp_mg;   /* opaque; owns the coarse levels' contexts */
+
+typedef struct {
+    int levels;                                  /* as created */
+    int64_t iterations[GABP_MG_MAX_LEVELS];      /* level k at [k] ([0] unused): GaBP iterations, all attempts */
+    double damping[GABP_MG_MAX_LEVELS];          /* damping of the level's last attempt */
+    double residual[GABP_MG_MAX_LEVELS];         /* the level's final relative residual */
+    int converged[GABP_MG_MAX_LEVELS];           /* 1 if the level's state was passed on */
+} gabp_mg_stats;
+
+/* Build the coarse levels of ctx's problem, 2 <= levels <= GABP_MG_MAX_LEVELS; every coarse level
+ * needs at least 2 nodes per axis (GABP_ERR_ARG otherwise).  The coarse contexts use ctx's
+ * precision, device and stream.  ctx must outlive the multigrid object.  Errors of this call are
+ * reported by gabp_last_error(ctx). */
+int gabp_mg_create(gabp_mg **out, gabp_ctx *ctx, int levels);
+
+/* Run the coarse levels and warm-start the target context (its iteration count restarts at 0).
+ * tol > 0: each level iterates until its relative residual is <= tol (checked every
+ * check_every iterations of ctx's options) or max_iters iterations; tol <= 0: exactly max_iters
+ * iterations per level.  damping in [0, 1), max_iters >= 1; stats may be NULL. */
+int gabp_mg_warm_start(gabp_mg *mg, double damping, double tol, int max_iters, gabp_mg_stats *stats);
+const char *gabp_mg_last_error(const gabp_mg *mg);
+void gabp_mg_destroy(gabp_mg *mg);
+
+/* ---------------------------------------------------------------------------------------
  * Learned warm start.  A small convolutional encoder-decoder (4 levels, 32 -> 256 channels,
  * BF16 weights and activations, FP32 accumulation) maps the gridded observations to initial
  * beliefs (mean, log precision); gabp_wsnet_warm_start() seeds a context's messages with them

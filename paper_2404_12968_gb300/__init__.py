@@ -31,6 +31,7 @@ __all__ = [
     "gabp_wsnet_set_kernels", "GABP_WSNET_TCGEN05", "GABP_WSNET_MMA_SYNC",
     "gabp_wsnet_input_shape", "gabp_wsnet_sample", "gabp_batch_input_shape", "gabp_batch_wsnet_sample",
     "gabp_wsnet_warm_start", "Solver", "Batch", "WarmStartNet", "GabpError",
+    "gabp_mg_create", "gabp_mg_warm_start", "gabp_mg_destroy", "Multigrid",
 ]
 
 
@@ -251,6 +252,57 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def gabp_mg_create(ctx: int, levels: int) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.load().gabp_mg_create(ctypes.byref(h), ctx, levels), ctx)
+    return h.value
+
+
+def gabp_mg_warm_start(mg: int, damping: float, tol: float, max_iters: int) -> dict:
+    """Run the coarse levels and warm-start the target context; per-level statistics."""
+    st = _lib.gabp_mg_stats()
+    rc = _lib.load().gabp_mg_warm_start(mg, damping, tol, max_iters, ctypes.byref(st))
+    if rc != GABP_OK:
+        raise GabpError(rc, (_lib.load().gabp_mg_last_error(mg) or b"").decode(errors="replace"))
+    L = st.levels
+    return {"levels": L, "iterations": [int(st.iterations[k]) for k in range(L)],
+            "damping": [float(st.damping[k]) for k in range(L)], "residual": [float(st.residual[k]) for k in range(L)],
+            "converged": [bool(st.converged[k]) for k in range(L)]}
+
+
+def gabp_mg_destroy(mg: int) -> None:
+    if mg:
+        _lib.load().gabp_mg_destroy(mg)
+
+
+class Multigrid:
+    """Coarse levels of a Solver's problem for the multigrid warm start (Sec. 3.2, Alg. 2).
+    The Solver must outlive it.  Entry k of the per-level lists is level k (0 unused)."""
+
+    def __init__(self, solver: "Solver", levels: int):
+        self.handle = gabp_mg_create(solver.ctx, levels)
+
+    def warm_start(self, damping: float = 0.3, tol: float = 1e-5, max_iters: int = 100000) -> dict:
+        return gabp_mg_warm_start(self.handle, damping, tol, max_iters)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gabp_mg_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _wcheck(rc: int, net):

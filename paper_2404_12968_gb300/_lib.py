@@ -54,6 +54,15 @@ class gabp_stats(ctypes.Structure):
                 ("tile_y", ctypes.c_int), ("bytes_per_iter", ctypes.c_double)]
 
 
+MG_MAX_LEVELS = 16
+
+
+class gabp_mg_stats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("iterations", ctypes.c_int64 * MG_MAX_LEVELS),
+                ("damping", ctypes.c_double * MG_MAX_LEVELS), ("residual", ctypes.c_double * MG_MAX_LEVELS),
+                ("converged", ctypes.c_int * MG_MAX_LEVELS)]
+
+
 class gabp_problem(ctypes.Structure):
     _fields_ = [("grid", gabp_grid), ("kappa", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("m", ctypes.c_int64), ("obs_xy", ctypes.c_void_p), ("y", ctypes.c_void_p),
@@ -91,6 +100,14 @@ def load():
     L.gabp_marginals.restype = ctypes.c_int
     L.gabp_residual.argtypes = [_vp, _dp]
     L.gabp_residual.restype = ctypes.c_int
+    L.gabp_mg_create.argtypes = [ctypes.POINTER(_vp), _vp, ctypes.c_int]
+    L.gabp_mg_create.restype = ctypes.c_int
+    L.gabp_mg_warm_start.argtypes = [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(gabp_mg_stats)]
+    L.gabp_mg_warm_start.restype = ctypes.c_int
+    L.gabp_mg_last_error.argtypes = [_vp]
+    L.gabp_mg_last_error.restype = ctypes.c_char_p
+    L.gabp_mg_destroy.argtypes = [_vp]
+    L.gabp_mg_destroy.restype = None
     L.gabp_warm_start.argtypes = [_vp, _vp, _vp]
     L.gabp_warm_start.restype = ctypes.c_int
     L.gabp_reset.argtypes = [_vp]

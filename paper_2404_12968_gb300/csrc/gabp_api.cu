@@ -41,6 +41,8 @@ struct gabp_ctx {
     double kappa = 0.0;
     double yscale = 1.0;          // spread of the observed values (network input scale)
     void *ws_x = nullptr;         // network input buffer (allocated on first use)
+    // host copy of the observations (sorted by base cell): the multigrid levels are built from it
+    std::vector<double> hxy, hy, hvar;
 };
 
 namespace {
@@ -387,6 +389,9 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     c->edges = 5 * n - 2 * (int64_t)(nx + ny) + 4 * m;
     const double ebytes = 4.0 * (double)T;    // (eta, Lambda) read + write per edge
     c->bytes_per_iter = ebytes * (double)c->edges + 5.0 * (double)T * (double)m;
+    c->hxy = std::move(sxy);
+    c->hy = std::move(sy);
+    c->hvar = std::move(svar);
     return GABP_OK;
 }
 
@@ -540,7 +545,13 @@ int gabp_warm_start(gabp_ctx *c, const double *mu0, const double *lam0) {
         CK(cudaMemcpyAsync(c->stage + n, lam0, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy lam0");
         dl = c->stage + n;
     }
-    CK(gabp::launch_init_warm(c->p, 0, dm, dl, c->stream), "warm init kernels");
+    if (c->p.prec == 0) {
+        // FP32 messages: FP32 arithmetic; the node pairs go to the staging buffer (each element
+        // is read before its slot is written when mu0 itself was staged there)
+        CK(gabp::launch_init_warm_f32(c->p, 0, dm, dl, (float2 *)c->stage, c->stream), "warm init kernels");
+    } else {
+        CK(gabp::launch_init_warm(c->p, 0, dm, dl, c->stream), "warm init kernels");
+    }
     CK(cudaStreamSynchronize(c->stream), "warm start sync");
     c->cur = 0;
     c->iters = 0;
@@ -1126,6 +1137,202 @@ int gabp_batch_wsnet_sample(gabp_batch *b, int index, void *x_out, float *t_out)
 int gabp_batch_input_shape(const gabp_batch *b, int index, int *H, int *W, double *scale) {
     if (!b || index < 0 || index >= (int)b->inst.size()) return GABP_ERR_ARG;
     return gabp_wsnet_input_shape(b->inst[index], H, W, scale);
+}
+
+// ---- multigrid warm start (Sec. 3.2 "Multigrid"; Alg. 2 "Multigrid MP", "Upscale Messages") ----
+}  // extern "C"
+
+struct gabp_mg {
+    gabp_ctx *target = nullptr;
+    int levels = 0;
+    std::vector<gabp_ctx *> lv;   // lv[k] = level k (k >= 1); lv[0] unused (the target)
+    double *mu[2] = {nullptr, nullptr}, *q[2] = {nullptr, nullptr};   // marginal buffers (target size)
+    std::string err;
+};
+
+namespace {
+
+int mfail(gabp_mg *g, int code, const std::string &msg) {
+    g->err = msg;
+    return code;
+}
+
+#define CK_MG(call, what)                                                                          \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            cudaGetLastError();                                                                    \
+            return mfail(g, GABP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e_));     \
+        }                                                                                          \
+    } while (0)
+
+void mg_free(gabp_mg *g) {
+    for (gabp_ctx *c : g->lv)
+        if (c) gabp_destroy(c);
+    g->lv.clear();
+    for (int i = 0; i < 2; ++i) {
+        if (g->mu[i]) cudaFree(g->mu[i]);
+        if (g->q[i]) cudaFree(g->q[i]);
+        g->mu[i] = g->q[i] = nullptr;
+    }
+}
+
+// run one level: exactly max_iters iterations (tol <= 0) or until the relative residual is
+// <= tol (checked every check_every iterations, at most max_iters); returns the final residual
+int mg_run_level(gabp_ctx *c, double damping, double tol, int max_iters, double *res) {
+    int rc;
+    if (tol > 0.0) {
+        c->opt.tol = tol;
+        c->opt.max_iters = max_iters;
+        rc = gabp_iterate(c, -1, damping);
+        if (rc == GABP_ERR_TIMEOUT || rc == GABP_ERR_DIVERGED) rc = GABP_OK;   // judged by the residual
+    } else {
+        rc = gabp_iterate(c, max_iters, damping);
+    }
+    if (rc) return rc;
+    return gabp_residual(c, res);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gabp_mg_create(gabp_mg **out, gabp_ctx *ctx, int levels) {
+    if (!out || !ctx) return GABP_ERR_ARG;
+    *out = nullptr;
+    if (levels < 2 || levels > GABP_MG_MAX_LEVELS) return fail(ctx, GABP_ERR_ARG, "levels must be in [2, 16]");
+    const int nx = ctx->p.nx, ny = ctx->p.ny;
+    const int64_t m = ctx->p.m;
+    for (int k = 1; k < levels; ++k) {
+        const int s = 1 << k;
+        const int nxk = (nx + s - 1) / s, nyk = (ny + s - 1) / s;
+        if (nxk < 2 || nyk < 2)
+            return fail(ctx, GABP_ERR_ARG, "too many levels: level " + std::to_string(k) + " has fewer than 2 nodes per axis");
+    }
+    gabp_mg *g = new (std::nothrow) gabp_mg();
+    if (!g) return GABP_ERR_OOM;
+    g->target = ctx;
+    g->levels = levels;
+    g->lv.assign((size_t)levels, nullptr);
+    DeviceGuard dg(ctx->dev);
+    std::vector<double> xy((size_t)(2 * m));
+    int rc = GABP_OK;
+    for (int k = 1; k < levels && rc == GABP_OK; ++k) {
+        // level k: the same SPDE at spacing 2^k (kappa 2^k kappa, gamma / 4^k), every observation at
+        // its coordinates on that grid, clamped to the last node
+        const int s = 1 << k;
+        const int nxk = (nx + s - 1) / s, nyk = (ny + s - 1) / s;
+        for (int64_t i = 0; i < m; ++i) {
+            xy[2 * i] = std::min(ctx->hxy[2 * i] / s, (double)(nxk - 1));
+            xy[2 * i + 1] = std::min(ctx->hxy[2 * i + 1] / s, (double)(nyk - 1));
+        }
+        gabp_grid gk{nxk, nyk, 1.0};
+        gabp_prior pk{ctx->p.gamma / ((double)s * s), 0};
+        gabp_options ok = ctx->opt;
+        ok.kernel = GABP_KERNEL_AUTO;
+        ok.tile_x = ok.tile_y = 0;
+        ok.debug_flags = 0;
+        ok.device = ctx->dev;
+        ok.stream = ctx->stream;
+        rc = gabp_create(&g->lv[(size_t)k], gk, ctx->kappa * s, &pk, m, xy.data(), ctx->hy.data(), ctx->hvar.data(), &ok);
+        if (rc) fail(ctx, rc, "multigrid level " + std::to_string(k) + ": " + gabp_create_error());
+    }
+    for (int i = 0; i < 2 && rc == GABP_OK; ++i) {
+        const size_t bytes = (size_t)ctx->p.n * sizeof(double);
+        if (cudaMalloc((void **)&g->mu[i], bytes) != cudaSuccess || cudaMalloc((void **)&g->q[i], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(ctx, GABP_ERR_OOM, "multigrid buffers");
+        }
+    }
+    if (rc) {
+        mg_free(g);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return GABP_OK;
+}
+
+int gabp_mg_warm_start(gabp_mg *g, double damping, double tol, int max_iters, gabp_mg_stats *stats) {
+    if (!g) return GABP_ERR_ARG;
+    if (!(damping >= 0.0 && damping < 1.0)) return mfail(g, GABP_ERR_ARG, "damping must be in [0, 1)");
+    if (max_iters < 1) return mfail(g, GABP_ERR_ARG, "max_iters must be >= 1");
+    gabp_ctx *t = g->target;
+    DeviceGuard dg(t->dev);
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->levels = g->levels;
+    }
+    // (mu[cur], q[cur]): marginals handed to the next finer level, on the grid of level `have_k`
+    int cur = 0, have_k = -1;
+    for (int k = g->levels - 1; k >= 1; --k) {
+        gabp_ctx *c = g->lv[(size_t)k];
+        const int nxk = c->p.nx, nyk = c->p.ny;
+        // this level's start: the upscaled state of level k+1 (precisions), or cold
+        const bool warm = have_k == k + 1;
+        if (warm) {
+            gabp_ctx *u = g->lv[(size_t)k + 1];
+            CK_MG(gabp::launch_upscale(g->mu[cur], g->q[cur], 0, 1, u->p.nx, u->p.ny, nxk, nyk, g->mu[cur ^ 1],
+                                       g->q[cur ^ 1], c->stream),
+                  "upscale");
+            cur ^= 1;
+        }
+        // GaBP on this level; a run whose final relative residual is not finite or not below 1
+        // is repeated from the same start with the damping (1 + b) / 2, up to three times
+        double b = damping, used = damping, res = NAN;
+        bool ok = false;
+        int64_t its = 0;
+        for (int attempt = 0; attempt <= 3 && !ok; ++attempt) {
+            int rc = warm ? gabp_warm_start(c, g->mu[cur], g->q[cur]) : gabp_reset(c);
+            if (rc) return mfail(g, rc, "multigrid level " + std::to_string(k) + ": " + c->err);
+            used = b;
+            rc = mg_run_level(c, b, tol, max_iters, &res);
+            its += c->iters;
+            if (rc) return mfail(g, rc, "multigrid level " + std::to_string(k) + ": " + c->err);
+            ok = std::isfinite(res) && res < 1.0;
+            b = 0.5 * (1.0 + b);
+        }
+        if (stats) {
+            stats->iterations[k] = its;
+            stats->damping[k] = used;
+            stats->residual[k] = res;
+            stats->converged[k] = ok ? 1 : 0;
+        }
+        if (ok) {
+            // this level's marginals (mean, variance) into the other buffer pair
+            const int o = cur ^ 1;
+            int rc = gabp_marginals(c, g->mu[o], g->q[o]);
+            if (rc) return mfail(g, rc, "multigrid level " + std::to_string(k) + ": " + c->err);
+            CK_MG(gabp::launch_upscale(g->mu[o], g->q[o], 1, 0, nxk, nyk, nxk, nyk, g->mu[cur], g->q[cur], c->stream),
+                  "precisions");
+            have_k = k;
+        } else if (warm) {
+            have_k = k;   // pass this level's own start on (already in mu[cur], q[cur])
+        }
+    }
+    // the target grid
+    int rc;
+    if (have_k == 1) {
+        gabp_ctx *u = g->lv[1];
+        CK_MG(gabp::launch_upscale(g->mu[cur], g->q[cur], 0, 1, u->p.nx, u->p.ny, t->p.nx, t->p.ny, g->mu[cur ^ 1],
+                                   g->q[cur ^ 1], t->stream),
+              "upscale");
+        cur ^= 1;
+        rc = gabp_warm_start(t, g->mu[cur], g->q[cur]);
+    } else {
+        rc = gabp_reset(t);
+    }
+    if (rc) return mfail(g, rc, std::string("target: ") + t->err);
+    return GABP_OK;
+}
+
+const char *gabp_mg_last_error(const gabp_mg *g) { return g ? g->err.c_str() : ""; }
+
+void gabp_mg_destroy(gabp_mg *g) {
+    if (!g) return;
+    DeviceGuard dg(g->target->dev);
+    mg_free(g);
+    delete g;
 }
 
 int gabp_wsnet_warm_start(gabp_ctx *c, gabp_wsnet *net) {

@@ -69,6 +69,13 @@ cudaError_t launch_marginals(const DevProblem &p, int src, double *mean, double 
 // ---- learned warm start (gabp_split.cu kernels, network in gabp_wsnet.cu) ----
 cudaError_t launch_ws_input(const DevProblem &p, double scale, double kappa, int Hp, int Wp, void *x, cudaStream_t st);
 cudaError_t launch_ws_target(const DevProblem &p, int src, double scale, int Hp, int Wp, float *t, cudaStream_t st);
+// multigrid: marginals of the finer grid copied from parent nodes (i >> shift, j >> shift); q_c
+// variances or precisions, the output precisions
+cudaError_t launch_upscale(const double *mu_c, const double *q_c, int q_is_var, int shift, int nxc, int nyc, int nxf,
+                           int nyf, double *mu_f, double *lam_f, cudaStream_t st);
+// FP32 contexts: warm-start messages from marginals in FP32 arithmetic; nm: n float2 scratch
+cudaError_t launch_init_warm_f32(const DevProblem &p, int dst, const double *mu0, const double *lam0, float2 *nm,
+                                 cudaStream_t st);
 // FP32 contexts: decode the network output and initialise the messages (dst buffer) in FP32;
 // nm: n float2 scratch
 cudaError_t launch_ws_init_f32(const DevProblem &p, int dst, double scale, int Wp, const float *out, float2 *nm,

@@ -550,6 +550,30 @@ __global__ void k_ws_node_msg(DevProblem p, float scale, int Wp, const float *ou
     const float L = expf(lg) / (float)node_slots(p, v);
     nm[v] = make_float2(scale * out[2 * q] * L, L);
 }
+// FP32 contexts: node message pairs from given marginals (mu0, lam0), as in the FP64 path but
+// in FP32 arithmetic (L = lam0 / slots, eta = mu0 L)
+__global__ void k_node_msg_marg(DevProblem p, const double *mu0, const double *lam0, float2 *nm) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const float L = (float)lam0[v] / (float)node_slots(p, v);
+    nm[v] = make_float2((float)mu0[v] * L, L);
+}
+
+// Multigrid upscaling (Alg. 2 "Upscale Messages", read as copying parent marginals): node (i, j)
+// of the finer grid takes mean and precision of node (i >> shift, j >> shift) of the coarser
+// (shift 1: the parent (floor(i/2), floor(j/2)); shift 0: the same grid, a plain copy);
+// q_c holds variances (q_is_var) or precisions
+__global__ void k_upscale_marg(const double *mu_c, const double *q_c, int q_is_var, int shift, int nxc, int nyc,
+                               int nxf, int nyf, double *mu_f, double *lam_f) {
+    const int64_t v = gtid();
+    if (v >= (int64_t)nxf * nyf) return;
+    const int i = (int)(v / nxf), j = (int)(v - (int64_t)i * nxf);
+    const int ic = min(i >> shift, nyc - 1), jc = min(j >> shift, nxc - 1);
+    const int64_t c = (int64_t)ic * nxc + jc;
+    mu_f[v] = mu_c[c];
+    lam_f[v] = q_is_var ? 1.0 / q_c[c] : q_c[c];
+}
+
 __global__ void k_init_nodes_prior(DevProblem p, int dst, const float2 *nm) {
     const int64_t c = gtid();
     if (c >= p.n) return;
@@ -681,6 +705,22 @@ cudaError_t launch_ws_target(const DevProblem &p, int src, double scale, int Hp,
     if (e != cudaSuccess) return e;
     if (p.prec) k_ws_target<double><<<nblocks((int64_t)Hp * Wp), TPB, 0, st>>>(p, 1.0 / scale, Hp, Wp, t);
     else k_ws_target<float><<<nblocks((int64_t)Hp * Wp), TPB, 0, st>>>(p, 1.0 / scale, Hp, Wp, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upscale(const double *mu_c, const double *q_c, int q_is_var, int shift, int nxc, int nyc, int nxf,
+                           int nyf, double *mu_f, double *lam_f, cudaStream_t st) {
+    k_upscale_marg<<<nblocks((int64_t)nxf * nyf), TPB, 0, st>>>(mu_c, q_c, q_is_var, shift, nxc, nyc, nxf, nyf, mu_f,
+                                                                 lam_f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_warm_f32(const DevProblem &p, int dst, const double *mu0, const double *lam0, float2 *nm,
+                                 cudaStream_t st) {
+    if (p.prec) return cudaErrorInvalidValue;
+    k_node_msg_marg<<<nblocks(p.n), TPB, 0, st>>>(p, mu0, lam0, nm);
+    k_init_nodes_prior<<<nblocks(p.n), TPB, 0, st>>>(p, dst, nm);
+    if (p.m > 0) k_init_nodes_obs<<<nblocks(p.m), TPB, 0, st>>>(p, dst, nm);
     return cudaGetLastError();
 }
 

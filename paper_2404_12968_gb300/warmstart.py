@@ -9,8 +9,9 @@ nodes (kappa ~ U[0.02, 0.2], 8-32 satellite-like tracks, sigma 0.05) are solved 
 from its observations on the GPU, target = its beliefs (mean / scale, log precision).  The
 network is trained on the GPU by the library's own forward and backward kernels (Adam, mean
 squared error).  Evaluation: on a 2048^2 problem (kappa 0.03, 48 tracks) the time to relative
-residual 1e-5 from the cold start and from the learned warm start (scatter + network inference
-+ message initialisation included).
+residual 1e-5 from the cold start, from the learned warm start (scatter + network inference
++ message initialisation included) and from the multigrid warm start (the paper's own
+accelerator: a coarse level solved to 1e-4, upscaled; its iterations included).
 
 PyTorch only holds the samples in device memory; every computation runs in libgabp.
 """
@@ -30,7 +31,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 import gabp_synth  # noqa: E402
-from paper_2404_12968_gb300 import (Batch, Solver, WarmStartNet, gabp_batch_input_shape,  # noqa: E402
+from paper_2404_12968_gb300 import (Batch, Multigrid, Solver, WarmStartNet, gabp_batch_input_shape,  # noqa: E402
                                     gabp_batch_wsnet_sample, gabp_wsnet_train_step)
 
 DAMPING = 0.3
@@ -80,30 +81,45 @@ def train(net: WarmStartNet, xs, ts, epochs: int = 8, batch: int = 8, lr: float 
     return hist
 
 
-def time_to_tol(solver: Solver, net: WarmStartNet | None, tol: float = TOL, check_every: int = 10):
-    """Seconds (wall, synchronous calls) and iterations from a fresh start to `tol`."""
+MG_LEVELS = 2      # multigrid: one coarse level (the best of 2..7 levels at 2048^2)
+MG_TOL = 1e-4      # relative residual the coarse level is solved to
+
+
+def time_to_tol(solver: Solver, net: WarmStartNet | None, tol: float = TOL, check_every: int = 10, mg=None):
+    """Seconds (wall, synchronous calls) and iterations from a fresh start to `tol`: cold, after
+    the learned warm start (`net`), or after the multigrid warm start (`mg`, coarse levels
+    included in the time and counted separately)."""
     solver.reset()
+    coarse = 0
     t0 = time.perf_counter()
     if net is not None:
         solver.learned_warm_start(net)
+    if mg is not None:
+        coarse = sum(mg.warm_start(DAMPING, MG_TOL, 100000)["iterations"])
     solver.iterate(-1, DAMPING)
     dt = time.perf_counter() - t0
     st = solver.stats()
-    return dt, int(st["iterations"]), float(st["last_residual"])
+    return dt, int(st["iterations"]), float(st["last_residual"]), coarse
 
 
 def evaluate(net: WarmStartNet, problem=None, device: int = 0, repeats: int = 3):
     p = problem if problem is not None else gabp_synth.config_warm_eval(0)
     with Solver(p, precision="fp32", tol=TOL, check_every=10, max_iters=400000, device=device) as s:
-        time_to_tol(s, None)                 # warm-up (graph capture, first launches)
-        time_to_tol(s, net)
-        cold = [time_to_tol(s, None) for _ in range(repeats)]
-        warm = [time_to_tol(s, net) for _ in range(repeats)]
+        with Multigrid(s, MG_LEVELS) as mg:      # the coarse problem is set up once, like the solver
+            time_to_tol(s, None)                 # warm-up (graph capture, first launches)
+            time_to_tol(s, net)
+            time_to_tol(s, None, mg=mg)
+            cold = [time_to_tol(s, None) for _ in range(repeats)]
+            warm = [time_to_tol(s, net) for _ in range(repeats)]
+            mgr = [time_to_tol(s, None, mg=mg) for _ in range(repeats)]
     best = lambda r: min(r, key=lambda z: z[0])  # noqa: E731
-    c, w = best(cold), best(warm)
+    c, w, g = best(cold), best(warm), best(mgr)
     return {"grid": [p.nx, p.ny], "kappa": p.kappa, "m": p.m, "tol": TOL, "damping": DAMPING,
             "cold_s": c[0], "cold_iters": c[1], "warm_s": w[0], "warm_iters": w[1],
-            "speedup": c[0] / w[0], "cold_residual": c[2], "warm_residual": w[2]}
+            "speedup": c[0] / w[0], "cold_residual": c[2], "warm_residual": w[2],
+            "multigrid_s": g[0], "multigrid_iters": g[1], "multigrid_coarse_iters": g[3],
+            "multigrid_levels": MG_LEVELS, "multigrid_coarse_tol": MG_TOL, "multigrid_speedup": c[0] / g[0],
+            "multigrid_residual": g[2]}
 
 
 def main():
