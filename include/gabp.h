@@ -212,6 +212,25 @@ const char *gabp_last_error(const gabp_ctx *ctx);
 /* Text of the last error of a gabp_create call that failed on this thread. */
 const char *gabp_create_error(void);
 
+/*
+ * Mean over the 2 E message components (eta and Lambda of every factor-variable edge) of
+ * |m_t - m_{t-1}|: the change made by the last iteration, the quantity of the paper's
+ * early-stopping rule (App. B).  GABP_ERR_STATE if no iteration ran since the last
+ * initialisation.
+ */
+int gabp_message_change(gabp_ctx *ctx, double *mean_abs_change);
+
+/*
+ * Iterate with the paper's early-stopping rule (App. B): stop after iteration t once
+ * mean|m_t - m_{t-1}| < tau * mean|m_2 - m_1|, where m_i is the message set after i iterations
+ * of this call (the paper uses tau = 1e-3).  The rule is checked after iteration 2 + j *
+ * check_every (check_every = 1: after every iteration, as in the paper).  *stopped_at (may be
+ * NULL) receives t.  GABP_ERR_TIMEOUT after max_iters (>= 3) iterations, GABP_ERR_DIVERGED if a
+ * change is not finite.
+ */
+int gabp_iterate_early_stop(gabp_ctx *ctx, int max_iters, double damping, double tau, int check_every,
+                            int64_t *stopped_at);
+
 /* Release the context and all its device memory.  NULL is ignored. */
 void gabp_destroy(gabp_ctx *ctx);
 

@@ -32,6 +32,7 @@ __all__ = [
     "gabp_wsnet_input_shape", "gabp_wsnet_sample", "gabp_batch_input_shape", "gabp_batch_wsnet_sample",
     "gabp_wsnet_warm_start", "Solver", "Batch", "WarmStartNet", "GabpError",
     "gabp_mg_create", "gabp_mg_warm_start", "gabp_mg_destroy", "Multigrid",
+    "gabp_message_change", "gabp_iterate_early_stop",
 ]
 
 
@@ -254,6 +255,21 @@ class Batch:
         self.close()
 
 
+def gabp_message_change(ctx: int) -> float:
+    """Mean |m_t - m_{t-1}| over both components of every edge (the early-stopping quantity)."""
+    d = ctypes.c_double()
+    _check(_lib.load().gabp_message_change(ctx, ctypes.byref(d)), ctx)
+    return d.value
+
+
+def gabp_iterate_early_stop(ctx: int, max_iters: int, damping: float, tau: float = 1e-3,
+                            check_every: int = 1) -> int:
+    """Iterate under the paper's early-stopping rule (App. B); returns the stopping iteration."""
+    t = ctypes.c_int64()
+    _check(_lib.load().gabp_iterate_early_stop(ctx, max_iters, damping, tau, check_every, ctypes.byref(t)), ctx)
+    return t.value
+
+
 def gabp_mg_create(ctx: int, levels: int) -> int:
     h = ctypes.c_void_p()
     _check(_lib.load().gabp_mg_create(ctypes.byref(h), ctx, levels), ctx)
@@ -467,6 +483,12 @@ class Solver:
 
     def reset(self) -> None:
         gabp_reset(self.ctx)
+
+    def message_change(self) -> float:
+        return gabp_message_change(self.ctx)
+
+    def iterate_early_stop(self, max_iters: int, damping: float, tau: float = 1e-3, check_every: int = 1) -> int:
+        return gabp_iterate_early_stop(self.ctx, max_iters, damping, tau, check_every)
 
     def get_messages(self) -> np.ndarray:
         buf = np.empty(gabp_message_bytes(self.ctx), np.uint8)

@@ -100,6 +100,11 @@ def load():
     L.gabp_marginals.restype = ctypes.c_int
     L.gabp_residual.argtypes = [_vp, _dp]
     L.gabp_residual.restype = ctypes.c_int
+    L.gabp_message_change.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+    L.gabp_message_change.restype = ctypes.c_int
+    L.gabp_iterate_early_stop.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int64)]
+    L.gabp_iterate_early_stop.restype = ctypes.c_int
     L.gabp_mg_create.argtypes = [ctypes.POINTER(_vp), _vp, ctypes.c_int]
     L.gabp_mg_create.restype = ctypes.c_int
     L.gabp_mg_warm_start.argtypes = [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(gabp_mg_stats)]

@@ -188,6 +188,17 @@ int compute_residual(gabp_ctx *c, double *out) {
     return GABP_OK;
 }
 
+// mean over the 2 E message components (eta and Lambda of every factor-variable edge) of
+// |m_t - m_{t-1}|, the quantity of the early-stopping rule (App. B)
+int compute_msg_change(gabp_ctx *c, double *out) {
+    CK(gabp::launch_msg_change(c->p, c->cur, c->p.scal + 2, c->stream), "message change kernels");
+    CK(cudaMemcpyAsync(c->hscal + 2, c->p.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "message change copy");
+    CK(cudaStreamSynchronize(c->stream), "message change sync");
+    *out = c->hscal[2] / (2.0 * (double)c->edges);
+    return GABP_OK;
+}
+
 int init_messages(gabp_ctx *c) {
     CK(gabp::launch_init_cold(c->p, 0, c->opt.init == GABP_INIT_PAPER, c->stream), "init kernels");
     c->cur = 0;
@@ -336,15 +347,15 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     p.e64 = (double *)q;
     if ((rc = dalloc(c, &q, gabp::RES_BLOCKS * sizeof(double), "alloc partial sums"))) return rc;
     p.part = (double *)q;
-    if ((rc = dalloc(c, &q, 2 * sizeof(double), "alloc scalars"))) return rc;
+    if ((rc = dalloc(c, &q, 4 * sizeof(double), "alloc scalars"))) return rc;   // |r|^2, |b|^2, message change
     p.scal = (double *)q;
     if ((rc = dalloc(c, &q, sizeof(int), "alloc error flag"))) return rc;
     p.err = (int *)q;
     CK(cudaMemsetAsync(p.err, 0, sizeof(int), c->stream), "memset");
     if ((rc = dalloc(c, &q, 2 * (size_t)n * sizeof(double), "alloc staging"))) return rc;
     c->stage = (double *)q;
-    CK(cudaMallocHost((void **)&c->hscal, 2 * sizeof(double)), "alloc pinned scalars");
-    CK(cudaMemsetAsync(p.scal, 0, 2 * sizeof(double), c->stream), "memset");
+    CK(cudaMallocHost((void **)&c->hscal, 4 * sizeof(double)), "alloc pinned scalars");
+    CK(cudaMemsetAsync(p.scal, 0, 4 * sizeof(double), c->stream), "memset");
 
     // upload the sorted observations; FP64 precompute of weights and 1/sigma^2 on the GPU
     if (m > 0) {
@@ -503,6 +514,47 @@ int gabp_iterate(gabp_ctx *c, int n_iters, double damping) {
         if (rc) return rc;
         if ((rc = check_device_error(c))) return rc;
         done += chunk;
+    }
+}
+
+int gabp_message_change(gabp_ctx *c, double *mean_abs_change) {
+    if (!c || !mean_abs_change) return c ? fail(c, GABP_ERR_ARG, "mean_abs_change must not be NULL") : GABP_ERR_ARG;
+    if (c->iters < 1) return fail(c, GABP_ERR_STATE, "no iteration since the last initialisation");
+    DeviceGuard g(c->dev);
+    if (!g.ok) return fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
+    return compute_msg_change(c, mean_abs_change);
+}
+
+int gabp_iterate_early_stop(gabp_ctx *c, int max_iters, double damping, double tau, int check_every,
+                            int64_t *stopped_at) {
+    if (!c) return GABP_ERR_ARG;
+    if (!(damping >= 0.0 && damping < 1.0)) return fail(c, GABP_ERR_ARG, "damping must be in [0, 1)");
+    if (!(tau > 0.0) || check_every < 1 || max_iters < 3)
+        return fail(c, GABP_ERR_ARG, "tau > 0, check_every >= 1 and max_iters >= 3 required");
+    DeviceGuard g(c->dev);
+    if (!g.ok) return fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
+    c->err.clear();
+    if (stopped_at) *stopped_at = 0;
+    // iterations 1 and 2 of this call; the change of iteration 2 is the reference
+    int rc = run_iterations(c, 2, damping);
+    if (rc || (rc = check_device_error(c))) return rc;
+    double ref = 0.0, d = 0.0;
+    if ((rc = compute_msg_change(c, &ref))) return rc;
+    if (!std::isfinite(ref)) return fail(c, GABP_ERR_DIVERGED, "message change is not finite");
+    int64_t t = 2;
+    for (;;) {
+        if (t >= max_iters) return fail(c, GABP_ERR_TIMEOUT, "max_iters reached before the early-stopping rule held");
+        int64_t chunk = check_every;
+        if (t + chunk > max_iters) chunk = max_iters - t;
+        rc = run_iterations(c, (int)chunk, damping);
+        if (rc || (rc = check_device_error(c))) return rc;
+        t += chunk;
+        if ((rc = compute_msg_change(c, &d))) return rc;
+        if (!std::isfinite(d)) return fail(c, GABP_ERR_DIVERGED, "message change is not finite");
+        if (d < tau * ref) {
+            if (stopped_at) *stopped_at = t;
+            return GABP_OK;
+        }
     }
 }
 

@@ -80,6 +80,8 @@ cudaError_t launch_init_warm_f32(const DevProblem &p, int dst, const double *mu0
 // nm: n float2 scratch
 cudaError_t launch_ws_init_f32(const DevProblem &p, int dst, double scale, int Wp, const float *out, float2 *nm,
                                cudaStream_t st);
+// sum over every stored message component of |m_t - m_{t-1}| (buffers cur and cur ^ 1) into *out
+cudaError_t launch_msg_change(const DevProblem &p, int cur, double *out, cudaStream_t st);
 // FP32 contexts: double-float (hi, lo) copies of the FP64 observation weights and (y, 1/sigma^2)
 cudaError_t launch_df_precompute(const DevProblem &p, cudaStream_t st);
 cudaError_t launch_ws_decode(const DevProblem &p, double scale, int Wp, const float *out, double *mu0, double *lam0,

@@ -662,6 +662,29 @@ cudaError_t launch_rhs_norm(const DevProblem &p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---- message change between the last two iterates (the early-stopping rule of App. B) ----
+// partial sums over a fixed grid of |m_t - m_{t-1}| for every stored message component: the
+// prior planes (slots without a neighbour hold (0, 0) in both buffers and add nothing) and the
+// observation messages.  Per-thread sums in T, block sums in FP64, fixed order.
+template <typename T> __global__ void k_msg_change(DevProblem p, int cur) {
+    const T *a = (const T *)p.P[cur], *b = (const T *)p.P[cur ^ 1];
+    const T *oa = (const T *)p.O[cur], *ob = (const T *)p.O[cur ^ 1];
+    const int64_t np_ = 10 * p.n, no = 8 * p.m;
+    const int64_t stride = (int64_t)gridDim.x * TPB;
+    T acc = T(0);
+    for (int64_t i = gtid(); i < np_; i += stride) acc += fabs(a[i] - b[i]);
+    for (int64_t i = gtid(); i < no; i += stride) acc += fabs(oa[i] - ob[i]);
+    double s = block_sum((double)acc);
+    if (threadIdx.x == 0) p.part[blockIdx.x] = s;
+}
+
+cudaError_t launch_msg_change(const DevProblem &p, int cur, double *out, cudaStream_t st) {
+    if (p.prec) k_msg_change<double><<<RES_BLOCKS, TPB, 0, st>>>(p, cur);
+    else k_msg_change<float><<<RES_BLOCKS, TPB, 0, st>>>(p, cur);
+    k_final_sum<<<1, TPB, 0, st>>>(p.part, RES_BLOCKS, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_df_precompute(const DevProblem &p, cudaStream_t st) {
     if (p.m == 0 || p.prec) return cudaSuccess;
     k_df_precompute<<<nblocks(p.m), TPB, 0, st>>>(p);
