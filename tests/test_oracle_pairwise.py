@@ -1,0 +1,80 @@
+"""Pins of the oracle's pairwise re-weighted message passing (oracle/pairwise.py)."""
+import numpy as np
+import pytest
+
+import gabp_synth
+import oracle
+from oracle import pairwise as pw
+
+
+def _grid_point_problem(N, kappa, frac, seed=0, sigma=0.1):
+    """Observations at a fraction of the grid points (the paper's synthetic setting)."""
+    rng = np.random.default_rng(seed)
+    nobs = int(frac * N * N)
+    idx = rng.choice(N * N, nobs, replace=False)
+    p = gabp_synth.make_problem(N, N, kappa, seed + 1)
+    y = p.truth.reshape(-1)[idx] + sigma * rng.standard_normal(nobs)
+    ox = (idx % N).astype(float)
+    oy = (idx // N).astype(float)
+    return oracle.build_factors(N, N, kappa, ox, oy, y, np.full(nobs, sigma ** 2))
+
+
+@pytest.mark.parametrize("c", [1.0, 10.0, -2.0, 0.5])
+def test_factor_message_equals_the_fractional_integral(c):
+    # m^(1/c)(f) = integral of exp(-(P/c) f g) exp(-alpha g^2 / 2 + beta g) dg, by quadrature:
+    # its log is a quadratic in f whose coefficients must be (-a/2, b)
+    alpha, beta, pij = 2.7, -0.8, -1.3
+    a, b = pw.factor_message(alpha, beta, pij, c)
+    g = np.linspace(-40, 40, 400001)
+    fs = np.array([-0.7, -0.2, 0.3, 0.9])
+    logI = []
+    for f in fs:
+        e = -(pij / c) * f * g - 0.5 * alpha * g * g + beta * g
+        m = e.max()
+        logI.append(m + np.log(np.trapezoid(np.exp(e - m), g)))
+    coef = np.polyfit(fs, np.array(logI), 2)
+    assert coef[0] == pytest.approx(-0.5 * a, rel=1e-6, abs=1e-9)
+    assert coef[1] == pytest.approx(b, rel=1e-6, abs=1e-9)
+
+
+def test_assembled_precision_is_the_posterior_precision():
+    p = gabp_synth.make_problem(9, 7, 0.4, 3, n_uniform=15)
+    fl = oracle.build_factors(p.nx, p.ny, p.kappa, p.obs_x, p.obs_y, p.y, p.noise_var)
+    P, h = pw.assemble(fl)
+    np.testing.assert_allclose(P.toarray(), oracle.dense_A(fl), rtol=1e-13, atol=1e-13)
+    # interior rows of gamma L^T L have the 13-point pattern; bilinear observations stay inside it
+    src, dst, _, rev = pw.edges(P)
+    assert np.bincount(dst, minlength=fl.n).max() == 12
+    assert np.array_equal(src[rev], dst) and np.array_equal(dst[rev], src)
+
+
+@pytest.mark.parametrize("c", [10.0, 20.0])
+def test_converged_means_are_exact(c):
+    # a fixed point of the re-weighted scheme carries the exact posterior means
+    fl = _grid_point_problem(32, 0.3, 0.05)
+    P, h = pw.assemble(fl)
+    exact = oracle.exact_mean(fl, 32)
+    mean, prec, _, ok = pw.run(P, h, c, 0.6, 20000)
+    assert ok and np.all(prec > 0)
+    assert np.linalg.norm(mean - exact) / np.linalg.norm(exact) < 1e-9
+
+
+def test_reproduces_the_papers_convergence_pattern():
+    # the grid search of App. D (5 % of the grid observed, learning rate 0.6): c = 1 and c = 5
+    # diverge, c = 10 and c = 20 converge; learning rate 0.8 diverges for c = 10
+    fl = _grid_point_problem(64, 0.05, 0.05)
+    P, h = pw.assemble(fl)
+    exact = oracle.exact_mean(fl, 64)
+
+    def diverged(c, eta):
+        mean, _, _, ok = pw.run(P, h, c, eta, 2000)
+        return not ok or not np.linalg.norm(mean - exact) / np.linalg.norm(exact) < 1e3   # mu = 0 has error 1
+
+    assert diverged(1.0, 0.6) and diverged(5.0, 0.6) and diverged(10.0, 0.8)
+    for c in (10.0, 20.0):
+        m1, _, msg, ok = pw.run(P, h, c, 0.6, 1000)
+        m2, _, _, ok2 = pw.run(P, h, c, 0.6, 1000, messages=msg)
+        assert ok and ok2
+        e1 = np.linalg.norm(m1 - exact) / np.linalg.norm(exact)
+        e2 = np.linalg.norm(m2 - exact) / np.linalg.norm(exact)
+        assert e2 < e1 < 1.0, (c, e1, e2)
