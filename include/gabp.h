@@ -327,6 +327,32 @@ const char *gabp_mg_last_error(const gabp_mg *mg);
 void gabp_mg_destroy(gabp_mg *mg);
 
 /* ---------------------------------------------------------------------------------------
+ * The paper's own pairwise re-weighted message passing (App. A, "Gaussian Setting" and
+ * "Re-weighted message updates"), a second iteration family over the same posterior: one node
+ * factor exp(-P_ii f_i^2 / 2 + h_i f_i) per node and one pair factor exp(-P_ij f_i f_j) per
+ * nonzero P_ij of P = gamma L^T L + H^T R^-1 H (the 13-point pattern), fractional messages with
+ * weight c, damping with the paper's learning rate eta (m <- (1 - eta) m_old + eta m_new; the
+ * paper uses c = 10, eta = 0.6).  The factor message follows the integral that defines it.
+ * Messages start at zero; the marginal is mean (h_i + c sum b) / (P_ii + c sum a), precision
+ * P_ii + c sum a (with the c of the last gabp_pw_iterate call).
+ * --------------------------------------------------------------------------------------- */
+typedef struct gabp_pw gabp_pw;   /* opaque; owns its coefficient and message buffers */
+
+/* The pairwise form of ctx's problem (ctx's precision, device and stream; ctx must outlive it).
+ * Errors are reported by gabp_last_error(ctx). */
+int gabp_pw_create(gabp_pw **out, gabp_ctx *ctx);
+/* n_iters synchronous iterations with weight c (finite, nonzero) and learning_rate in (0, 1]. */
+int gabp_pw_iterate(gabp_pw *pw, int n_iters, double c, double learning_rate);
+/* Marginal means and variances (n doubles each, host or device; var may be NULL). */
+int gabp_pw_marginals(gabp_pw *pw, double *mean, double *var);
+/* Relative residual ||b - A mu|| / ||b|| of the current means (as gabp_residual). */
+int gabp_pw_residual(gabp_pw *pw, double *rel_residual);
+int gabp_pw_reset(gabp_pw *pw);
+int64_t gabp_pw_iterations(const gabp_pw *pw);
+const char *gabp_pw_last_error(const gabp_pw *pw);
+void gabp_pw_destroy(gabp_pw *pw);
+
+/* ---------------------------------------------------------------------------------------
  * Learned warm start.  A small convolutional encoder-decoder (4 levels, 32 -> 256 channels,
  * BF16 weights and activations, FP32 accumulation) maps the gridded observations to initial
  * beliefs (mean, log precision); gabp_wsnet_warm_start() seeds a context's messages with them

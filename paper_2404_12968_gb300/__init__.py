@@ -33,6 +33,8 @@ __all__ = [
     "gabp_wsnet_warm_start", "Solver", "Batch", "WarmStartNet", "GabpError",
     "gabp_mg_create", "gabp_mg_warm_start", "gabp_mg_destroy", "Multigrid",
     "gabp_message_change", "gabp_iterate_early_stop",
+    "gabp_pw_create", "gabp_pw_iterate", "gabp_pw_marginals", "gabp_pw_residual", "gabp_pw_reset",
+    "gabp_pw_destroy", "Pairwise",
 ]
 
 
@@ -268,6 +270,85 @@ def gabp_iterate_early_stop(ctx: int, max_iters: int, damping: float, tau: float
     t = ctypes.c_int64()
     _check(_lib.load().gabp_iterate_early_stop(ctx, max_iters, damping, tau, check_every, ctypes.byref(t)), ctx)
     return t.value
+
+
+def _pcheck(rc: int, pw):
+    if rc != GABP_OK:
+        raise GabpError(rc, (_lib.load().gabp_pw_last_error(pw) or b"").decode(errors="replace"))
+
+
+def gabp_pw_create(ctx: int) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.load().gabp_pw_create(ctypes.byref(h), ctx), ctx)
+    return h.value
+
+
+def gabp_pw_iterate(pw: int, n_iters: int, c: float = 10.0, learning_rate: float = 0.6) -> None:
+    _pcheck(_lib.load().gabp_pw_iterate(pw, n_iters, c, learning_rate), pw)
+
+
+def gabp_pw_marginals(pw: int, mean, var=None) -> None:
+    _pcheck(_lib.load().gabp_pw_marginals(pw, _ptr(mean), _ptr(var) if var is not None else None), pw)
+
+
+def gabp_pw_residual(pw: int) -> float:
+    r = ctypes.c_double()
+    _pcheck(_lib.load().gabp_pw_residual(pw, ctypes.byref(r)), pw)
+    return r.value
+
+
+def gabp_pw_reset(pw: int) -> None:
+    _pcheck(_lib.load().gabp_pw_reset(pw), pw)
+
+
+def gabp_pw_destroy(pw: int) -> None:
+    if pw:
+        _lib.load().gabp_pw_destroy(pw)
+
+
+class Pairwise:
+    """The paper's pairwise re-weighted message passing (App. A) on a Solver's problem.
+    The Solver must outlive it."""
+
+    def __init__(self, solver: "Solver"):
+        self.n = solver.nx * solver.ny
+        self.handle = gabp_pw_create(solver.ctx)
+
+    def iterate(self, n_iters: int, c: float = 10.0, learning_rate: float = 0.6) -> None:
+        gabp_pw_iterate(self.handle, n_iters, c, learning_rate)
+
+    def marginals(self, want_var: bool = True):
+        mean = np.empty(self.n, np.float64)
+        var = np.empty(self.n, np.float64) if want_var else None
+        gabp_pw_marginals(self.handle, mean, var)
+        return mean, var
+
+    def residual(self) -> float:
+        return gabp_pw_residual(self.handle)
+
+    def reset(self) -> None:
+        gabp_pw_reset(self.handle)
+
+    @property
+    def iterations(self) -> int:
+        return int(_lib.load().gabp_pw_iterations(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gabp_pw_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gabp_mg_create(ctx: int, levels: int) -> int:

@@ -100,6 +100,22 @@ def load():
     L.gabp_marginals.restype = ctypes.c_int
     L.gabp_residual.argtypes = [_vp, _dp]
     L.gabp_residual.restype = ctypes.c_int
+    L.gabp_pw_create.argtypes = [ctypes.POINTER(_vp), _vp]
+    L.gabp_pw_create.restype = ctypes.c_int
+    L.gabp_pw_iterate.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.gabp_pw_iterate.restype = ctypes.c_int
+    L.gabp_pw_marginals.argtypes = [_vp, _vp, _vp]
+    L.gabp_pw_marginals.restype = ctypes.c_int
+    L.gabp_pw_residual.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+    L.gabp_pw_residual.restype = ctypes.c_int
+    L.gabp_pw_reset.argtypes = [_vp]
+    L.gabp_pw_reset.restype = ctypes.c_int
+    L.gabp_pw_iterations.argtypes = [_vp]
+    L.gabp_pw_iterations.restype = ctypes.c_int64
+    L.gabp_pw_last_error.argtypes = [_vp]
+    L.gabp_pw_last_error.restype = ctypes.c_char_p
+    L.gabp_pw_destroy.argtypes = [_vp]
+    L.gabp_pw_destroy.restype = None
     L.gabp_message_change.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
     L.gabp_message_change.restype = ctypes.c_int
     L.gabp_iterate_early_stop.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,

@@ -1387,6 +1387,142 @@ void gabp_mg_destroy(gabp_mg *g) {
     delete g;
 }
 
+// ---- the paper's pairwise re-weighted form (App. A) ----
+}  // extern "C"
+
+struct gabp_pw {
+    gabp_ctx *ctx = nullptr;
+    void *Pd = nullptr, *hv = nullptr, *Pn = nullptr, *msg[2] = {nullptr, nullptr};
+    int cur = 0;
+    double c = 1.0;
+    int64_t iters = 0;
+    std::string err;
+};
+
+namespace {
+
+int pfail(gabp_pw *w, int code, const std::string &msg) {
+    w->err = msg;
+    return code;
+}
+
+#define CK_PW(call, what)                                                                          \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            cudaGetLastError();                                                                    \
+            return pfail(w, GABP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e_));     \
+        }                                                                                          \
+    } while (0)
+
+void pw_free(gabp_pw *w) {
+    void *ps[5] = {w->Pd, w->hv, w->Pn, w->msg[0], w->msg[1]};
+    for (void *q : ps)
+        if (q) cudaFree(q);
+    w->Pd = w->hv = w->Pn = w->msg[0] = w->msg[1] = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gabp_pw_create(gabp_pw **out, gabp_ctx *ctx) {
+    if (!out || !ctx) return GABP_ERR_ARG;
+    *out = nullptr;
+    gabp_pw *w = new (std::nothrow) gabp_pw();
+    if (!w) return GABP_ERR_OOM;
+    w->ctx = ctx;
+    DeviceGuard dg(ctx->dev);
+    const size_t T = ctx->p.prec ? sizeof(double) : sizeof(float);
+    const size_t n = (size_t)ctx->p.n;
+    cudaError_t e = cudaMalloc(&w->Pd, n * T);
+    if (e == cudaSuccess) e = cudaMalloc(&w->hv, n * T);
+    if (e == cudaSuccess) e = cudaMalloc(&w->Pn, 12 * n * T);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&w->msg[b], 24 * n * T);
+    if (e == cudaSuccess) e = gabp::pw_setup(ctx->p, w->Pd, w->hv, w->Pn, ctx->stream);
+    if (e == cudaSuccess) e = gabp::pw_zero(ctx->p, w->msg[0], ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        const int code = e == cudaErrorMemoryAllocation ? GABP_ERR_OOM : GABP_ERR_CUDA;
+        fail(ctx, code, std::string("pairwise setup: ") + cudaGetErrorString(e));
+        pw_free(w);
+        delete w;
+        return code;
+    }
+    *out = w;
+    return GABP_OK;
+}
+
+int gabp_pw_iterate(gabp_pw *w, int n_iters, double c, double learning_rate) {
+    if (!w) return GABP_ERR_ARG;
+    if (n_iters < 0 || c == 0.0 || !std::isfinite(c) || !(learning_rate > 0.0 && learning_rate <= 1.0))
+        return pfail(w, GABP_ERR_ARG, "n_iters >= 0, c finite and nonzero, learning_rate in (0, 1] required");
+    gabp_ctx *ctx = w->ctx;
+    DeviceGuard dg(ctx->dev);
+    for (int t = 0; t < n_iters; ++t) {
+        CK_PW(gabp::pw_iterate(ctx->p, w->Pd, w->hv, w->Pn, w->msg[w->cur], w->msg[w->cur ^ 1], c, learning_rate,
+                               ctx->stream),
+              "pairwise iteration");
+        w->cur ^= 1;
+    }
+    CK_PW(cudaStreamSynchronize(ctx->stream), "pairwise sync");
+    w->c = c;
+    w->iters += n_iters;
+    return GABP_OK;
+}
+
+int gabp_pw_marginals(gabp_pw *w, double *mean, double *var) {
+    if (!w || !mean) return w ? pfail(w, GABP_ERR_ARG, "mean must not be NULL") : GABP_ERR_ARG;
+    gabp_ctx *ctx = w->ctx;
+    DeviceGuard dg(ctx->dev);
+    const int64_t n = ctx->p.n;
+    const bool dmean = is_device_ptr(mean), dvar = var ? is_device_ptr(var) : true;
+    double *km = dmean ? mean : ctx->stage;
+    double *kv = var ? (dvar ? var : ctx->stage + n) : nullptr;
+    CK_PW(gabp::pw_marginals(ctx->p, w->Pd, w->hv, w->msg[w->cur], w->c, km, kv, 0, ctx->stream), "pairwise marginals");
+    if (!dmean) CK_PW(cudaMemcpyAsync(mean, km, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "copy mean");
+    if (var && !dvar) CK_PW(cudaMemcpyAsync(var, kv, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "copy var");
+    CK_PW(cudaStreamSynchronize(ctx->stream), "pairwise marginals sync");
+    return GABP_OK;
+}
+
+int gabp_pw_residual(gabp_pw *w, double *rel) {
+    if (!w || !rel) return w ? pfail(w, GABP_ERR_ARG, "rel must not be NULL") : GABP_ERR_ARG;
+    gabp_ctx *ctx = w->ctx;
+    DeviceGuard dg(ctx->dev);
+    CK_PW(gabp::pw_marginals(ctx->p, w->Pd, w->hv, w->msg[w->cur], w->c, nullptr, nullptr, 1, ctx->stream),
+          "pairwise mean");
+    CK_PW(gabp::launch_residual_mu(ctx->p, ctx->stream), "residual kernels");
+    CK_PW(cudaMemcpyAsync(ctx->hscal, ctx->p.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "residual copy");
+    CK_PW(cudaStreamSynchronize(ctx->stream), "residual sync");
+    const double r2 = ctx->hscal[0], b2 = ctx->hscal[1];
+    *rel = b2 > 0.0 ? std::sqrt(r2) / std::sqrt(b2) : std::sqrt(r2);
+    return GABP_OK;
+}
+
+int gabp_pw_reset(gabp_pw *w) {
+    if (!w) return GABP_ERR_ARG;
+    DeviceGuard dg(w->ctx->dev);
+    CK_PW(gabp::pw_zero(w->ctx->p, w->msg[0], w->ctx->stream), "pairwise reset");
+    CK_PW(cudaStreamSynchronize(w->ctx->stream), "pairwise reset sync");
+    w->cur = 0;
+    w->iters = 0;
+    w->c = 1.0;
+    return GABP_OK;
+}
+
+int64_t gabp_pw_iterations(const gabp_pw *w) { return w ? w->iters : -1; }
+
+const char *gabp_pw_last_error(const gabp_pw *w) { return w ? w->err.c_str() : ""; }
+
+void gabp_pw_destroy(gabp_pw *w) {
+    if (!w) return;
+    DeviceGuard dg(w->ctx->dev);
+    pw_free(w);
+    delete w;
+}
+
 int gabp_wsnet_warm_start(gabp_ctx *c, gabp_wsnet *net) {
     if (!c || !net) return c ? fail(c, GABP_ERR_ARG, "net must not be NULL") : GABP_ERR_ARG;
     if (gabp::wsnet_device(net) != c->dev) return fail(c, GABP_ERR_ARG, "network and context on different devices");

@@ -63,6 +63,18 @@ cudaError_t launch_obs_precompute(const DevProblem &p, const double *raw_xy, con
 cudaError_t launch_rhs_norm(const DevProblem &p, cudaStream_t st);   // scal[1] = ||b||^2
 // residual of the messages in buffer src; leaves ||r||^2 in scal[0] (beliefs recomputed)
 cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st);
+// ---- the paper's pairwise re-weighted form (gabp_pairwise.cu) ----
+// coefficients P_ii (n), h (n), P_{i, i + off_d} (12 n) in the context's precision; messages are
+// 12 n (a, b) pairs per buffer
+cudaError_t pw_setup(const DevProblem &p, void *Pd, void *hv, void *Pn, cudaStream_t st);
+cudaError_t pw_zero(const DevProblem &p, void *msg, cudaStream_t st);
+cudaError_t pw_iterate(const DevProblem &p, const void *Pd, const void *hv, const void *Pn, const void *src, void *dst,
+                       double c, double eta, cudaStream_t st);
+// marginals into mean / var (FP64, var may be NULL), or (to_residual) the mean into p.mu64
+cudaError_t pw_marginals(const DevProblem &p, const void *Pd, const void *hv, const void *msg, double c, double *mean,
+                         double *var, int to_residual, cudaStream_t st);
+// residual of the mean already in p.mu64 (double-float pairs for FP32 contexts, FP64 otherwise)
+cudaError_t launch_residual_mu(const DevProblem &p, cudaStream_t st);
 cudaError_t launch_marginals(const DevProblem &p, int src, double *mean, double *var,
                              cudaStream_t st);
 

@@ -691,6 +691,22 @@ cudaError_t launch_df_precompute(const DevProblem &p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// the residual of a mean already in p.mu64 (double-float pairs for FP32 contexts, FP64 values
+// for FP64 contexts): the kernels after the mean in launch_residual
+cudaError_t launch_residual_mu(const DevProblem &p, cudaStream_t st) {
+    if (p.prec == 0) {
+        if (p.m > 0) k_obs_err_df<<<nblocks(p.m), TPB, 0, st>>>(p);
+        k_Lmu_df<<<nblocks(p.n), TPB, 0, st>>>(p);
+        k_res_df<<<RES_BLOCKS, TPB, 0, st>>>(p);
+    } else {
+        if (p.m > 0) k_obs_err<<<nblocks(p.m), TPB, 0, st>>>(p);
+        k_Lmu<<<nblocks(p.n), TPB, 0, st>>>(p);
+        k_res<<<RES_BLOCKS, TPB, 0, st>>>(p);
+    }
+    k_final_sum<<<1, TPB, 0, st>>>(p.part, RES_BLOCKS, p.scal);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st) {
     cudaError_t e = launch_beliefs(p, src, st);
     if (e != cudaSuccess) return e;
