@@ -289,6 +289,7 @@ def own_arm(args):
                      "launch_ms": iter_ms},
     }
     if rank == 0 and not args.no_e2e:
+        line["pairwise_form"] = pairwise_rate(p, local)
         line["time_to_1e-5"] = warm_vs_cold(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
@@ -296,6 +297,24 @@ def own_arm(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def pairwise_rate(p, device: int):
+    """Iteration rate of the paper's pairwise re-weighted form (13-point pair factors, App. A)
+    on the same workload: 12 incoming + 12 outgoing (a, b) pairs read, 12 written, and 14
+    coefficients per node per iteration (FP32: 344 B/node)."""
+    import torch
+    from paper_2404_12968_gb300 import Pairwise, Solver
+    with Solver(p, precision="fp32", device=device) as s, Pairwise(s) as pw:
+        pw.iterate(5, 20.0, 0.6)
+        torch.cuda.synchronize(device)
+        t = time.perf_counter()
+        pw.iterate(50, 20.0, 0.6)
+        dt = (time.perf_counter() - t) / 50
+    nbytes = 344.0 * p.n
+    peak, _ = measured_peak_gbs()
+    return {"ms_per_iter": dt * 1e3, "node_updates_per_s": p.n / dt, "algorithmic_gbs": nbytes / dt / 1e9,
+            "frac_of_measured_hbm": nbytes / dt / 1e9 / peak, "bytes_per_node": 344}
 
 
 def warm_vs_cold(device: int):
