@@ -237,10 +237,14 @@ void gabp_destroy(gabp_ctx *ctx);
 /* ---------------------------------------------------------------------------------------
  * Batches: many independent problems (ensemble members, successive analysis windows) of
  * uneven sizes iterated together.  Every iteration of the whole batch is ONE persistent
- * kernel launch (the column-sweep kernel over the strips of all problems; FP32 messages),
- * replayed from a CUDA graph; the per-problem residual checks are a second graph.  The strip
- * height is chosen by the autotuner (timed candidates on this batch at create time; the choice
- * is cached per device and batch shape in the file named by GABP_AUTOTUNE_CACHE, if set).
+ * kernel launch over the work items of all active problems (FP32 messages), replayed from a
+ * CUDA graph; the per-problem residual checks are a second graph.  Two kernels serve batches:
+ * the TMA kernel over 30 x 22 or 30 x 30 tiles (tensor copies for problems with nx a multiple of 4,
+ * cp.async copies of the same tiles for the others) and the column-sweep kernel over strips of
+ * 16, 32, 64 or 128 rows.  The autotuner times every candidate on this batch at create time
+ * and keeps the fastest (cached per device and batch shape in the file named by
+ * GABP_AUTOTUNE_CACHE, if set).  Messages are bit-identical to single-problem contexts
+ * whichever kernel runs.
  * --------------------------------------------------------------------------------------- */
 typedef struct gabp_batch gabp_batch;   /* opaque; owns the device memory of all its problems */
 
@@ -256,10 +260,14 @@ typedef struct {
 
 /*
  * Create a batch of `count` problems (each built as in gabp_create: Sec. 3.1 and Sec. 3.2).
- * opt: NULL = defaults; precision must be GABP_FP32; opt->tile_y, if non-zero, fixes the
- * strip height (16, 32, 64 or 128) instead of the autotuner; tol, check_every (rounded up to
- * even), max_iters, device and stream apply to the whole batch.  Host arrays are read during
- * the call only.  Errors as for gabp_create; the failing problem's index is in the message.
+ * opt: NULL = defaults; precision must be GABP_FP32; opt->kernel GABP_KERNEL_AUTO (the
+ * autotuner's choice among both kernels), GABP_KERNEL_TMA or GABP_KERNEL_SWEEP (the
+ * autotuner's choice among that kernel's shapes; others: GABP_ERR_ARG); opt->tile_y, if
+ * non-zero, fixes the configuration instead of the autotuner: 22 or 30 = the TMA kernel's tile
+ * height, 16, 32, 64 or 128 = the sweep kernel's strip height; tol, check_every (rounded up
+ * to even), max_iters, device and stream apply
+ * to the whole batch.  Host arrays are read during the call only.  Errors as for gabp_create;
+ * the failing problem's index is in the message.
  */
 int gabp_batch_create(gabp_batch **out, int count, const gabp_problem *problems, const gabp_options *opt);
 
@@ -270,6 +278,8 @@ int gabp_batch_create(gabp_batch **out, int count, const gabp_problem *problems,
  *                 reaches it stops being updated at the next check (every check_every
  *                 iterations).  GABP_ERR_TIMEOUT after max_iters, GABP_ERR_DIVERGED if a
  *                 residual becomes non-finite.
+ * GABP_ERR_TIMEOUT also if a bounded wait inside the TMA kernel gave up (reported at the end
+ * of the call or at the next residual check; the messages are then unspecified).
  */
 int gabp_batch_iterate(gabp_batch *b, int n_iters, double damping);
 
@@ -279,10 +289,12 @@ int gabp_batch_residuals(gabp_batch *b, double *rel);
 /* Marginals of problem `index` (as gabp_marginals). */
 int gabp_batch_marginals(gabp_batch *b, int index, double *mean, double *var);
 
-/* Statistics of problem `index` (iterations it has been updated, last residual, sizes). */
+/* Statistics of problem `index` (iterations it has been updated, last residual, sizes; kernel
+ * is GABP_KERNEL_TMA or GABP_KERNEL_SWEEP, tile_x x tile_y its tile or strip shape). */
 int gabp_batch_get_stats(const gabp_batch *b, int index, gabp_stats *stats);
 
-/* Strip height in use (chosen by the autotuner or opt.tile_y). */
+/* Tile or strip height in use (chosen by the autotuner or opt.tile_y): 22 or 30 for the TMA
+ * kernel, 16, 32, 64 or 128 for the sweep kernel. */
 int gabp_batch_strip_height(const gabp_batch *b);
 
 const char *gabp_batch_last_error(const gabp_batch *b);

@@ -237,7 +237,17 @@ class Batch:
 
     @property
     def strip_height(self) -> int:
+        """Tile height of the TMA kernel (22, 30) or strip height of the sweep kernel."""
         return gabp_batch_strip_height(self.handle)
+
+    @property
+    def kernel(self) -> int:
+        """GABP_KERNEL_TMA or GABP_KERNEL_SWEEP: the kernel iterating this batch."""
+        return self.stats(0)["kernel"]
+
+    @property
+    def kernel_name(self) -> str:
+        return "k_fused_tma (batched)" if self.kernel == GABP_KERNEL_TMA else "k_sweep_batch"
 
     def close(self):
         if getattr(self, "handle", None):

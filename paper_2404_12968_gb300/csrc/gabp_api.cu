@@ -690,10 +690,17 @@ struct gabp_batch {
     cudaStream_t cap = nullptr;
     gabp_options opt{};
     std::vector<gabp_ctx *> inst;
+    int kernel = GABP_KERNEL_SWEEP;   // GABP_KERNEL_TMA or GABP_KERNEL_SWEEP
     gabp::DevProblem *d_table = nullptr;
-    int *d_prefix = nullptr;     // count + 1 strip offsets
-    int *d_active = nullptr;     // count flags
-    int *h_active = nullptr;     // pinned mirror
+    int *d_prefix = nullptr;     // sweep: count + 1 strip offsets
+    int *d_active = nullptr;     // sweep: count active flags
+    int *h_active = nullptr;     // pinned: count active flags
+    int *d_items = nullptr;      // TMA: [nitems, pad, (problem, tile) x all_tiles]
+    int *h_items = nullptr;      // pinned mirror
+    int *d_err = nullptr;        // TMA: a bounded wait in the batched kernel gave up
+    gabp::TmaMapsGlobal *d_maps = nullptr;   // TMA: the problems' tensor maps
+    int all_tiles = 0;           // TMA: tiles of all problems at the current height (grid bound)
+    int maps_ty = 0;             // TMA: tile height the tensor maps were encoded for
     double *h_scal = nullptr;    // pinned, 2 per problem
     int H = 64;
     int total_strips = 0;
@@ -739,27 +746,114 @@ void batch_drop_graphs(gabp_batch *b) {
     b->g_H = 0;
 }
 
-int batch_set_height(gabp_batch *b, int H) {
+int tma_tiles(const gabp::DevProblem &p, int ty) { return ((p.nx + 29) / 30) * ((p.ny + ty - 1) / ty); }
+
+constexpr int TMA_MIN_TY = 22;   // the smallest batched TMA tile height (sizes the work-item list)
+
+cudaError_t batch_launch(gabp_batch *b, int src, double beta, cudaStream_t st) {
     const int count = (int)b->inst.size();
-    std::vector<int> pre(count + 1, 0);
-    for (int i = 0; i < count; ++i)
-        pre[i + 1] = pre[i] + gabp::sweep_strips(b->inst[i]->p.nx, b->inst[i]->p.ny, H);
-    BK(cudaMemcpyAsync(b->d_prefix, pre.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, b->stream),
-       "upload strip offsets");
-    BK(cudaStreamSynchronize(b->stream), "sync");
-    b->H = H;
-    b->total_strips = pre[count];
+    if (b->kernel == GABP_KERNEL_TMA) {
+        gabp::TmaBatchArgs ba;
+        ba.maps = b->d_maps;
+        ba.table = b->d_table;
+        ba.nitems = b->d_items;
+        ba.items = reinterpret_cast<const int2 *>(b->d_items + 2);
+        ba.err = b->d_err;
+        // the grid does not depend on the active set, so captured graphs stay valid when it changes
+        return gabp::launch_tma_batch(ba, b->inst[0]->p, b->H, b->all_tiles, src, beta, st);
+    }
+    return gabp::launch_sweep_batch(b->d_table, b->d_prefix, b->d_active, count, b->total_strips, src, beta, b->H,
+                                    st);
+}
+
+// Upload the active set (h_active[0 .. count)): flags for the sweep kernel; for the TMA kernel
+// the (problem, tile) work items of the active problems.
+int batch_upload_active(gabp_batch *b) {
+    const int count = (int)b->inst.size();
+    if (b->kernel == GABP_KERNEL_TMA) {
+        int k = 0;
+        for (int i = 0; i < count; ++i)
+            if (b->h_active[i]) {
+                const int t = tma_tiles(b->inst[i]->p, b->H);
+                for (int j = 0; j < t; ++j, ++k) {
+                    b->h_items[2 + 2 * k] = i;
+                    b->h_items[3 + 2 * k] = j;
+                }
+            }
+        b->h_items[0] = k;
+        b->h_items[1] = 0;
+        BK(cudaMemcpyAsync(b->d_items, b->h_items, sizeof(int) * (2 + 2 * (size_t)k), cudaMemcpyHostToDevice,
+                           b->stream),
+           "upload work items");
+        return GABP_OK;
+    }
+    BK(cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int) * count, cudaMemcpyHostToDevice, b->stream),
+       "upload active flags");
     return GABP_OK;
 }
 
-cudaError_t batch_launch(gabp_batch *b, int src, double beta, cudaStream_t st) {
-    return gabp::launch_sweep_batch(b->d_table, b->d_prefix, b->d_active, (int)b->inst.size(), b->total_strips,
-                                    src, beta, b->H, st);
+// Tensor maps of the problems whose rows are 16-byte strided, with boxes for 30 x ty tiles (the
+// batched TMA kernel copies the other problems' tiles with cp.async).
+int batch_encode_maps(gabp_batch *b, int ty) {
+    const int count = (int)b->inst.size();
+    std::vector<gabp::TmaMapsGlobal> maps(count);
+    std::memset((void *)maps.data(), 0, sizeof(gabp::TmaMapsGlobal) * count);
+    for (int i = 0; i < count; ++i) {
+        if (!gabp::tma_problem_supported(b->inst[i]->p)) continue;
+        gabp::TmaMaps m{};
+        BK(gabp::make_tma_maps(b->inst[i]->p, 30, ty, m), "tensor map encode");
+        maps[i].planes[0] = m.planes[0];
+        maps[i].planes[1] = m.planes[1];
+        maps[i].optr = m.optr;
+    }
+    BK(cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(gabp::TmaMapsGlobal) * count, cudaMemcpyHostToDevice,
+                       b->stream),
+       "upload tensor maps");
+    BK(cudaStreamSynchronize(b->stream), "sync");   // the host copy of the maps goes out of scope
+    b->maps_ty = ty;
+    return GABP_OK;
 }
 
-int batch_upload_active(gabp_batch *b) {
-    BK(cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int) * b->inst.size(), cudaMemcpyHostToDevice, b->stream),
-       "upload active flags");
+// Kernel configuration of the batch: H = 22 or 30 selects the batched TMA kernel (30 x H tiles),
+// 16, 32, 64 or 128 the sweep kernel with strips of H rows.  The active set is re-uploaded in the
+// layout the kernel reads.
+int batch_set_height(gabp_batch *b, int H) {
+    const int count = (int)b->inst.size();
+    if (gabp::tma_batch_shape_supported(H)) {
+        b->kernel = GABP_KERNEL_TMA;
+        if (b->maps_ty != H) {
+            int rc = batch_encode_maps(b, H);
+            if (rc) return rc;
+        }
+        b->all_tiles = 0;
+        for (int i = 0; i < count; ++i) b->all_tiles += tma_tiles(b->inst[i]->p, H);
+    } else {
+        std::vector<int> pre(count + 1, 0);
+        for (int i = 0; i < count; ++i)
+            pre[i + 1] = pre[i] + gabp::sweep_strips(b->inst[i]->p.nx, b->inst[i]->p.ny, H);
+        BK(cudaMemcpyAsync(b->d_prefix, pre.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, b->stream),
+           "upload strip offsets");
+        b->kernel = GABP_KERNEL_SWEEP;
+        b->total_strips = pre[count];
+    }
+    b->H = H;
+    int rc = batch_upload_active(b);
+    if (rc) return rc;
+    BK(cudaStreamSynchronize(b->stream), "sync");
+    return GABP_OK;
+}
+
+// A bounded wait of the batched TMA kernel gave up: report it (and clear the flag).
+int batch_check_error(gabp_batch *b) {
+    if (b->kernel != GABP_KERNEL_TMA) return GABP_OK;
+    int h = 0;
+    BK(cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "error flag copy");
+    BK(cudaStreamSynchronize(b->stream), "error flag sync");
+    if (h) {
+        BK(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream), "error flag reset");
+        BK(cudaStreamSynchronize(b->stream), "error flag sync");
+        return bfail(b, GABP_ERR_TIMEOUT, "a bounded wait inside the batched iteration kernel gave up");
+    }
     return GABP_OK;
 }
 
@@ -848,6 +942,7 @@ int batch_residuals(gabp_batch *b) {
     }
     BK(cudaGraphLaunch(b->g_res, b->stream), "residual graph launch");
     BK(cudaStreamSynchronize(b->stream), "residual sync");
+    if (int rc = batch_check_error(b)) return rc;
     if (b->cur != 0) {   // only the parity-0 graph is kept
         cudaGraphExecDestroy(b->g_res);
         b->g_res = nullptr;
@@ -887,7 +982,7 @@ int autotune_cache_lookup(const std::string &key) {
         if (sp != std::string::npos && s.compare(0, sp, key) == 0) found = std::atoi(s.c_str() + sp + 1);
     }
     std::fclose(f);
-    return gabp::sweep_shape_supported(found) ? found : 0;
+    return (gabp::tma_batch_shape_supported(found) || gabp::sweep_shape_supported(found)) ? found : 0;
 }
 
 void autotune_cache_store(const std::string &key, int value) {
@@ -899,13 +994,16 @@ void autotune_cache_store(const std::string &key, int value) {
     std::fclose(f);
 }
 
-// Time each candidate strip height on this batch and keep the fastest; messages are
-// re-initialised afterwards.
-int batch_autotune(gabp_batch *b) {
-    const std::string key = autotune_key(b);
+// Time each candidate (the sweep kernel at each strip height, the batched TMA kernel at each tile
+// height; `kernels` = GABP_KERNEL_AUTO for both, else the one kernel) on this batch and keep the
+// fastest; messages are re-initialised afterwards.
+int batch_autotune(gabp_batch *b, int kernels) {
+    const std::string key = autotune_key(b) + " k" + std::to_string(kernels);
     int best = autotune_cache_lookup(key);
     if (!best) {
-        const int cands[4] = {16, 32, 64, 128};
+        std::vector<int> cands;
+        if (kernels != GABP_KERNEL_TMA) cands.insert(cands.end(), {16, 32, 64, 128});
+        if (kernels != GABP_KERNEL_SWEEP) cands.insert(cands.end(), {22, 30});
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
         BK(cudaEventCreate(&e0), "event");
@@ -947,6 +1045,13 @@ void batch_free(gabp_batch *b) {
     if (b->d_table) cudaFree(b->d_table);
     if (b->d_prefix) cudaFree(b->d_prefix);
     if (b->d_active) cudaFree(b->d_active);
+    if (b->d_err) cudaFree(b->d_err);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->h_items) cudaFreeHost(b->h_items);
+    b->d_items = b->h_items = nullptr;
+    if (b->d_maps) cudaFree(b->d_maps);
+    b->d_err = nullptr;
+    b->d_maps = nullptr;
     if (b->h_active) cudaFreeHost(b->h_active);
     if (b->h_scal) cudaFreeHost(b->h_scal);
     b->d_table = nullptr;
@@ -961,8 +1066,15 @@ void batch_free(gabp_batch *b) {
 int batch_create_impl(gabp_batch *b, int count, const gabp_problem *problems) {
     if (count < 1 || !problems) return bfail(b, GABP_ERR_ARG, "count must be >= 1 and problems non-NULL");
     if (b->opt.precision != GABP_FP32) return bfail(b, GABP_ERR_ARG, "batches use FP32 messages");
-    if (b->opt.tile_y && !gabp::sweep_shape_supported(b->opt.tile_y))
+    const int kreq = b->opt.kernel, ty = b->opt.tile_y;
+    if (kreq != GABP_KERNEL_AUTO && kreq != GABP_KERNEL_TMA && kreq != GABP_KERNEL_SWEEP)
+        return bfail(b, GABP_ERR_ARG, "batches run the TMA or the sweep kernel");
+    if (kreq == GABP_KERNEL_TMA && ty && !gabp::tma_batch_shape_supported(ty))
+        return bfail(b, GABP_ERR_ARG, "the batched TMA kernel uses 30 x 22 or 30 x 30 tiles");
+    if (kreq == GABP_KERNEL_SWEEP && ty && !gabp::sweep_shape_supported(ty))
         return bfail(b, GABP_ERR_ARG, "strip height must be 16, 32, 64 or 128");
+    if (kreq == GABP_KERNEL_AUTO && ty && !gabp::tma_batch_shape_supported(ty) && !gabp::sweep_shape_supported(ty))
+        return bfail(b, GABP_ERR_ARG, "strip height must be 16, 32, 64 or 128 (sweep) or 22, 30 (TMA)");
     gabp_options io = b->opt;
     io.stream = b->stream;
     io.kernel = GABP_KERNEL_SWEEP;
@@ -988,17 +1100,18 @@ int batch_create_impl(gabp_batch *b, int count, const gabp_problem *problems) {
     }
     BK(cudaMemcpyAsync(b->d_table, table.data(), sizeof(gabp::DevProblem) * count, cudaMemcpyHostToDevice, b->stream),
        "upload table");
-    int rc = batch_upload_active(b);
-    if (rc) return rc;
+    int max_tiles = 0;
+    for (int i = 0; i < count; ++i) max_tiles += tma_tiles(b->inst[i]->p, TMA_MIN_TY);
+    BK(cudaMalloc((void **)&b->d_maps, sizeof(gabp::TmaMapsGlobal) * count), "alloc tensor maps");
+    BK(cudaMalloc((void **)&b->d_items, sizeof(int) * (2 + 2 * (size_t)max_tiles)), "alloc work items");
+    BK(cudaMallocHost((void **)&b->h_items, sizeof(int) * (2 + 2 * (size_t)max_tiles)), "alloc pinned items");
+    BK(cudaMalloc((void **)&b->d_err, sizeof(int)), "alloc error flag");
+    BK(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream), "memset");
     b->iters.assign(count, 0);
     b->res.assign(count, NAN);
     if (b->opt.check_every & 1) b->opt.check_every += 1;
-    if (b->opt.tile_y) {
-        rc = batch_set_height(b, b->opt.tile_y);
-    } else {
-        rc = batch_autotune(b);
-    }
-    return rc;
+    if (ty) return batch_set_height(b, ty);
+    return batch_autotune(b, kreq);
 }
 
 }  // namespace
@@ -1062,7 +1175,7 @@ int gabp_batch_iterate(gabp_batch *b, int n_iters, double damping) {
         rc = batch_run(b, n_iters, damping);
         if (rc) return rc;
         BK(cudaStreamSynchronize(b->stream), "iterate sync");
-        return GABP_OK;
+        return batch_check_error(b);
     }
     int rc;
     if (b->cur == 1) {   // checks run at parity 0
@@ -1112,7 +1225,7 @@ int gabp_batch_get_stats(const gabp_batch *b, int index, gabp_stats *s) {
     const int rc = gabp_get_stats(b->inst[index], s);
     s->iterations = b->iters[index];
     s->last_residual = b->res[index];
-    s->kernel = GABP_KERNEL_SWEEP;
+    s->kernel = b->kernel;
     s->tile_x = 30;
     s->tile_y = b->H;
     return rc;

@@ -25,6 +25,7 @@
 // Requirements (checked on the host): FP32 messages, nx a multiple of 4.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cstring>
 
 #include "gabp_device.cuh"
 #include "gabp_internal.h"
@@ -45,6 +46,23 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Asynchronous copy of `size` (4 or 8) bytes, of which the first `src_bytes` are read from
+// global memory and the rest zero-filled (src_bytes = 0: a zero, the address is not read).
+template <int SIZE> __device__ __forceinline__ void cp_async_zfill(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"(SIZE), "r"(src_bytes)
+                 : "memory");
+}
+
+// The mbarrier's current phase also waits for this thread's earlier cp.async copies (its
+// pending count is raised now and lowered when they have landed: no net arrival).
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 // Bounded wait on phase `parity` of an mbarrier: gives up after `limit` clock cycles
@@ -209,10 +227,12 @@ template <int TY, int S, int RW> struct TileLayout {
     static_assert(2 * RX <= 256 && RY <= 256 && OXW <= 256 && OY <= 256, "TMA box dimension above 256");
 };
 
-template <int TY, int S, int RW>
-__global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, RW>::MINB) k_fused_tma(const __grid_constant__ CUtensorMap mplanes,
-                                                   const __grid_constant__ CUtensorMap moptr, DevProblem p,
-                                                   int src, float beta) {
+// BATCH: the tiles of several problems (TmaBatchArgs) instead of one; the per-tile work is the
+// same, on the problem that owns the tile.
+template <int TY, int S, int RW, bool BATCH>
+__global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, RW>::MINB)
+    k_fused_tma(const __grid_constant__ CUtensorMap mplanes, const __grid_constant__ CUtensorMap moptr,
+                const __grid_constant__ DevProblem p, const __grid_constant__ TmaBatchArgs ba, int src, float beta) {
     using LY = TileLayout<TY, S, RW>;
     constexpr int RX = LY::RX, RY = LY::RY, BX = LY::BX, BY = LY::BY, OXW = LY::OXW;
     constexpr int TW = LY::TW, TNT = LY::TNT;
@@ -220,36 +240,99 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + LY::bar_off);
     int *flag = reinterpret_cast<int *>(smem + LY::ints_off) + 2 * LY::NI;
 
-    const int nx = p.nx, ny = p.ny;
-    const int64_t n = p.n;
-    const int ntx = (nx + TTX - 1) / TTX;
-    const int ntiles = ntx * ((ny + TY - 1) / TY);
+    const int ntx1 = (p.nx + TTX - 1) / TTX;   // single problem: tiles per row
+    const int ntiles = BATCH ? *ba.nitems : ntx1 * ((p.ny + TY - 1) / TY);
     const int G = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float2 *Q = (float2 *)p.P[src ^ 1];
-    const float *O = (const float *)p.O[src];
-    float *OQ = (float *)p.O[src ^ 1];
-    const float var_prior = p.var_f;
-    const float aC_in = p.aC_f[4];
     const float2 beta2 = f2(beta, beta);
 
-    auto issue = [&](int stage, int tile) {
-        const int x0 = (tile % ntx) * TTX, y0 = (tile / ntx) * TY;
+    // BATCH: work item -> (problem, tile of that problem)
+    auto locate = [&](int item, int &prob, int &tile) {
+        const int2 it = ba.items[item];
+        prob = it.x;
+        tile = it.y;
+    };
+
+    // single problem (thread 0): the tile's two tensor loads
+    auto issue = [&](int stage, int item) {
         unsigned char *base = smem + stage * LY::stage;
         const uint32_t bar = smem_addr(&bars[stage]);
+        const int x0 = (item % ntx1) * TTX, y0 = (item / ntx1) * TY;
         mbar_expect_tx(bar, LY::plane_bytes + LY::optr_bytes);
         tma_load_3d(smem_addr(base), &mplanes, 2 * (x0 - 2), y0 - 2, 0, bar);
         tma_load_2d(smem_addr(base + a128(LY::plane_bytes)), &moptr, (x0 - 2) & ~3, y0 - 2, bar);
     };
 
+    // BATCH (every thread; a stage barrier counts one arrival per warp): a problem whose nx is
+    // a multiple of 4 (16-byte row strides) is loaded by the tensor copies of its own maps,
+    // issued by thread 0; any other problem by cp.async copies of the same boxes (a warp per
+    // box row), zero-filled outside the grid as the tensor copies are, each thread's copies
+    // tracked by the barrier
+    auto fill = [&](int stage, int item) {
+        unsigned char *base = smem + stage * LY::stage;
+        const uint32_t bar = smem_addr(&bars[stage]);
+        int prob, tile;
+        locate(item, prob, tile);
+        const DevProblem &q = ba.table[prob];
+        const int qnx = q.nx, qny = q.ny;
+        const int qtx = (qnx + TTX - 1) / TTX;
+        const int x0 = (tile % qtx) * TTX, y0 = (tile / qtx) * TY;
+        if (qnx % 4 == 0) {
+            if (tid == 0) {
+                mbar_expect_tx(bar, LY::plane_bytes + LY::optr_bytes);
+                tma_load_3d(smem_addr(base), &ba.maps[prob].planes[src], 2 * (x0 - 2), y0 - 2, 0, bar);
+                tma_load_2d(smem_addr(base + a128(LY::plane_bytes)), &ba.maps[prob].optr, (x0 - 2) & ~3, y0 - 2,
+                            bar);
+            } else if (lane == 0) {
+                mbar_arrive(bar);
+            }
+            return;
+        }
+        const float2 *P = (const float2 *)q.P[src];
+        const int64_t qn = q.n;
+        const uint32_t dp = smem_addr(base);
+        for (int row = warp; row < 5 * RY; row += TW) {   // [5][RY][RX] cells from (x0 - 2, y0 - 2)
+            const int d = row / RY, gy = y0 - 2 + (row - d * RY);
+            const bool rin = gy >= 0 && gy < qny;
+            const float2 *src_row = P + d * qn + (int64_t)(rin ? gy : 0) * qnx;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int cx = lane + 32 * h, gx = x0 - 2 + cx;
+                if (cx < RX) {
+                    const bool in = rin && gx >= 0 && gx < qnx;
+                    cp_async_zfill<8>(dp + 8u * (row * RX + cx), in ? src_row + gx : P, in ? 8u : 0u);
+                }
+            }
+        }
+        const int xs = (x0 - 2) & ~3;
+        const uint32_t dw = smem_addr(base + a128(LY::plane_bytes));
+        for (int r = warp; r < LY::OY; r += TW) {   // [OY][OXW] indices from (xs, y0 - 2)
+            const int gy = y0 - 2 + r;
+            const bool rin = gy >= 0 && gy < qny;
+            const int *src_row = q.optr + (int64_t)(rin ? gy : 0) * qnx;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int cx = lane + 32 * h, gx = xs + cx;
+                if (cx < OXW) {
+                    const bool in = rin && gx >= 0 && gx < qnx;
+                    cp_async_zfill<4>(dw + 4u * (r * OXW + cx), in ? src_row + gx : q.optr, in ? 4u : 0u);
+                }
+            }
+        }
+        cp_async_arrive(bar);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar);
+    };
+
     if (tid == 0) {
-        for (int s = 0; s <= S; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        for (int s = 0; s < S; ++s) mbar_init(smem_addr(&bars[s]), BATCH ? TW : 1);
+        mbar_init(smem_addr(&bars[S]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         *flag = 0;
     }
     __syncthreads();
-    if (p.debug_stall) {
+    if (!BATCH && p.debug_stall) {
         // failure-detection test: wait on a barrier that nothing arrives on, before any copy is
         // issued; the bounded wait runs out, the block raises the error flag and returns
         if (tid == 0 && !mbar_wait(smem_addr(&bars[S]), 0, 1LL << 22)) {
@@ -259,28 +342,40 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         __syncthreads();
         if (*flag) return;
     }
-    if (tid == 0)
-        for (int s = 0; s < S; ++s) {
-            const int t = blockIdx.x + s * G;
-            if (t < ntiles) issue(s, t);
-        }
+    for (int s = 0; s < S; ++s) {
+        const int t = blockIdx.x + s * G;
+        if (t >= ntiles) break;
+        if constexpr (BATCH) fill(s, t);
+        else if (tid == 0) issue(s, t);
+    }
 
     // tile coordinates advance by G tiles per step without a division
-    const int step_x = G % ntx, step_y = G / ntx;
-    int tcx = (int)blockIdx.x % ntx, tcy = (int)blockIdx.x / ntx;
+    const int step_x = G % ntx1, step_y = G / ntx1;
+    int tcx = (int)blockIdx.x % ntx1, tcy = (int)blockIdx.x / ntx1;
     int it = 0;
     bool failed = false;
     for (;; ++it) {
         if (it > 0) {
             tcx += step_x;
             tcy += step_y;
-            if (tcx >= ntx) {
-                tcx -= ntx;
+            if (tcx >= ntx1) {
+                tcx -= ntx1;
                 ++tcy;
             }
         }
         const int tile = blockIdx.x + it * G;
         if (tile >= ntiles) break;
+        // the tile's problem: the kernel parameter, or (BATCH) the table entry of its problem
+        int prob = 0, t = tile;
+        if constexpr (BATCH) locate(tile, prob, t);
+        const DevProblem &cur = BATCH ? ba.table[prob] : p;
+        const int nx = cur.nx, ny = cur.ny;
+        const int64_t n = cur.n, m = cur.m;
+        float2 *const Q = (float2 *)cur.P[src ^ 1];
+        const float *const O = (const float *)cur.O[src];
+        float *const OQ = (float *)cur.O[src ^ 1];
+        const float var_prior = cur.var_f;
+        const float aC_in = cur.aC_f[4];
         const int stage = it % S;
         // a thread whose wait ran out skips phase A (its staged indices may be stale) and the
         // barrier after phase A stops the whole block
@@ -289,14 +384,15 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         int *rstart = reinterpret_cast<int *>(smem + LY::ints_off) + (it & 1) * LY::NI;   // [TY]
         int *rpre = rstart + TY;                                                          // [TY + 1]
 
-        const int x0 = tcx * TTX, y0 = tcy * TY;
+        const int x0 = (BATCH ? t % ((nx + TTX - 1) / TTX) : tcx) * TTX;
+        const int y0 = (BATCH ? t / ((nx + TTX - 1) / TTX) : tcy) * TY;
         const int xs = (x0 - 2) & ~3;
         const float2 *sm = reinterpret_cast<const float2 *>(smem + stage * LY::stage);   // [5][RY][RX]
         const int *W = reinterpret_cast<const int *>(smem + stage * LY::stage + a128(LY::plane_bytes));
         auto wptr = [&](int x, int y) { return W[(y - y0 + 2) * OXW + (x - xs)]; };
 
         // ---- A: observation ranges of the tile's rows (last warp), beliefs of the window ----
-        if (ok && p.m > 0 && warp == TW - 1) {
+        if (ok && m > 0 && warp == TW - 1) {
             int st = 0, cnt = 0;
             const int gy = y0 + lane;
             if (lane < TY && gy < ny) {
@@ -326,7 +422,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                 // sums, so that its latency overlaps them (the order of the sum is unchanged)
                 int lo1 = 0, mid1 = 0, hi1 = 0, lo2 = 0, mid2 = 0, hi2 = 0;
                 float2 first1 = f2(0.f, 0.f), first2 = f2(0.f, 0.f);
-                if (p.m > 0) {
+                if (m > 0) {
                     const bool last = gx == nx - 1;
                     mid1 = wptr(gx, gy);
                     lo1 = gx > 0 ? wptr(gx - 1, gy) : mid1;
@@ -372,11 +468,12 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
             break;
         }
         // every thread has finished tile it-1: refill its stage with tile it-1+S
-        if (tid == 0 && it > 0) {
+        if (it > 0) {
             const int t2 = blockIdx.x + (it - 1 + S) * G;
             if (t2 < ntiles) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue((it - 1) % S, t2);
+                if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if constexpr (BATCH) fill((it - 1) % S, t2);
+                else if (tid == 0) issue((it - 1) % S, t2);
             }
         }
 
@@ -396,15 +493,16 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                 const float a[5] = {aC_in, -1.f, -1.f, -1.f, -1.f};
                 cell_factor(a, bs, own, var_prior, beta2, Q + c, n);
             } else {
-                const float a[5] = {p.aC_f[grid_degree(gy, gx, nx, ny)], gx > 0 ? -1.f : 0.f,
+                const float a[5] = {cur.aC_f[grid_degree(gy, gx, nx, ny)], gx > 0 ? -1.f : 0.f,
                                     gx < nx - 1 ? -1.f : 0.f, gy > 0 ? -1.f : 0.f, gy < ny - 1 ? -1.f : 0.f};
                 cell_factor(a, bs, own, var_prior, beta2, Q + c, n);
             }
         }
-        if (p.m > 0) {
+        if (m > 0) {
             const int total = rpre[TY];
-            const float *Wt = (const float *)p.ow;
-            const float *YV = (const float *)p.ovar;
+            const float *Wt = (const float *)cur.ow;
+            const float *YV = (const float *)cur.ovar;
+            const int *ob = cur.obase;
             // observation factors go first to the two warps with one cell row fewer
             for (int q = (tid + TNT - 32 * (TW - 2)) % TNT; q < total; q += TNT) {
                 int lo = 0, hi = TY - 1;   // last row r with rpre[r] <= q
@@ -415,7 +513,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                 }
                 const int r = lo;
                 const int64_t k = rstart[r] + (q - rpre[r]);
-                const int bx = p.obase[k] - (y0 + r) * nx;
+                const int bx = ob[k] - (y0 + r) * nx;
                 const int lx = bx - x0 + 1, ly = r + 1;   // window coordinates of the base node
                 const Belief2 *ob[4] = {&sb[ly * BX + lx], &sb[ly * BX + lx + 1], &sb[(ly + 1) * BX + lx],
                                               &sb[(ly + 1) * BX + lx + 1]};
@@ -445,7 +543,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
     }
 
     if (failed && tid == 0) {
-        atomicExch(p.err, 1);
+        atomicExch(BATCH ? ba.err : p.err, 1);
         // drain this block's outstanding copies (bounded): the prologue issued tiles 0 .. S-1 and
         // the barrier of tile i >= 1 tile i-1+S, so tiles it .. jmax may be in flight
         const int jmax = it == 0 ? S - 1 : it + S - 2;
@@ -457,32 +555,45 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
     }
 }
 
-template <int TY, int S, int RW>
-cudaError_t launch_cfg(const DevProblem &p, const TmaMaps &maps, int src, double beta, cudaStream_t st) {
+// persistent grid of k_fused_tma<TY, S, RW, BATCH>: SMs x resident blocks (set up once per device)
+template <int TY, int S, int RW, bool BATCH> cudaError_t persistent_grid(int &grid) {
     using LY = TileLayout<TY, S, RW>;
     static int grid_cache = 0;
     static int configured_dev = -1;
-    // the tensor maps' boxes must have been encoded for this tile height (the smem layout and
-    // the expected transaction bytes depend on it)
-    if (maps.tx != TTX || maps.ty != TY) return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (configured_dev != dev) {
-        e = cudaFuncSetAttribute(k_fused_tma<TY, S, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::bytes);
+        e = cudaFuncSetAttribute(k_fused_tma<TY, S, RW, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)LY::bytes);
         if (e != cudaSuccess) return e;
         int nsm = 0, per_sm = 0;
         e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tma<TY, S, RW>, LY::TNT, LY::bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tma<TY, S, RW, BATCH>, LY::TNT, LY::bytes);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         grid_cache = nsm * per_sm;
         configured_dev = dev;
     }
+    grid = grid_cache;
+    return cudaSuccess;
+}
+
+template <int TY, int S, int RW>
+cudaError_t launch_cfg(const DevProblem &p, const TmaMaps &maps, int src, double beta, cudaStream_t st) {
+    using LY = TileLayout<TY, S, RW>;
+    // the tensor maps' boxes must have been encoded for this tile height (the smem layout and
+    // the expected transaction bytes depend on it)
+    if (maps.tx != TTX || maps.ty != TY) return cudaErrorInvalidValue;
+    int grid = 0;
+    cudaError_t e = persistent_grid<TY, S, RW, false>(grid);
+    if (e != cudaSuccess) return e;
     const int ntiles = ((p.nx + TTX - 1) / TTX) * ((p.ny + TY - 1) / TY);
-    const int grid = ntiles < grid_cache ? ntiles : grid_cache;
-    k_fused_tma<TY, S, RW><<<grid, LY::TNT, LY::bytes, st>>>(maps.planes[src], maps.optr, p, src, (float)beta);
+    if (ntiles < grid) grid = ntiles;
+    const TmaBatchArgs none{};
+    k_fused_tma<TY, S, RW, false><<<grid, LY::TNT, LY::bytes, st>>>(maps.planes[src], maps.optr, p, none, src,
+                                                                     (float)beta);
     return cudaGetLastError();
 }
 
@@ -536,6 +647,34 @@ cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps) {
     maps.ty = ty;
     maps.valid = true;
     return cudaSuccess;
+}
+
+template <int TY>
+cudaError_t launch_batch_cfg(const TmaBatchArgs &ba, const DevProblem &first, int max_tiles, int src, double beta,
+                             cudaStream_t st) {
+    using LY = TileLayout<TY, 2, 1>;
+    int grid = 0;
+    cudaError_t e = persistent_grid<TY, 2, 1, true>(grid);
+    if (e != cudaSuccess) return e;
+    if (max_tiles < grid) grid = max_tiles;
+    CUtensorMap unused;
+    std::memset(&unused, 0, sizeof unused);
+    k_fused_tma<TY, 2, 1, true><<<grid, LY::TNT, LY::bytes, st>>>(unused, unused, first, ba, src, (float)beta);
+    return cudaGetLastError();
+}
+
+bool tma_batch_shape_supported(int ty) { return ty == 22 || ty == 30; }
+
+// Batched iteration over the 30 x ty tiles of the active problems.  `first` is any one problem
+// of the batch (it stands in for the kernel's single-problem parameters, of which batch mode
+// reads only nx); max_tiles bounds *nitems (the tiles of all problems).
+cudaError_t launch_tma_batch(const TmaBatchArgs &ba, const DevProblem &first, int ty, int max_tiles, int src,
+                             double beta, cudaStream_t st) {
+    if (max_tiles <= 0) return cudaSuccess;
+    if (!ba.maps || !ba.table || !ba.items || !ba.nitems || !ba.err || first.nx < 1) return cudaErrorInvalidValue;
+    if (ty == 22) return launch_batch_cfg<22>(ba, first, max_tiles, src, beta, st);
+    if (ty == 30) return launch_batch_cfg<30>(ba, first, max_tiles, src, beta, st);
+    return cudaErrorInvalidValue;
 }
 
 size_t tma_smem_bytes(int tx, int ty) {

@@ -123,6 +123,24 @@ struct TmaMaps {
     int tx = 0, ty = 0;
     bool valid = false;
 };
+// Batched TMA iteration: the work items are the tiles of the active problems, item k being
+// tile items[k].y of problem items[k].x (k < *nitems); every problem's tensor maps sit in a
+// global array (CUtensorMap's own alignment; zero for a problem whose rows are not 16-byte
+// strided).  *err is raised if a bounded wait ran out.
+struct TmaMapsGlobal {
+    CUtensorMap planes[2];
+    CUtensorMap optr;
+};
+struct TmaBatchArgs {
+    const TmaMapsGlobal *maps;
+    const DevProblem *table;
+    const int2 *items;
+    const int *nitems;
+    int *err;
+};
+bool tma_batch_shape_supported(int ty);   // tile heights of the batched TMA kernel (22, 30)
+cudaError_t launch_tma_batch(const TmaBatchArgs &ba, const DevProblem &first, int ty, int max_tiles, int src,
+                             double beta, cudaStream_t st);
 bool tma_shape_supported(int tx, int ty);
 bool tma_problem_supported(const DevProblem &p);
 cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps);
