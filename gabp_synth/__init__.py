@@ -49,6 +49,7 @@ class Problem:
     noise_var: np.ndarray        # (m,) float64 observation noise variances
     truth: np.ndarray | None = None  # (ny, nx) float64 ground truth, row-major
     meta: dict = field(default_factory=dict)
+    gamma: float = 1.0               # prior scale (precision gamma L^T L)
 
     @property
     def n(self) -> int:
@@ -165,6 +166,34 @@ def scaled_config(side: int, kappa: float, seed: int, n_tracks: int, *, n_unifor
         per_track = int(round(2.5 * side / 1.5))
     return make_problem(side, side, kappa, seed, n_uniform=n_uniform, n_tracks=n_tracks,
                         per_track=per_track, sigma=sigma)
+
+
+def paper_synthetic(side: int, frac: float, seed: int, *, sigma_y: float = 0.1, length: float = 0.15,
+                    sigma: float = 1.1) -> Problem:
+    """The synthetic setting of the grid-size / observation-density comparison (Sec. 4.1 with
+    the hyperparameters of App. E): Matern prior with alpha = 2, nu = 1, lengthscale
+    ``length`` and marginal standard deviation ``sigma`` on the unit square, discretised on
+    side x side nodes of spacing h = 1 / side; a fraction ``frac`` of the grid points observed
+    (uniformly, without replacement) with noise standard deviation ``sigma_y``.
+
+    kappa = sqrt(2 nu) / length and gamma = h^2 / (sigma^2 q) with q = 4 pi kappa^2 (d = 2,
+    nu = 1).  The library's grids have unit spacing; since L_h = h^-2 L_1(kappa h), the same
+    prior is kappa' = kappa h and gamma' = gamma / h^4 at unit spacing, which is what the
+    returned problem carries."""
+    h = 1.0 / side
+    kappa = math.sqrt(2.0) / length
+    q = 4.0 * math.pi * kappa * kappa
+    gamma_u = (h * h / (sigma * sigma * q)) / h ** 4
+    kappa_u = kappa * h
+    rng = np.random.default_rng(70_000 + 1000 * side + seed)
+    truth = sample_truth(side, side, kappa_u, rng) / math.sqrt(gamma_u)
+    m = int(round(frac * side * side))
+    idx = np.sort(rng.choice(side * side, m, replace=False))
+    ox = (idx % side).astype(np.float64)
+    oy = (idx // side).astype(np.float64)
+    y = truth.reshape(-1)[idx] + sigma_y * rng.standard_normal(m)
+    return Problem(side, side, float(kappa_u), ox, oy, y, np.full(m, sigma_y * sigma_y), truth,
+                   dict(seed=seed, frac=frac, sigma_y=sigma_y, length=length, sigma=sigma), gamma=float(gamma_u))
 
 
 def config_batch(seed: int = 0, count: int = 64, lo: int = 128, hi: int = 1024) -> list[Problem]:
