@@ -13,6 +13,9 @@ Contents
       a = row i of L, s = gamma, r = 0.  Zero-Neumann boundary, read as a cell-centred
       ghost equal to the boundary value, so row i of L has kappa^2 + deg(i) on the
       diagonal and -1 on each existing 4-neighbour (deg(i) = number of neighbours);
+      alpha = 4 (Sec. 3.1, the SPDE with alpha/2 = 2; App. C, higher powers of the operator
+      as powers of its matrix): the operator matrix is L^2, one factor per cell with
+      a = row i of L^2 (13-point stencil), P = gamma (L^2)^T L^2;
     - observations (Sec. 3.2, "Including Observations", generalised to a row of H):
       one factor per observation with the four bilinear weights of its location,
       s = 1 / noise variance, r = y.
@@ -35,7 +38,7 @@ from .build import build_oracle, library_path
 __all__ = [
     "FactorList", "build_factors", "prior_factors", "obs_factors", "bilinear_base_weights",
     "concat", "gabp", "init_messages", "factor_update", "beliefs", "apply_A", "rhs",
-    "residual", "exact_mean", "exact_variances", "dense_A", "band_solve", "lib",
+    "residual", "exact_mean", "exact_variances", "dense_A", "band_solve", "half_bandwidth", "lib",
 ]
 
 _LIB = None
@@ -121,12 +124,25 @@ def concat(*lists: FactorList) -> FactorList:
                       np.concatenate([fl.s for fl in lists]), np.concatenate([fl.r for fl in lists]))
 
 
-def prior_factors(nx: int, ny: int, kappa: float, gamma: float = 1.0) -> FactorList:
-    """One factor per cell: a = row of L = kappa^2 I + graph Laplacian (zero-Neumann).
+# slot offsets (dx, dy) of the alpha = 4 cell factor: the cell, its 4 neighbours, the 4
+# diagonal neighbours, the 4 nodes two steps away
+_L2_OFFSETS = [(0, 0), (-1, 0), (1, 0), (0, -1), (0, 1), (-1, -1), (1, -1), (-1, 1), (1, 1),
+               (-2, 0), (2, 0), (0, -2), (0, 2)]
+
+
+def prior_factors(nx: int, ny: int, kappa: float, gamma: float = 1.0, alpha: int = 2) -> FactorList:
+    """One factor per cell: a = row of L = kappa^2 I + graph Laplacian (zero-Neumann), or for
+    alpha = 4 a row of L^2.
 
     Slot order within a cell factor: the cell itself, then its west (x-1), east (x+1),
-    south (y-1) and north (y+1) neighbours, those that exist.
+    south (y-1) and north (y+1) neighbours, those that exist; for alpha = 4 then the
+    diagonal neighbours (x-1, y-1), (x+1, y-1), (x-1, y+1), (x+1, y+1) and the nodes
+    (x-2, y), (x+2, y), (x, y-2), (x, y+2), those that exist.
     """
+    if alpha == 4:
+        return _prior_factors_l2(nx, ny, kappa, gamma)
+    if alpha != 2:
+        raise ValueError("alpha must be 2 or 4")
     n = nx * ny
     ii, jj = np.divmod(np.arange(n, dtype=np.int64), nx)
     c = ii * nx + jj
@@ -142,6 +158,37 @@ def prior_factors(nx: int, ny: int, kappa: float, gamma: float = 1.0) -> FactorL
     np.cumsum(counts, out=ptr[1:])
     return FactorList(n, ptr, cand[exists].astype(np.int64), coefs[exists].astype(np.float64),
                       np.full(n, float(gamma)), np.zeros(n))
+
+
+def _prior_factors_l2(nx: int, ny: int, kappa: float, gamma: float) -> FactorList:
+    """Rows of L^2: L assembled from the alpha = 2 factor rows, squared by a sparse matrix
+    product (a library step), each row read out in the slot order of ``_L2_OFFSETS``."""
+    import scipy.sparse as sp
+    fl1 = _prior_factors_l1(nx, ny, kappa)
+    rows = np.repeat(np.arange(fl1.nf), np.diff(fl1.ptr))
+    L = sp.csr_matrix((fl1.coef, (rows, fl1.var)), shape=(fl1.n, fl1.n))
+    L2 = (L @ L).tocsr()
+    n = nx * ny
+    ii, jj = np.divmod(np.arange(n, dtype=np.int64), nx)
+    cand, exists = [], []
+    for dx, dy in _L2_OFFSETS:
+        x, y = jj + dx, ii + dy
+        cand.append(y * nx + x)
+        exists.append((x >= 0) & (x < nx) & (y >= 0) & (y < ny))
+    cand = np.stack(cand, axis=1)
+    exists = np.stack(exists, axis=1)
+    var = cand[exists].astype(np.int64)
+    cell = np.repeat(np.arange(n), exists.sum(axis=1))
+    coef = np.asarray(L2[cell, var]).reshape(-1).astype(np.float64)
+    ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(exists.sum(axis=1), out=ptr[1:])
+    # the slots are exactly the nonzeros of each row of L^2
+    assert L2.nnz == var.size and np.all(coef != 0.0)
+    return FactorList(n, ptr, var, coef, np.full(n, float(gamma)), np.zeros(n))
+
+
+def _prior_factors_l1(nx: int, ny: int, kappa: float) -> FactorList:
+    return prior_factors(nx, ny, kappa, 1.0, 2)
 
 
 def bilinear_base_weights(nx: int, ny: int, ox: np.ndarray, oy: np.ndarray):
@@ -182,9 +229,9 @@ def obs_factors(nx: int, ny: int, ox, oy, y, noise_var) -> FactorList:
                       w.reshape(-1).copy(), 1.0 / nv, np.asarray(y, np.float64).copy())
 
 
-def build_factors(nx, ny, kappa, ox, oy, y, noise_var, gamma: float = 1.0) -> FactorList:
+def build_factors(nx, ny, kappa, ox, oy, y, noise_var, gamma: float = 1.0, alpha: int = 2) -> FactorList:
     """The posterior's factor list: prior cell factors first, then observations in input order."""
-    return concat(prior_factors(nx, ny, kappa, gamma), obs_factors(nx, ny, ox, oy, y, noise_var)).check()
+    return concat(prior_factors(nx, ny, kappa, gamma, alpha), obs_factors(nx, ny, ox, oy, y, noise_var)).check()
 
 
 def factor_update(a, s, r, lam_c, eta_c):
@@ -286,7 +333,7 @@ def dense_A(fl: FactorList) -> np.ndarray:
 def exact_mean(fl: FactorList, nx: int, method: str = "band") -> np.ndarray:
     """Exact posterior mean A^-1 b.
 
-    'band': banded Cholesky in natural order with half bandwidth 2 nx (C);
+    'band': banded Cholesky in natural order with the factor list's half bandwidth (C);
     'sparse': scipy's sparse LU (a library solve step) for grids too large for the band.
     """
     b = rhs(fl)
@@ -311,11 +358,27 @@ def exact_mean(fl: FactorList, nx: int, method: str = "band") -> np.ndarray:
     raise ValueError(method)
 
 
+def half_bandwidth(fl: FactorList) -> int:
+    """Largest index distance between two variables of one factor: A = sum s a a^T is zero
+    farther from the diagonal (2 nx for the alpha = 2 prior, 4 nx for alpha = 4)."""
+    k = np.diff(fl.ptr)
+    hb = 0
+    for kk in np.unique(k):
+        if kk == 0:
+            continue
+        fs = np.nonzero(k == kk)[0]
+        v = fl.var[fl.ptr[fs][:, None] + np.arange(kk)[None, :]]
+        hb = max(hb, int((v.max(axis=1) - v.min(axis=1)).max()))
+    return hb
+
+
 def band_solve(fl: FactorList, nx: int, b) -> np.ndarray:
-    """Solve A x = b (A from the factor list) by the banded Cholesky, half bandwidth 2 nx."""
+    """Solve A x = b (A from the factor list) by the banded Cholesky; the half bandwidth is
+    the factor list's (at least 2 nx)."""
     x = np.array(b, np.float64, copy=True).reshape(-1)
+    hb = max(2 * nx, half_bandwidth(fl))
     rc = lib().orc_band_solve(fl.n, fl.nf, _p(fl.ptr, _i64p), _p(fl.var, _i64p),
-                              _p(fl.coef, _f64p), _p(fl.s, _f64p), 2 * nx, _p(x, _f64p))
+                              _p(fl.coef, _f64p), _p(fl.s, _f64p), hb, _p(x, _f64p))
     if rc != 0:
         raise RuntimeError(f"orc_band_solve failed ({rc})")
     return x
