@@ -291,6 +291,7 @@ def own_arm(args):
     if rank == 0 and not args.no_e2e:
         line["batch"] = batch_rate(local)
         line["pairwise_form"] = pairwise_rate(p, local)
+        line["alpha4_prior"] = alpha4_rate(p, local)
         line["time_to_1e-5"] = warm_vs_cold(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
@@ -338,6 +339,26 @@ def pairwise_rate(p, device: int):
     peak, _ = measured_peak_gbs()
     return {"ms_per_iter": dt * 1e3, "node_updates_per_s": p.n / dt, "algorithmic_gbs": nbytes / dt / 1e9,
             "frac_of_measured_hbm": nbytes / dt / 1e9 / peak, "bytes_per_node": 344}
+
+
+def alpha4_rate(p, device: int):
+    """Iteration rate with the alpha = 4 prior (cell factors = rows of L^2, 13 slots; the split
+    kernels) on the same grid and observations: algorithmic bytes = 16 B per factor-variable
+    edge plus 20 B per observation, as for alpha = 2."""
+    import torch
+    from paper_2404_12968_gb300 import Solver
+    with Solver(p, precision="fp32", alpha=4, device=device) as s:
+        s.iterate(5, DAMPING)
+        torch.cuda.synchronize(device)
+        t = time.perf_counter()
+        s.iterate(50, DAMPING)
+        dt = (time.perf_counter() - t) / 50
+        st = s.stats()
+    nbytes = st["bytes_per_iter"]
+    peak, _ = measured_peak_gbs()
+    return {"ms_per_iter": dt * 1e3, "node_updates_per_s": p.n / dt, "edges": st["edges"],
+            "algorithmic_gbs": nbytes / dt / 1e9, "frac_of_measured_hbm": nbytes / dt / 1e9 / peak,
+            "kernels": "k_beliefs_l2 + k_prior_l2 + k_obs"}
 
 
 def warm_vs_cold(device: int):

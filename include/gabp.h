@@ -86,6 +86,13 @@ typedef struct {
 typedef struct {
     double gamma;  /* prior precision scale gamma of P = gamma L^T L (Sec. 3.1); > 0 */
     int boundary;  /* 0 = zero-Neumann (the only boundary implemented) */
+    int alpha;     /* SPDE exponent (Sec. 3.1, (kappa^2 - Delta)^(alpha/2) f = W): 0 or 2 = the
+                      operator L (one 5-slot factor per cell, a = row of L); 4 = L^2 (App. C,
+                      powers of the operator: one 13-slot factor per cell, a = row of L^2,
+                      P = gamma (L^2)^T L^2).  alpha = 4 contexts run the split kernels
+                      (kernel AUTO or SPLIT, no tile shape) and their prior messages are 13
+                      planes; warm starts, multigrid and the pairwise form need alpha = 2
+                      (GABP_ERR_STATE).  Other values: GABP_ERR_ARG. */
 } gabp_prior;
 
 typedef struct {
@@ -196,8 +203,8 @@ int gabp_reset(gabp_ctx *ctx);
 
 /*
  * Copy the current messages out / in (checkpoint and resume).  The buffer is opaque:
- * gabp_message_bytes() bytes, host or device, valid only for a context with the same
- * problem and precision.
+ * gabp_message_bytes() bytes (prior planes, 5 or 13 for alpha = 4, then the observation
+ * messages), host or device, valid only for a context with the same problem and precision.
  */
 int64_t gabp_message_bytes(const gabp_ctx *ctx);
 int gabp_get_messages(gabp_ctx *ctx, void *buf);

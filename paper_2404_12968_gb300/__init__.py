@@ -68,9 +68,10 @@ def gabp_default_options(**over) -> _lib.gabp_options:
     return o
 
 
-def gabp_create(nx: int, ny: int, kappa: float, obs_xy, y, noise_var, *, gamma: float = 1.0,
+def gabp_create(nx: int, ny: int, kappa: float, obs_xy, y, noise_var, *, gamma: float = 1.0, alpha: int = 2,
                 options: _lib.gabp_options | None = None, **opts) -> int:
-    """Create a context; returns its handle.  ``obs_xy`` is (m, 2) float64 host data."""
+    """Create a context; returns its handle.  ``obs_xy`` is (m, 2) float64 host data; ``alpha``
+    the SPDE exponent (2: cell factors = rows of L, 4: rows of L^2)."""
     L = _lib.load()
     obs_xy = np.ascontiguousarray(obs_xy, np.float64).reshape(-1)
     y = np.ascontiguousarray(y, np.float64).reshape(-1)
@@ -79,7 +80,7 @@ def gabp_create(nx: int, ny: int, kappa: float, obs_xy, y, noise_var, *, gamma: 
     if obs_xy.shape[0] != 2 * m or noise_var.shape[0] != m:
         raise ValueError("obs_xy must be (m, 2) and noise_var (m,)")
     o = options if options is not None else gabp_default_options(**opts)
-    prior = _lib.gabp_prior(gamma, 0)
+    prior = _lib.gabp_prior(gamma, 0, int(alpha))
     h = ctypes.c_void_p()
     rc = L.gabp_create(ctypes.byref(h), _lib.gabp_grid(nx, ny, 1.0), float(kappa), ctypes.byref(prior),
                        m, obs_xy.ctypes.data if m else None, y.ctypes.data if m else None,
@@ -537,14 +538,14 @@ class Solver:
     object (fields nx, ny, kappa, obs_x, obs_y, y, noise_var)."""
 
     def __init__(self, problem=None, *, nx=None, ny=None, kappa=None, obs_xy=None, y=None,
-                 noise_var=None, precision: str = "fp32", gamma: float = 1.0, **opts):
+                 noise_var=None, precision: str = "fp32", gamma: float = 1.0, alpha: int = 2, **opts):
         if problem is not None:
             nx, ny, kappa = problem.nx, problem.ny, problem.kappa
             obs_xy = np.stack([problem.obs_x, problem.obs_y], axis=1)
             y, noise_var = problem.y, problem.noise_var
         opts.setdefault("precision", GABP_FP64 if precision == "fp64" else GABP_FP32)
         self.nx, self.ny = int(nx), int(ny)
-        self.ctx = gabp_create(self.nx, self.ny, kappa, obs_xy, y, noise_var, gamma=gamma, **opts)
+        self.ctx = gabp_create(self.nx, self.ny, kappa, obs_xy, y, noise_var, gamma=gamma, alpha=alpha, **opts)
 
     @property
     def n(self) -> int:

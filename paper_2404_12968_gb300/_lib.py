@@ -37,7 +37,7 @@ class gabp_grid(ctypes.Structure):
 
 
 class gabp_prior(ctypes.Structure):
-    _fields_ = [("gamma", ctypes.c_double), ("boundary", ctypes.c_int)]
+    _fields_ = [("gamma", ctypes.c_double), ("boundary", ctypes.c_int), ("alpha", ctypes.c_int)]
 
 
 class gabp_options(ctypes.Structure):

@@ -233,6 +233,8 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     const double gamma = prior ? prior->gamma : 1.0;
     if (!(gamma > 0.0) || !std::isfinite(gamma)) return fail(c, GABP_ERR_ARG, "gamma must be finite and > 0");
     if (prior && prior->boundary != 0) return fail(c, GABP_ERR_ARG, "only the zero-Neumann boundary (0) is implemented");
+    const int alpha = prior && prior->alpha ? prior->alpha : 2;
+    if (alpha != 2 && alpha != 4) return fail(c, GABP_ERR_ARG, "alpha must be 2 or 4");
     if (m < 0 || m > ((int64_t)1 << 28)) return fail(c, GABP_ERR_ARG, "observation count out of range");
     if (m > 0 && (!obs_xy || !y || !noise_var)) return fail(c, GABP_ERR_ARG, "observation arrays must not be NULL");
     if (m > 0 && (nx < 2 || ny < 2)) return fail(c, GABP_ERR_ARG, "observations need a grid of at least 2 x 2");
@@ -241,7 +243,11 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     if (o.init != GABP_INIT_COLD && o.init != GABP_INIT_PAPER) return fail(c, GABP_ERR_ARG, "bad init mode");
     if (o.kernel < GABP_KERNEL_AUTO || o.kernel > GABP_KERNEL_SWEEP) return fail(c, GABP_ERR_ARG, "bad kernel");
     if (!(o.tol > 0.0) || o.check_every < 1 || o.max_iters < 1) return fail(c, GABP_ERR_ARG, "bad tol/check_every/max_iters");
-    {
+    if (alpha == 4 && ((o.kernel != GABP_KERNEL_AUTO && o.kernel != GABP_KERNEL_SPLIT) || o.tile_x || o.tile_y))
+        return fail(c, GABP_ERR_ARG, "the alpha = 4 prior runs the split kernels (kernel AUTO or SPLIT, no tile shape)");
+    if (alpha == 4) {
+        // nothing else to check
+    } else {
         // the kernel AUTO resolves to: the sweep for FP32, the plain fused kernel for FP64
         const int k = o.kernel != GABP_KERNEL_AUTO
                           ? o.kernel
@@ -303,6 +309,8 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     p.prec = o.precision;
     p.gamma = gamma;
     p.debug_stall = (o.debug_flags & 1) ? 1 : 0;
+    p.order = alpha == 4 ? 2 : 1;
+    p.planes = alpha == 4 ? 13 : 5;
     for (int d = 0; d <= 4; ++d) p.aC[d] = kappa * kappa + (double)d;
     p.var_f = (float)(1.0 / gamma);
     for (int d = 0; d <= 4; ++d) {
@@ -317,7 +325,7 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     int rc;
     void *q;
     for (int b = 0; b < 2; ++b) {
-        if ((rc = dalloc(c, &p.P[b], 5 * (size_t)n * 2 * T, "alloc prior messages"))) return rc;
+        if ((rc = dalloc(c, &p.P[b], (size_t)p.planes * (size_t)n * 2 * T, "alloc prior messages"))) return rc;
         if ((rc = dalloc(c, &p.O[b], 8 * (size_t)m * T, "alloc obs messages"))) return rc;
     }
     if ((rc = dalloc(c, &q, (size_t)m * sizeof(int), "alloc obs base"))) return rc;
@@ -383,7 +391,7 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
         return fail(c, GABP_ERR_ARG, "the TMA kernel needs FP32 messages and nx a multiple of 4");
     if (o.kernel == GABP_KERNEL_SWEEP && p.prec != 0)
         return fail(c, GABP_ERR_ARG, "the sweep kernel needs FP32 messages");
-    if (o.kernel == GABP_KERNEL_SPLIT) c->kernel = GABP_KERNEL_SPLIT;
+    if (o.kernel == GABP_KERNEL_SPLIT || p.order == 2) c->kernel = GABP_KERNEL_SPLIT;
     else if (o.kernel == GABP_KERNEL_TMA || (o.kernel == GABP_KERNEL_AUTO && tma_ok)) c->kernel = GABP_KERNEL_TMA;
     else if (o.kernel == GABP_KERNEL_SWEEP || (o.kernel == GABP_KERNEL_AUTO && p.prec == 0)) c->kernel = GABP_KERNEL_SWEEP;
     else c->kernel = GABP_KERNEL_FUSED;
@@ -392,12 +400,22 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     } else if (c->kernel == GABP_KERNEL_TMA) {
         c->shape = o.tile_x ? gabp::FusedShape{o.tile_x, o.tile_y} : gabp::FusedShape{30, 14};
         CK(gabp::make_tma_maps(p, c->shape.tx, c->shape.ty, c->maps), "tensor map encode");
+    } else if (p.order == 2) {
+        c->shape = {0, 0};
     } else if (o.tile_x) {
         c->shape = {o.tile_x, o.tile_y};
     } else {
         c->shape = p.prec ? gabp::FusedShape{32, 8} : gabp::FusedShape{64, 16};
     }
     c->edges = 5 * n - 2 * (int64_t)(nx + ny) + 4 * m;
+    if (p.order == 2) {   // 13-slot cell factors: count the slots whose node exists
+        static const int dx[13] = {0, -1, 1, 0, 0, -1, 1, -1, 1, -2, 2, 0, 0};
+        static const int dy[13] = {0, 0, 0, -1, 1, -1, -1, 1, 1, 0, 0, -2, 2};
+        int64_t e = 0;
+        for (int d = 0; d < 13; ++d)
+            e += (int64_t)std::max(0, nx - std::abs(dx[d])) * std::max(0, ny - std::abs(dy[d]));
+        c->edges = e + 4 * m;
+    }
     const double ebytes = 4.0 * (double)T;    // (eta, Lambda) read + write per edge
     c->bytes_per_iter = ebytes * (double)c->edges + 5.0 * (double)T * (double)m;
     c->hxy = std::move(sxy);
@@ -584,6 +602,7 @@ int gabp_marginals(gabp_ctx *c, double *mean, double *var) {
 
 int gabp_warm_start(gabp_ctx *c, const double *mu0, const double *lam0) {
     if (!c) return GABP_ERR_ARG;
+    if (c->p.order == 2) return fail(c, GABP_ERR_STATE, "warm starts are not available for the alpha = 4 prior");
     if (!mu0 || !lam0) return fail(c, GABP_ERR_ARG, "mu0 and lam0 must not be NULL");
     DeviceGuard g(c->dev);
     if (!g.ok) return fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
@@ -624,14 +643,14 @@ int gabp_reset(gabp_ctx *c) {
 int64_t gabp_message_bytes(const gabp_ctx *c) {
     if (!c) return -1;
     const int64_t T = c->p.prec ? 8 : 4;
-    return 10 * c->p.n * T + 8 * c->p.m * T;
+    return 2 * (int64_t)c->p.planes * c->p.n * T + 8 * c->p.m * T;
 }
 
 int gabp_get_messages(gabp_ctx *c, void *buf) {
     if (!c || !buf) return c ? fail(c, GABP_ERR_ARG, "buffer must not be NULL") : GABP_ERR_ARG;
     DeviceGuard g(c->dev);
     const size_t T = tsize(c);
-    const size_t pb = 10 * (size_t)c->p.n * T, ob = 8 * (size_t)c->p.m * T;
+    const size_t pb = 2 * (size_t)c->p.planes * (size_t)c->p.n * T, ob = 8 * (size_t)c->p.m * T;
     CK(cudaMemcpyAsync(buf, c->p.P[c->cur], pb, cudaMemcpyDefault, c->stream), "copy messages");
     if (ob) CK(cudaMemcpyAsync((char *)buf + pb, c->p.O[c->cur], ob, cudaMemcpyDefault, c->stream), "copy messages");
     CK(cudaStreamSynchronize(c->stream), "messages sync");
@@ -642,7 +661,7 @@ int gabp_set_messages(gabp_ctx *c, const void *buf) {
     if (!c || !buf) return c ? fail(c, GABP_ERR_ARG, "buffer must not be NULL") : GABP_ERR_ARG;
     DeviceGuard g(c->dev);
     const size_t T = tsize(c);
-    const size_t pb = 10 * (size_t)c->p.n * T, ob = 8 * (size_t)c->p.m * T;
+    const size_t pb = 2 * (size_t)c->p.planes * (size_t)c->p.n * T, ob = 8 * (size_t)c->p.m * T;
     CK(cudaMemcpyAsync(c->p.P[0], buf, pb, cudaMemcpyDefault, c->stream), "copy messages");
     if (ob) CK(cudaMemcpyAsync(c->p.O[0], (const char *)buf + pb, ob, cudaMemcpyDefault, c->stream), "copy messages");
     CK(cudaStreamSynchronize(c->stream), "messages sync");
@@ -1366,6 +1385,7 @@ int gabp_mg_create(gabp_mg **out, gabp_ctx *ctx, int levels) {
     if (!out || !ctx) return GABP_ERR_ARG;
     *out = nullptr;
     if (levels < 2 || levels > GABP_MG_MAX_LEVELS) return fail(ctx, GABP_ERR_ARG, "levels must be in [2, 16]");
+    if (ctx->p.order == 2) return fail(ctx, GABP_ERR_STATE, "multigrid is not available for the alpha = 4 prior");
     const int nx = ctx->p.nx, ny = ctx->p.ny;
     const int64_t m = ctx->p.m;
     for (int k = 1; k < levels; ++k) {
@@ -1542,6 +1562,7 @@ extern "C" {
 int gabp_pw_create(gabp_pw **out, gabp_ctx *ctx) {
     if (!out || !ctx) return GABP_ERR_ARG;
     *out = nullptr;
+    if (ctx->p.order == 2) return fail(ctx, GABP_ERR_STATE, "the pairwise form is built for the alpha = 2 prior only");
     gabp_pw *w = new (std::nothrow) gabp_pw();
     if (!w) return GABP_ERR_OOM;
     w->ctx = ctx;
@@ -1639,6 +1660,7 @@ void gabp_pw_destroy(gabp_pw *w) {
 int gabp_wsnet_warm_start(gabp_ctx *c, gabp_wsnet *net) {
     if (!c || !net) return c ? fail(c, GABP_ERR_ARG, "net must not be NULL") : GABP_ERR_ARG;
     if (gabp::wsnet_device(net) != c->dev) return fail(c, GABP_ERR_ARG, "network and context on different devices");
+    if (c->p.order == 2) return fail(c, GABP_ERR_STATE, "warm starts are not available for the alpha = 4 prior");
     DeviceGuard g(c->dev);
     int rc = ws_ensure_input(c);
     if (rc) return rc;

@@ -38,6 +38,8 @@ struct DevProblem {
     double *scal;        // 2 doubles: [0] = ||r||^2, [1] = ||b||^2
     int *err;            // device error flag (a bounded wait in a kernel gave up)
     int debug_stall;     // test hook: the TMA kernel first waits on a barrier nothing completes
+    int order;           // prior operator: 1 = L (alpha = 2, 5-slot cell factors), 2 = L^2 (alpha = 4)
+    int planes;          // prior message planes: 5 (order 1) or 13 (order 2)
 };
 
 // Prior constants in the kernel's precision.  FP32 kernels read the values rounded once on the
@@ -63,6 +65,11 @@ cudaError_t launch_obs_precompute(const DevProblem &p, const double *raw_xy, con
 cudaError_t launch_rhs_norm(const DevProblem &p, cudaStream_t st);   // scal[1] = ||b||^2
 // residual of the messages in buffer src; leaves ||r||^2 in scal[0] (beliefs recomputed)
 cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st);
+// ---- the alpha = 4 prior (order 2: cell factors = rows of L^2, 13 planes; gabp_split.cu) ----
+// one synchronous iteration (beliefs, cell factors, observation factors); initialisation as
+// launch_init_cold (which dispatches on p.order, as do launch_beliefs, launch_residual and
+// launch_msg_change)
+cudaError_t launch_l2_iteration(const DevProblem &p, int src, double beta, cudaStream_t st);
 // ---- the paper's pairwise re-weighted form (gabp_pairwise.cu) ----
 // coefficients P_ii (n), h (n), P_{i, i + off_d} (12 n) in the context's precision; messages are
 // 12 n (a, b) pairs per buffer

@@ -99,6 +99,121 @@ template <typename T> __global__ void k_prior(DevProblem p, int src, T beta) {
     }
 }
 
+// ---- the alpha = 4 prior (Sec. 3.1 with alpha / 2 = 2; App. C, powers of the operator) ----
+// The operator matrix is L^2 and cell c's factor has a = row c of L^2 over 13 slots: the cell,
+// its 4 neighbours, the 4 diagonal neighbours and the 4 nodes two steps away.  Plane d holds
+// the message of cell c's factor to node c + offset(d).  Row c of L^2 = sum_w L_cw L_w.:
+// centre (kappa^2 + deg c)^2 + deg c; neighbour u: -(kappa^2 + deg c) - (kappa^2 + deg u)
+// (the two one-step paths through c and u); diagonal: 2 (two paths); two steps away: 1.
+constexpr int L2_SLOTS = 13;
+__host__ __device__ constexpr int l2_dx(int d) {
+    return d == 1 || d == 5 || d == 7 ? -1 : d == 2 || d == 6 || d == 8 ? 1 : d == 9 ? -2 : d == 10 ? 2 : 0;
+}
+__host__ __device__ constexpr int l2_dy(int d) {
+    return d == 3 || d == 5 || d == 6 ? -1 : d == 4 || d == 7 || d == 8 ? 1 : d == 11 ? -2 : d == 12 ? 2 : 0;
+}
+
+// coefficient of slot d of cell (i, j)'s factor; 0 if the slot's node is outside the grid
+__device__ __forceinline__ double l2_coef(const DevProblem &p, int i, int j, int d) {
+    const int nx = p.nx, ny = p.ny;
+    const int y = i + l2_dy(d), x = j + l2_dx(d);
+    if (x < 0 || x >= nx || y < 0 || y >= ny) return 0.0;
+    if (d == 0) {
+        const int dc = grid_degree(i, j, nx, ny);
+        return p.aC[dc] * p.aC[dc] + (double)dc;
+    }
+    if (d <= 4) return -(p.aC[grid_degree(i, j, nx, ny)] + p.aC[grid_degree(y, x, nx, ny)]);
+    return d <= 8 ? 2.0 : 1.0;
+}
+
+// beliefs of order-2 contexts: node v receives slot d of the factor of cell v - offset(d),
+// summed in slot order, then the observation messages as for order 1
+template <typename T> __global__ void k_beliefs_l2(DevProblem p, int src) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const int nx = p.nx, ny = p.ny;
+    const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
+    const T2<T> *P = (const T2<T> *)p.P[src];
+    const T *O = (const T *)p.O[src];
+    const int64_t n = p.n;
+    T2<T> q = P[v];
+    CompSum<T> se(q.x), sl(q.y);
+#pragma unroll
+    for (int d = 1; d < L2_SLOTS; ++d) {
+        const int ci = i - l2_dy(d), cj = j - l2_dx(d);
+        if (ci >= 0 && ci < ny && cj >= 0 && cj < nx) {
+            q = P[d * n + (int64_t)ci * nx + cj];
+            se.add(q.x);
+            sl.add(q.y);
+        }
+    }
+    if (p.m > 0) {
+        const int *optr = p.optr;
+        add_obs_pair(se, sl, O, j > 0 ? optr[v - 1] : optr[v], optr[v], optr[v + 1], 1, 0);
+        if (i > 0) add_obs_pair(se, sl, O, j > 0 ? optr[v - nx - 1] : optr[v - nx], optr[v - nx], optr[v - nx + 1], 3, 2);
+    }
+    se.finish();
+    sl.finish();
+    BeliefStore<T> b;
+    b.ehi = se.hi; b.elo = se.lo; b.lhi = sl.hi; b.llo = sl.lo;
+    ((BeliefStore<T> *)p.belief)[v] = b;
+}
+
+// order-2 cell factors: a = row c of L^2, var = 1/gamma, r = 0
+template <typename T> __global__ void k_prior_l2(DevProblem p, int src, T beta) {
+    const int64_t c = gtid();
+    if (c >= p.n) return;
+    const int nx = p.nx;
+    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    const int64_t n = p.n;
+    const T2<T> *P = (const T2<T> *)p.P[src];
+    T2<T> *Q = (T2<T> *)p.P[src ^ 1];
+    T a[L2_SLOTS], lam[L2_SLOTS], eta[L2_SLOTS];
+    T2<T> own[L2_SLOTS];
+#pragma unroll
+    for (int d = 0; d < L2_SLOTS; ++d) {
+        a[d] = (T)l2_coef(p, i, j, d);
+        own[d] = P[d * n + c];
+        if (a[d] != T(0)) {
+            cavity(load_belief<T>(p, c + (int64_t)l2_dy(d) * nx + l2_dx(d)), own[d].x, own[d].y, eta[d], lam[d]);
+        } else {
+            lam[d] = T(1);
+            eta[d] = T(0);
+        }
+    }
+    T L[L2_SLOTS], E[L2_SLOTS];
+    factor_messages<T, L2_SLOTS>(a, prior_var<T>(p), T(0), lam, eta, L, E);
+#pragma unroll
+    for (int d = 0; d < L2_SLOTS; ++d) {
+        T2<T> out;
+        if (a[d] != T(0)) {
+            out.x = damp(own[d].x, E[d], beta);
+            out.y = damp(own[d].y, L[d], beta);
+        } else {
+            out.x = T(0);
+            out.y = T(0);
+        }
+        Q[d * n + c] = out;
+    }
+}
+
+// cold / paper initialisation of the 13 planes (as k_init_prior)
+template <typename T> __global__ void k_init_prior_l2(DevProblem p, int dst, int paper) {
+    const int64_t c = gtid();
+    if (c >= p.n) return;
+    const int nx = p.nx;
+    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    T2<T> *Q = (T2<T> *)p.P[dst];
+#pragma unroll
+    for (int d = 0; d < L2_SLOTS; ++d) {
+        const double a = l2_coef(p, i, j, d);
+        T2<T> o;
+        o.x = T(0);
+        o.y = a == 0.0 ? T(0) : (paper ? T(1e-8) : T(p.gamma * a * a));
+        Q[d * p.n + c] = o;
+    }
+}
+
 // ---- observation factors: a = bilinear weights, var = sigma^2, r = y ----
 template <typename T> __global__ void k_obs(DevProblem p, int src, T beta) {
     const int64_t k = gtid();
@@ -447,6 +562,14 @@ __device__ __forceinline__ double apply_L(const DevProblem &p, const double *x, 
     return s;
 }
 
+// y = L x (FP64); the alpha = 4 residual applies L four times
+__global__ void k_Lx(DevProblem p, const double *x, double *y) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+    y[v] = apply_L(p, x, v, i, j);
+}
+
 __global__ void k_Lmu(DevProblem p) {
     const int64_t v = gtid();
     if (v >= p.n) return;
@@ -616,16 +739,46 @@ template <typename T> cudaError_t split_iteration(const DevProblem &p, int src, 
 }  // namespace
 
 cudaError_t launch_split_iteration(const DevProblem &p, int src, double beta, cudaStream_t st) {
+    if (p.order == 2) return launch_l2_iteration(p, src, beta, st);
     return p.prec ? split_iteration<double>(p, src, beta, st) : split_iteration<float>(p, src, beta, st);
 }
 
+cudaError_t launch_l2_iteration(const DevProblem &p, int src, double beta, cudaStream_t st) {
+    if (p.order != 2) return cudaErrorInvalidValue;
+    if (p.prec) {
+        k_beliefs_l2<double><<<nblocks(p.n), TPB, 0, st>>>(p, src);
+        k_prior_l2<double><<<nblocks(p.n), TPB, 0, st>>>(p, src, beta);
+        if (p.m > 0) k_obs<double><<<nblocks(p.m), TPB, 0, st>>>(p, src, beta);
+    } else {
+        k_beliefs_l2<float><<<nblocks(p.n), TPB, 0, st>>>(p, src);
+        k_prior_l2<float><<<nblocks(p.n), TPB, 0, st>>>(p, src, (float)beta);
+        if (p.m > 0) k_obs<float><<<nblocks(p.m), TPB, 0, st>>>(p, src, (float)beta);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_beliefs(const DevProblem &p, int src, cudaStream_t st) {
+    if (p.order == 2) {
+        if (p.prec) k_beliefs_l2<double><<<nblocks(p.n), TPB, 0, st>>>(p, src);
+        else k_beliefs_l2<float><<<nblocks(p.n), TPB, 0, st>>>(p, src);
+        return cudaGetLastError();
+    }
     if (p.prec) k_beliefs<double><<<nblocks(p.n), TPB, 0, st>>>(p, src);
     else k_beliefs<float><<<nblocks(p.n), TPB, 0, st>>>(p, src);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_cold(const DevProblem &p, int dst, int paper, cudaStream_t st) {
+    if (p.order == 2) {
+        if (p.prec) {
+            k_init_prior_l2<double><<<nblocks(p.n), TPB, 0, st>>>(p, dst, paper);
+            if (p.m > 0) k_init_obs<double><<<nblocks(p.m), TPB, 0, st>>>(p, dst, paper);
+        } else {
+            k_init_prior_l2<float><<<nblocks(p.n), TPB, 0, st>>>(p, dst, paper);
+            if (p.m > 0) k_init_obs<float><<<nblocks(p.m), TPB, 0, st>>>(p, dst, paper);
+        }
+        return cudaGetLastError();
+    }
     if (p.prec) {
         k_init_prior<double><<<nblocks(p.n), TPB, 0, st>>>(p, dst, paper);
         if (p.m > 0) k_init_obs<double><<<nblocks(p.m), TPB, 0, st>>>(p, dst, paper);
@@ -669,7 +822,7 @@ cudaError_t launch_rhs_norm(const DevProblem &p, cudaStream_t st) {
 template <typename T> __global__ void k_msg_change(DevProblem p, int cur) {
     const T *a = (const T *)p.P[cur], *b = (const T *)p.P[cur ^ 1];
     const T *oa = (const T *)p.O[cur], *ob = (const T *)p.O[cur ^ 1];
-    const int64_t np_ = 10 * p.n, no = 8 * p.m;
+    const int64_t np_ = 2 * (int64_t)p.planes * p.n, no = 8 * p.m;
     const int64_t stride = (int64_t)gridDim.x * TPB;
     T acc = T(0);
     for (int64_t i = gtid(); i < np_; i += stride) acc += fabs(a[i] - b[i]);
@@ -694,6 +847,7 @@ cudaError_t launch_df_precompute(const DevProblem &p, cudaStream_t st) {
 // the residual of a mean already in p.mu64 (double-float pairs for FP32 contexts, FP64 values
 // for FP64 contexts): the kernels after the mean in launch_residual
 cudaError_t launch_residual_mu(const DevProblem &p, cudaStream_t st) {
+    if (p.order == 2) return cudaErrorInvalidValue;   // order-2 contexts: launch_residual only
     if (p.prec == 0) {
         if (p.m > 0) k_obs_err_df<<<nblocks(p.m), TPB, 0, st>>>(p);
         k_Lmu_df<<<nblocks(p.n), TPB, 0, st>>>(p);
@@ -710,6 +864,19 @@ cudaError_t launch_residual_mu(const DevProblem &p, cudaStream_t st) {
 cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st) {
     cudaError_t e = launch_beliefs(p, src, st);
     if (e != cudaSuccess) return e;
+    if (p.order == 2) {
+        // r = b - gamma L^4 mu - H^T S (H mu - y) in FP64 (both precisions): z = L mu, then L
+        // twice more through the scratch vectors, and k_res applies the fourth L
+        if (p.prec) k_mu<double><<<nblocks(p.n), TPB, 0, st>>>(p);
+        else k_mu<float><<<nblocks(p.n), TPB, 0, st>>>(p);
+        if (p.m > 0) k_obs_err<<<nblocks(p.m), TPB, 0, st>>>(p);
+        k_Lx<<<nblocks(p.n), TPB, 0, st>>>(p, p.mu64, p.z64);
+        k_Lx<<<nblocks(p.n), TPB, 0, st>>>(p, p.z64, p.mu64);
+        k_Lx<<<nblocks(p.n), TPB, 0, st>>>(p, p.mu64, p.z64);
+        k_res<<<RES_BLOCKS, TPB, 0, st>>>(p);
+        k_final_sum<<<1, TPB, 0, st>>>(p.part, RES_BLOCKS, p.scal);
+        return cudaGetLastError();
+    }
     if (p.prec == 0) {
         // FP32 messages: the residual in double-float arithmetic (FP32 pipes, ~48-bit significands)
         k_mu_df<<<nblocks(p.n), TPB, 0, st>>>(p);
