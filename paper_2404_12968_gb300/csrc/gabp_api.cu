@@ -3,6 +3,7 @@
 // A context owns the device buffers of one problem: ping-pong message buffers, the sorted
 // observation data, the residual scratch.  Iterations run as CUDA-graph replays of a chunk
 // of fused (or split) iteration kernels on the context's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -276,20 +277,35 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
         if (i0 > ny - 2) i0 = ny - 2;
         base[(size_t)k] = i0 * nx + j0;
     }
-    std::vector<int> optr((size_t)n + 1, 0);
-    for (int64_t k = 0; k < m; ++k) optr[(size_t)base[(size_t)k] + 1] += 1;
-    for (int64_t v = 0; v < n; ++v) optr[(size_t)v + 1] += optr[(size_t)v];
-    std::vector<int> fillpos(optr.begin(), optr.end() - 1);
+    // stable LSD radix sort of the observations by base cell (two 15-bit digits: base < 2^30),
+    // with bucket arrays of 2^15 entries instead of one per cell; the per-cell index optr is
+    // then built on the GPU from the sorted base cells
+    std::vector<int> perm((size_t)m), tmp((size_t)m);
+    for (int64_t k = 0; k < m; ++k) perm[(size_t)k] = (int)k;
+    {
+        constexpr int DIG = 15, NB = 1 << DIG;
+        std::vector<int> cnt(NB + 1);
+        for (int pass = 0; pass < 2; ++pass) {
+            const int shift = pass * DIG;
+            std::fill(cnt.begin(), cnt.end(), 0);
+            for (int64_t k = 0; k < m; ++k) ++cnt[(size_t)((base[(size_t)k] >> shift) & (NB - 1)) + 1];
+            for (int b = 0; b < NB; ++b) cnt[(size_t)b + 1] += cnt[(size_t)b];
+            for (int64_t k = 0; k < m; ++k) {
+                const int src = perm[(size_t)k];
+                tmp[(size_t)cnt[(size_t)((base[(size_t)src] >> shift) & (NB - 1))]++] = src;
+            }
+            perm.swap(tmp);
+        }
+    }
     std::vector<int> sbase((size_t)m);
     std::vector<double> sxy((size_t)(2 * m)), sy((size_t)m), svar((size_t)m);
-    for (int64_t k = 0; k < m; ++k) {
-        const int b = base[(size_t)k];
-        const int dst = fillpos[(size_t)b]++;
-        sbase[(size_t)dst] = b;
-        sxy[2 * (size_t)dst] = obs_xy[2 * k];
-        sxy[2 * (size_t)dst + 1] = obs_xy[2 * k + 1];
-        sy[(size_t)dst] = y[k];
-        svar[(size_t)dst] = noise_var[k];
+    for (int64_t d = 0; d < m; ++d) {
+        const int64_t k = perm[(size_t)d];
+        sbase[(size_t)d] = base[(size_t)k];
+        sxy[2 * (size_t)d] = obs_xy[2 * k];
+        sxy[2 * (size_t)d + 1] = obs_xy[2 * k + 1];
+        sy[(size_t)d] = y[k];
+        svar[(size_t)d] = noise_var[k];
     }
 
     c->kappa = kappa;
@@ -365,22 +381,24 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     CK(cudaMallocHost((void **)&c->hscal, 4 * sizeof(double)), "alloc pinned scalars");
     CK(cudaMemsetAsync(p.scal, 0, 4 * sizeof(double), c->stream), "memset");
 
-    // upload the sorted observations; FP64 precompute of weights and 1/sigma^2 on the GPU
+    // upload the sorted observations; FP64 precompute of weights and 1/sigma^2 on the GPU (the
+    // raw values go through the staging buffer when it is large enough)
     if (m > 0) {
         double *raw = nullptr;
-        CK(cudaMalloc((void **)&raw, 4 * (size_t)m * sizeof(double)), "alloc raw observations");
+        const bool own_raw = 4 * m > 2 * n;
+        if (own_raw) CK(cudaMalloc((void **)&raw, 4 * (size_t)m * sizeof(double)), "alloc raw observations");
+        else raw = c->stage;
         cudaError_t e = cudaMemcpyAsync(raw, sxy.data(), 2 * (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 2 * m, sy.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 3 * m, svar.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync((void *)p.obase, sbase.data(), (size_t)m * sizeof(int), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = gabp::launch_obs_precompute(p, raw, raw + 2 * m, raw + 3 * m, c->stream);
         if (e == cudaSuccess && p.prec == 0) e = gabp::launch_df_precompute(p, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        cudaFree(raw);
+        if (e == cudaSuccess && own_raw) e = cudaStreamSynchronize(c->stream);
+        if (own_raw) cudaFree(raw);
         if (e != cudaSuccess) return cuda_fail(c, e, "observation upload/precompute");
     }
-    CK(cudaMemcpyAsync((void *)p.optr, optr.data(), ((size_t)n + 1) * sizeof(int), cudaMemcpyHostToDevice, c->stream),
-       "upload obs pointers");
+    CK(gabp::launch_obs_pointers(p, c->stream), "observation pointers");
     CK(gabp::launch_rhs_norm(p, c->stream), "rhs norm");
     if ((rc = init_messages(c))) return rc;
     CK(cudaStreamSynchronize(c->stream), "create sync");

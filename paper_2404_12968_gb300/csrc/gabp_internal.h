@@ -63,6 +63,8 @@ cudaError_t launch_init_warm(const DevProblem &p, int dst, const double *mu0, co
 cudaError_t launch_obs_precompute(const DevProblem &p, const double *raw_xy, const double *raw_y,
                                   const double *raw_var, cudaStream_t st);
 cudaError_t launch_rhs_norm(const DevProblem &p, cudaStream_t st);   // scal[1] = ||b||^2
+// optr[c] = number of observations with base cell < c (c = 0 .. n), from the sorted obase
+cudaError_t launch_obs_pointers(const DevProblem &p, cudaStream_t st);
 // residual of the messages in buffer src; leaves ||r||^2 in scal[0] (beliefs recomputed)
 cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st);
 // ---- the alpha = 4 prior (order 2: cell factors = rows of L^2, 13 planes; gabp_split.cu) ----

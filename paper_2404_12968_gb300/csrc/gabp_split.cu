@@ -352,6 +352,19 @@ __global__ void k_obs_precompute(DevProblem p, const double *xy, const double *y
     YS64[2 * k + 1] = 1.0 / var[k];
 }
 
+// ---- per-cell observation index: optr[c] = lower bound of c in the sorted base cells ----
+__global__ void k_obs_pointers(DevProblem p) {
+    const int64_t c = gtid();
+    if (c > p.n) return;
+    int64_t lo = 0, hi = p.m;   // first k with obase[k] >= c
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (p.obase[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    ((int *)p.optr)[c] = (int)lo;
+}
+
 // ---- deterministic FP64 reductions: fixed grid, fixed per-thread order, smem tree ----
 __device__ __forceinline__ double block_sum(double x) {
     __shared__ double sh[TPB];
@@ -806,6 +819,11 @@ cudaError_t launch_obs_precompute(const DevProblem &p, const double *xy, const d
     if (p.m == 0) return cudaSuccess;
     if (p.prec) k_obs_precompute<double><<<nblocks(p.m), TPB, 0, st>>>(p, xy, yv, var);
     else k_obs_precompute<float><<<nblocks(p.m), TPB, 0, st>>>(p, xy, yv, var);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_obs_pointers(const DevProblem &p, cudaStream_t st) {
+    k_obs_pointers<<<nblocks(p.n + 1), TPB, 0, st>>>(p);
     return cudaGetLastError();
 }
 
