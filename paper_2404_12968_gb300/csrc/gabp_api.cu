@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "gabp.h"
@@ -224,6 +225,29 @@ void free_all(gabp_ctx *c) {
 
 size_t tsize(const gabp_ctx *c) { return c->p.prec ? sizeof(double) : sizeof(float); }
 
+// Host set-up work in parallel chunks: chunk ch of nchunk covers [ch * count / nchunk, ...); the
+// results of every caller below do not depend on the number of chunks.
+int host_chunks(int64_t count) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int64_t by_size = count / 65536 + 1;   // small inputs stay on one thread
+    int64_t t = hw ? (int64_t)hw : 1;
+    if (t > 32) t = 32;
+    return (int)(t < by_size ? t : by_size);
+}
+
+template <typename F> void parallel_chunks(int64_t count, int nchunk, F f) {
+    if (nchunk <= 1) {
+        f(0, (int64_t)0, count);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve((size_t)nchunk - 1);
+    for (int ch = 1; ch < nchunk; ++ch)
+        th.emplace_back([&, ch]() { f(ch, count * ch / nchunk, count * (ch + 1) / nchunk); });
+    f(0, (int64_t)0, count / nchunk);
+    for (std::thread &t : th) t.join();
+}
+
 int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *prior, int64_t m,
                 const double *obs_xy, const double *y, const double *noise_var) {
     const int nx = grid.nx, ny = grid.ny;
@@ -263,50 +287,85 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
             return fail(c, GABP_ERR_ARG, "unsupported tile shape for the TMA kernel");
     }
     const int64_t n = (int64_t)nx * ny;
-    // validate observations and sort them by base cell (stable counting sort, FP64 floor)
+    // validate the observations and compute their base cells (FP64 floor), in parallel chunks;
+    // the first invalid index decides the error
     std::vector<int> base((size_t)m);
-    for (int64_t k = 0; k < m; ++k) {
-        const double x = obs_xy[2 * k], yy = obs_xy[2 * k + 1];
-        if (!std::isfinite(x) || !std::isfinite(yy) || !std::isfinite(y[k]) || !std::isfinite(noise_var[k]))
-            return fail(c, GABP_ERR_ARG, "non-finite observation data at index " + std::to_string(k));
-        if (x < 0.0 || x > nx - 1.0 || yy < 0.0 || yy > ny - 1.0)
-            return fail(c, GABP_ERR_ARG, "observation " + std::to_string(k) + " outside the grid");
-        if (!(noise_var[k] > 0.0)) return fail(c, GABP_ERR_ARG, "noise variance must be > 0");
-        int j0 = (int)std::floor(x), i0 = (int)std::floor(yy);
-        if (j0 > nx - 2) j0 = nx - 2;
-        if (i0 > ny - 2) i0 = ny - 2;
-        base[(size_t)k] = i0 * nx + j0;
+    const int nchunk = host_chunks(m);
+    std::vector<int64_t> first_bad((size_t)nchunk, -1);
+    std::vector<int> bad_kind((size_t)nchunk, 0);
+    parallel_chunks(m, nchunk, [&](int ch, int64_t k0, int64_t k1) {
+        for (int64_t k = k0; k < k1; ++k) {
+            const double x = obs_xy[2 * k], yy = obs_xy[2 * k + 1];
+            int kind = 0;
+            if (!std::isfinite(x) || !std::isfinite(yy) || !std::isfinite(y[k]) || !std::isfinite(noise_var[k])) kind = 1;
+            else if (x < 0.0 || x > nx - 1.0 || yy < 0.0 || yy > ny - 1.0) kind = 2;
+            else if (!(noise_var[k] > 0.0)) kind = 3;
+            if (kind) {
+                first_bad[(size_t)ch] = k;
+                bad_kind[(size_t)ch] = kind;
+                return;
+            }
+            int j0 = (int)std::floor(x), i0 = (int)std::floor(yy);
+            if (j0 > nx - 2) j0 = nx - 2;
+            if (i0 > ny - 2) i0 = ny - 2;
+            base[(size_t)k] = i0 * nx + j0;
+        }
+    });
+    for (int ch = 0; ch < nchunk; ++ch) {
+        const int64_t k = first_bad[(size_t)ch];
+        if (k < 0) continue;
+        if (bad_kind[(size_t)ch] == 1) return fail(c, GABP_ERR_ARG, "non-finite observation data at index " + std::to_string(k));
+        if (bad_kind[(size_t)ch] == 2) return fail(c, GABP_ERR_ARG, "observation " + std::to_string(k) + " outside the grid");
+        return fail(c, GABP_ERR_ARG, "noise variance must be > 0");
     }
-    // stable LSD radix sort of the observations by base cell (two 15-bit digits: base < 2^30),
-    // with bucket arrays of 2^15 entries instead of one per cell; the per-cell index optr is
-    // then built on the GPU from the sorted base cells
+    // stable LSD radix sort of the observations by base cell (two 15-bit digits: base < 2^30):
+    // per chunk digit counts, offsets in (digit, chunk) order, then each chunk places its own
+    // elements in order, so the result is the stable order whatever the chunking; the per-cell
+    // index optr is then built on the GPU from the sorted base cells
     std::vector<int> perm((size_t)m), tmp((size_t)m);
-    for (int64_t k = 0; k < m; ++k) perm[(size_t)k] = (int)k;
+    parallel_chunks(m, nchunk, [&](int, int64_t k0, int64_t k1) {
+        for (int64_t k = k0; k < k1; ++k) perm[(size_t)k] = (int)k;
+    });
     {
         constexpr int DIG = 15, NB = 1 << DIG;
-        std::vector<int> cnt(NB + 1);
+        std::vector<int64_t> cnt((size_t)nchunk * NB);
         for (int pass = 0; pass < 2; ++pass) {
             const int shift = pass * DIG;
-            std::fill(cnt.begin(), cnt.end(), 0);
-            for (int64_t k = 0; k < m; ++k) ++cnt[(size_t)((base[(size_t)k] >> shift) & (NB - 1)) + 1];
-            for (int b = 0; b < NB; ++b) cnt[(size_t)b + 1] += cnt[(size_t)b];
-            for (int64_t k = 0; k < m; ++k) {
-                const int src = perm[(size_t)k];
-                tmp[(size_t)cnt[(size_t)((base[(size_t)src] >> shift) & (NB - 1))]++] = src;
-            }
+            parallel_chunks(m, nchunk, [&](int ch, int64_t k0, int64_t k1) {
+                int64_t *h = cnt.data() + (size_t)ch * NB;
+                std::fill(h, h + NB, 0);
+                for (int64_t k = k0; k < k1; ++k) ++h[(base[(size_t)perm[(size_t)k]] >> shift) & (NB - 1)];
+            });
+            int64_t run = 0;
+            for (int b = 0; b < NB; ++b)
+                for (int ch = 0; ch < nchunk; ++ch) {
+                    int64_t &v = cnt[(size_t)ch * NB + b];
+                    const int64_t t = v;
+                    v = run;
+                    run += t;
+                }
+            parallel_chunks(m, nchunk, [&](int ch, int64_t k0, int64_t k1) {
+                int64_t *o = cnt.data() + (size_t)ch * NB;
+                for (int64_t k = k0; k < k1; ++k) {
+                    const int src = perm[(size_t)k];
+                    tmp[(size_t)o[(base[(size_t)src] >> shift) & (NB - 1)]++] = src;
+                }
+            });
             perm.swap(tmp);
         }
     }
     std::vector<int> sbase((size_t)m);
     std::vector<double> sxy((size_t)(2 * m)), sy((size_t)m), svar((size_t)m);
-    for (int64_t d = 0; d < m; ++d) {
-        const int64_t k = perm[(size_t)d];
-        sbase[(size_t)d] = base[(size_t)k];
-        sxy[2 * (size_t)d] = obs_xy[2 * k];
-        sxy[2 * (size_t)d + 1] = obs_xy[2 * k + 1];
-        sy[(size_t)d] = y[k];
-        svar[(size_t)d] = noise_var[k];
-    }
+    parallel_chunks(m, nchunk, [&](int, int64_t d0, int64_t d1) {
+        for (int64_t d = d0; d < d1; ++d) {
+            const int64_t k = perm[(size_t)d];
+            sbase[(size_t)d] = base[(size_t)k];
+            sxy[2 * (size_t)d] = obs_xy[2 * k];
+            sxy[2 * (size_t)d + 1] = obs_xy[2 * k + 1];
+            sy[(size_t)d] = y[k];
+            svar[(size_t)d] = noise_var[k];
+        }
+    });
 
     c->kappa = kappa;
     if (m >= 2) {
