@@ -888,16 +888,19 @@ int batch_upload_active(gabp_batch *b) {
     return GABP_OK;
 }
 
-// Tensor maps of the problems whose rows are 16-byte strided, with boxes for 30 x ty tiles (the
-// batched TMA kernel copies the other problems' tiles with cp.async).
+// Tensor maps with boxes for 30 x ty tiles: the message planes of the problems with nx even and
+// the observation index of those with nx a multiple of 4 (16-byte row strides); the batched
+// TMA kernel copies the other parts with cp.async.
 int batch_encode_maps(gabp_batch *b, int ty) {
     const int count = (int)b->inst.size();
     std::vector<gabp::TmaMapsGlobal> maps(count);
     std::memset((void *)maps.data(), 0, sizeof(gabp::TmaMapsGlobal) * count);
     for (int i = 0; i < count; ++i) {
-        if (!gabp::tma_problem_supported(b->inst[i]->p)) continue;
+        const int nxi = b->inst[i]->p.nx;
+        const int parts = (nxi % 2 == 0 ? gabp::TMA_MAP_PLANES : 0) | (nxi % 4 == 0 ? gabp::TMA_MAP_OPTR : 0);
+        if (!parts) continue;
         gabp::TmaMaps m{};
-        BK(gabp::make_tma_maps(b->inst[i]->p, 30, ty, m), "tensor map encode");
+        BK(gabp::make_tma_maps(b->inst[i]->p, 30, ty, m, parts), "tensor map encode");
         maps[i].planes[0] = m.planes[0];
         maps[i].planes[1] = m.planes[1];
         maps[i].optr = m.optr;

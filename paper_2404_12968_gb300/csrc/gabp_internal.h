@@ -152,7 +152,9 @@ cudaError_t launch_tma_batch(const TmaBatchArgs &ba, const DevProblem &first, in
                              double beta, cudaStream_t st);
 bool tma_shape_supported(int tx, int ty);
 bool tma_problem_supported(const DevProblem &p);
-cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps);
+// parts: which maps to encode (planes need nx even, the observation index nx a multiple of 4)
+constexpr int TMA_MAP_PLANES = 1, TMA_MAP_OPTR = 2;
+cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps, int parts = TMA_MAP_PLANES | TMA_MAP_OPTR);
 size_t tma_smem_bytes(int tx, int ty);
 cudaError_t launch_tma_iteration(const DevProblem &p, const TmaMaps &maps, int src, double beta,
                                  cudaStream_t st);

@@ -15,15 +15,18 @@ def _built():
 
 
 def _mixed_batch():
-    """Uneven sizes: nx a multiple of 4 (tensor copies in the TMA kernel) and not (cp.async
-    copies), a problem smaller than one tile, one without observations, ragged tile edges."""
+    """Uneven sizes: every width class of the TMA kernel's copies, a problem smaller than one
+    tile, one without observations, ragged tile edges."""
     probs = gabp_synth.config_batch(seed=3, count=6, lo=48, hi=200)
     probs += [gabp_synth.make_problem(64, 37, 0.1, 1, n_uniform=200, n_tracks=2, per_track=64, sigma=(0.02, 0.1)),
               gabp_synth.make_problem(61, 30, 0.1, 2, n_uniform=150, sigma=0.05),
               gabp_synth.make_problem(7, 5, 0.2, 3, n_uniform=6, sigma=0.1),
               gabp_synth.make_problem(33, 62, 0.05, 4),
-              gabp_synth.make_problem(120, 91, 0.03, 5, n_tracks=3, per_track=200, sigma=0.05)]
-    assert any(p.nx % 4 == 0 for p in probs) and any(p.nx % 4 for p in probs)
+              gabp_synth.make_problem(120, 91, 0.03, 5, n_tracks=3, per_track=200, sigma=0.05),
+              gabp_synth.make_problem(62, 31, 0.08, 6, n_uniform=120, n_tracks=2, per_track=60, sigma=0.05)]
+    # widths: multiples of 4 (tensor copies), 2 mod 4 (planes by tensor copies, index by
+    # cp.async) and odd (cp.async)
+    assert {p.nx % 4 for p in probs} >= {0, 1, 2} and any(p.nx % 2 for p in probs)
     return probs
 
 
