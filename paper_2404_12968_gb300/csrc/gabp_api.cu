@@ -1449,7 +1449,7 @@ int mg_run_level(gabp_ctx *c, double damping, double tol, int max_iters, double 
         c->opt.tol = tol;
         c->opt.max_iters = max_iters;
         rc = gabp_iterate(c, -1, damping);
-        if (rc == GABP_ERR_TIMEOUT || rc == GABP_ERR_DIVERGED) rc = GABP_OK;   // judged by the residual
+        if (rc == GABP_ERR_TIMEOUT || rc == GABP_ERR_DIVERGED) rc = GABP_OK;   // decided by the residual
     } else {
         rc = gabp_iterate(c, max_iters, damping);
     }
