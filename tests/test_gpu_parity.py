@@ -105,11 +105,14 @@ def test_fp64_warm_start_matches_oracle(orc):
 # ---------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-@pytest.mark.parametrize("shape", [(67, 45), (68, 45), (256, 130), (300, 7)])
+@pytest.mark.parametrize("shape", [(67, 45), (68, 45), (256, 130), (300, 7), (4, 2), (4, 37), (124, 1), (32, 15)])
 def test_split_and_fused_bit_identical(prec, shape):
+    """Every kernel and tile shape gives the same bits; includes the narrowest TMA grid (4
+    columns), a single row without observations and tiles ragged in both directions."""
     nx, ny = shape
-    p = gabp_synth.make_problem(nx, ny, 0.05, 9, n_tracks=4, per_track=nx, n_uniform=nx * ny // 20,
-                                sigma=(0.02, 0.1))
+    obs = nx >= 2 and ny >= 2
+    p = gabp_synth.make_problem(nx, ny, 0.05, 9, n_tracks=4 if obs else 0, per_track=nx,
+                                n_uniform=max(nx * ny // 20, 2) if obs else 0, sigma=(0.02, 0.1))
     variants = [(2, (0, 0)), (1, (32, 8)), (1, (64, 16)), (1, (128, 8)), (1, (32, 32))]
     if prec == "fp32" and nx % 4 == 0:
         variants += [(3, (30, 14)), (3, (30, 22)), (3, (30, 30))]
