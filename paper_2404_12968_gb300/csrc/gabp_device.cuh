@@ -92,8 +92,8 @@ __device__ __forceinline__ void add_obs_pair(CompSum<T> &se, CompSum<T> &sl, con
                                              int hi, int cl, int cr) {
     for (int k = lo; k < hi; ++k) {
         const int c = k < mid ? cl : cr;
-        se.add(O[8 * (int64_t)k + c]);
-        sl.add(O[8 * (int64_t)k + 4 + c]);
+        se.add(O[8 * (int64_t)k + 2 * c]);
+        sl.add(O[8 * (int64_t)k + 2 * c + 1]);
     }
 }
 

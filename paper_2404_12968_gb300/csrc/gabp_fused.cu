@@ -167,16 +167,16 @@ __global__ void __launch_bounds__(FT) k_fused(DevProblem p, int src, T beta) {
             T oe[4], ol[4], lam[4], eta[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                oe[u] = O[8 * k + u];
-                ol[u] = O[8 * k + 4 + u];
+                oe[u] = O[8 * k + 2 * u];
+                ol[u] = O[8 * k + 2 * u + 1];
                 cavity(sb[bidx[u]], oe[u], ol[u], eta[u], lam[u]);
             }
             T L[4], E[4];
             factor_messages<T, 4>(a, YV[2 * k + 1], YV[2 * k], lam, eta, L, E);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                OQ[8 * k + u] = damp(oe[u], E[u], beta);
-                OQ[8 * k + 4 + u] = damp(ol[u], L[u], beta);
+                OQ[8 * k + 2 * u] = damp(oe[u], E[u], beta);
+                OQ[8 * k + 2 * u + 1] = damp(ol[u], L[u], beta);
             }
         }
     }

@@ -156,7 +156,7 @@ __device__ __forceinline__ float2 cavity2(const Belief2 &b, float2 own) { return
 __device__ __forceinline__ void add_obs_pair2(CompSum2 &s, const float *O, int lo, int mid, int hi, int cl, int cr) {
     for (int k = lo; k < hi; ++k) {
         const int c = k < mid ? cl : cr;
-        s.add(f2(O[8 * (int64_t)k + c], O[8 * (int64_t)k + 4 + c]));
+        s.add(*reinterpret_cast<const float2 *>(O + 8 * (int64_t)k + 2 * c));
     }
 }
 
@@ -449,11 +449,11 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                     }
                     if (lo1 < hi1) {
                         const int c = lo1 < mid1 ? 1 : 0;
-                        first1 = f2(O[8 * (int64_t)lo1 + c], O[8 * (int64_t)lo1 + 4 + c]);
+                        first1 = *reinterpret_cast<const float2 *>(O + 8 * (int64_t)lo1 + 2 * c);
                     }
                     if (lo2 < hi2) {
                         const int c = lo2 < mid2 ? 3 : 2;
-                        first2 = f2(O[8 * (int64_t)lo2 + c], O[8 * (int64_t)lo2 + 4 + c]);
+                        first2 = *reinterpret_cast<const float2 *>(O + 8 * (int64_t)lo2 + 2 * c);
                     }
                 }
                 CompSum2 s(sm[(DIR_C * RY + ry) * RX + rx]);
@@ -534,25 +534,18 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                                               &sb[(ly + 1) * BX + lx + 1]};
                 const float4 w4 = *reinterpret_cast<const float4 *>(Wt + 4 * k);
                 const float aw[4] = {w4.x, w4.y, w4.z, w4.w};
-                const float4 oe4 = *reinterpret_cast<const float4 *>(O + 8 * k);
-                const float4 ol4 = *reinterpret_cast<const float4 *>(O + 8 * k + 4);
-                const float oe[4] = {oe4.x, oe4.y, oe4.z, oe4.w};
-                const float ol[4] = {ol4.x, ol4.y, ol4.z, ol4.w};
-                float2 own4[4], cav[4];
+                const float4 o01 = *reinterpret_cast<const float4 *>(O + 8 * k);   // (eta, Lambda) x 2
+                const float4 o23 = *reinterpret_cast<const float4 *>(O + 8 * k + 4);
+                float2 own4[4] = {f2(o01.x, o01.y), f2(o01.z, o01.w), f2(o23.x, o23.y), f2(o23.z, o23.w)}, cav[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    own4[u] = f2(oe[u], ol[u]);
-                    cav[u] = cavity2(*ob[u], own4[u]);
-                }
+                for (int u = 0; u < 4; ++u) cav[u] = cavity2(*ob[u], own4[u]);
                 const float2 yv = *reinterpret_cast<const float2 *>(YV + 2 * k);
                 float2 msg[4];
                 factor_messages2<4>(aw, yv.y, yv.x, cav, msg);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) msg[u] = damp2(own4[u], msg[u], beta2);
-                const float4 ne = make_float4(msg[0].x, msg[1].x, msg[2].x, msg[3].x);
-                const float4 nl = make_float4(msg[0].y, msg[1].y, msg[2].y, msg[3].y);
-                *reinterpret_cast<float4 *>(OQ + 8 * k) = ne;
-                *reinterpret_cast<float4 *>(OQ + 8 * k + 4) = nl;
+                *reinterpret_cast<float4 *>(OQ + 8 * k) = make_float4(msg[0].x, msg[0].y, msg[1].x, msg[1].y);
+                *reinterpret_cast<float4 *>(OQ + 8 * k + 4) = make_float4(msg[2].x, msg[2].y, msg[3].x, msg[3].y);
             }
         }
     }

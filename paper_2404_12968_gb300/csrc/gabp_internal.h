@@ -23,7 +23,7 @@ struct DevProblem {
     const float2 *owdf;  // FP32 contexts: 4 * m observation weights as double-float (hi, lo) pairs
     const float2 *oysdf; // FP32 contexts: 2 * m (y, 1/sigma^2) as double-float pairs
     void *P[2];          // prior messages, ping-pong: 5 * n (eta, Lambda) pairs
-    void *O[2];          // observation messages, ping-pong: 8 * m values
+    void *O[2];          // observation messages, ping-pong: per observation (eta, Lambda) of corners 0..3, interleaved
     const int *obase;    // m base-cell indices (sorted ascending)
     const void *ow;      // 4 * m bilinear weights (T)
     const void *ovar;    // 2 * m (y, sigma^2) pairs (T)

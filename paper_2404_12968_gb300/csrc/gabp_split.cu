@@ -231,16 +231,16 @@ template <typename T> __global__ void k_obs(DevProblem p, int src, T beta) {
     T oe[4], ol[4], lam[4], eta[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        oe[u] = O[8 * k + u];
-        ol[u] = O[8 * k + 4 + u];
+        oe[u] = O[8 * k + 2 * u];
+        ol[u] = O[8 * k + 2 * u + 1];
         cavity(load_belief<T>(p, node[u]), oe[u], ol[u], eta[u], lam[u]);
     }
     T L[4], E[4];
     factor_messages<T, 4>(a, YV[2 * k + 1], YV[2 * k], lam, eta, L, E);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        Q[8 * k + u] = damp(oe[u], E[u], beta);
-        Q[8 * k + 4 + u] = damp(ol[u], L[u], beta);
+        Q[8 * k + 2 * u] = damp(oe[u], E[u], beta);
+        Q[8 * k + 2 * u + 1] = damp(ol[u], L[u], beta);
     }
 }
 
@@ -270,8 +270,8 @@ template <typename T> __global__ void k_init_obs(DevProblem p, int dst, int pape
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const double w = p.ow64[4 * k + u];
-        Q[8 * k + u] = T(0);
-        Q[8 * k + 4 + u] = paper ? T(1e-8) : T(p.oys64[2 * k + 1] * w * w);
+        Q[8 * k + 2 * u] = T(0);
+        Q[8 * k + 2 * u + 1] = paper ? T(1e-8) : T(p.oys64[2 * k + 1] * w * w);
     }
 }
 
@@ -323,8 +323,8 @@ __global__ void k_init_warm_obs(DevProblem p, int dst, const double *mu0, const 
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const double L = lam0[node[u]] / (double)node_slots(p, node[u]);
-        Q[8 * k + u] = T(mu0[node[u]] * L);
-        Q[8 * k + 4 + u] = T(L);
+        Q[8 * k + 2 * u] = T(mu0[node[u]] * L);
+        Q[8 * k + 2 * u + 1] = T(L);
     }
 }
 
@@ -729,8 +729,8 @@ __global__ void k_init_nodes_obs(DevProblem p, int dst, const float2 *nm) {
     const int64_t b = p.obase[k];
     const float2 m0 = nm[b], m1 = nm[b + 1], m2 = nm[b + p.nx], m3 = nm[b + p.nx + 1];
     float4 *Q = (float4 *)((float *)p.O[dst] + 8 * k);
-    Q[0] = make_float4(m0.x, m1.x, m2.x, m3.x);
-    Q[1] = make_float4(m0.y, m1.y, m2.y, m3.y);
+    Q[0] = make_float4(m0.x, m0.y, m1.x, m1.y);
+    Q[1] = make_float4(m2.x, m2.y, m3.x, m3.y);
 }
 
 __global__ void k_ws_decode(DevProblem p, double scale, int Wp, const float *out, double *mu0, double *lam0) {

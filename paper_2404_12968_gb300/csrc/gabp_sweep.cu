@@ -236,23 +236,23 @@ __device__ __forceinline__ void obs_batch(const DevProblem &p, const WarpRing &r
             const Belief<float> *ob[4] = {&r0[lb], &r0[lb + 1], &r1[lb], &r1[lb + 1]};
             const float4 w4 = *reinterpret_cast<const float4 *>(Wt + 4 * k);
             const float a4[4] = {w4.x, w4.y, w4.z, w4.w};
-            const float4 oe4 = *reinterpret_cast<const float4 *>(O + 8 * k);
-            const float4 ol4 = *reinterpret_cast<const float4 *>(O + 8 * k + 4);
-            const float oe[4] = {oe4.x, oe4.y, oe4.z, oe4.w};
-            const float ol[4] = {ol4.x, ol4.y, ol4.z, ol4.w};
+            const float4 o01 = *reinterpret_cast<const float4 *>(O + 8 * k);       // (eta, Lambda) x 2
+            const float4 o23 = *reinterpret_cast<const float4 *>(O + 8 * k + 4);
+            const float oe[4] = {o01.x, o01.z, o23.x, o23.z};
+            const float ol[4] = {o01.y, o01.w, o23.y, o23.w};
             float olam[4], oeta[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) cavity(*ob[u], oe[u], ol[u], oeta[u], olam[u]);
             float OL[4], OE[4];
             const float2 yv = *reinterpret_cast<const float2 *>(YV + 2 * k);
             factor_messages<float, 4>(a4, yv.y, yv.x, olam, oeta, OL, OE);
-            float4 ne, nl;
-            ne.x = damp(oe[0], OE[0], beta); ne.y = damp(oe[1], OE[1], beta);
-            ne.z = damp(oe[2], OE[2], beta); ne.w = damp(oe[3], OE[3], beta);
-            nl.x = damp(ol[0], OL[0], beta); nl.y = damp(ol[1], OL[1], beta);
-            nl.z = damp(ol[2], OL[2], beta); nl.w = damp(ol[3], OL[3], beta);
-            *reinterpret_cast<float4 *>(OQ + 8 * k) = ne;
-            *reinterpret_cast<float4 *>(OQ + 8 * k + 4) = nl;
+            float4 n01, n23;
+            n01.x = damp(oe[0], OE[0], beta); n01.y = damp(ol[0], OL[0], beta);
+            n01.z = damp(oe[1], OE[1], beta); n01.w = damp(ol[1], OL[1], beta);
+            n23.x = damp(oe[2], OE[2], beta); n23.y = damp(ol[2], OL[2], beta);
+            n23.z = damp(oe[3], OE[3], beta); n23.w = damp(ol[3], OL[3], beta);
+            *reinterpret_cast<float4 *>(OQ + 8 * k) = n01;
+            *reinterpret_cast<float4 *>(OQ + 8 * k + 4) = n23;
         }
     }
 }

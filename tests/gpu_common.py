@@ -34,16 +34,16 @@ def solver(p: gabp_synth.Problem, precision="fp32", **opts):
 
 
 def decode_messages(buf: np.ndarray, p: gabp_synth.Problem, precision="fp32"):
-    """Split the opaque message buffer into prior planes (5, n, 2) and obs messages (m, 8).
+    """Split the opaque message buffer into prior planes (5, n, 2) and obs messages (m, 4, 2).
 
     The layout is the library's (documented in its device header): 5 prior planes of
-    (eta, Lambda) pairs in outgoing order C, W, E, S, N, then 8 values per observation in
-    base-cell-sorted order."""
+    (eta, Lambda) pairs in outgoing order C, W, E, S, N, then per observation (in
+    base-cell-sorted order) the (eta, Lambda) pairs of its four corners."""
     dt = np.float64 if precision == "fp64" else np.float32
     a = buf.view(dt)
     n, m = p.n, p.m
     prior = a[: 10 * n].reshape(5, n, 2)
-    obs = a[10 * n: 10 * n + 8 * m].reshape(m, 8)
+    obs = a[10 * n: 10 * n + 8 * m].reshape(m, 4, 2)   # corner, (eta, Lambda)
     return prior, obs
 
 

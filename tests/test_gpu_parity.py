@@ -221,8 +221,8 @@ def _gpu_state_to_oracle_slots(orc, p, fl, prior, obs):
     order, _, _ = sorted_obs_order(orc, p)
     oe = np.empty((p.m, 4))
     ol = np.empty((p.m, 4))
-    oe[order] = obs[:, :4]
-    ol[order] = obs[:, 4:]
+    oe[order] = obs[:, :, 0]
+    ol[order] = obs[:, :, 1]
     me = np.concatenate([pe, oe.reshape(-1)])
     ml = np.concatenate([pl, ol.reshape(-1)])
     assert me.shape[0] == fl.ne
