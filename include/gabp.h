@@ -112,7 +112,9 @@ typedef struct {
     int debug_flags;  /* 0 (default).  Bit 0 is a test hook for failure detection: every launch of
                          the TMA kernel first waits on an mbarrier that nothing completes, so its
                          bounded wait runs out (after ~2 ms) and gabp_iterate returns
-                         GABP_ERR_TIMEOUT without having changed the messages. */
+                         GABP_ERR_TIMEOUT without having changed the messages; for a batch
+                         the batched TMA kernel does the same and gabp_batch_iterate
+                         returns GABP_ERR_TIMEOUT (its messages are then unspecified). */
 } gabp_options;
 
 typedef struct {

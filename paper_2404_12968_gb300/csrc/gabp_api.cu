@@ -855,6 +855,7 @@ cudaError_t batch_launch(gabp_batch *b, int src, double beta, cudaStream_t st) {
         ba.nitems = b->d_items;
         ba.items = reinterpret_cast<const int2 *>(b->d_items + 2);
         ba.err = b->d_err;
+        ba.debug_stall = (b->opt.debug_flags & 1) ? 1 : 0;
         // the grid does not depend on the active set, so captured graphs stay valid when it changes
         return gabp::launch_tma_batch(ba, b->inst[0]->p, b->H, b->all_tiles, src, beta, st);
     }

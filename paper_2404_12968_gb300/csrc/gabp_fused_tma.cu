@@ -347,12 +347,12 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         *flag = 0;
     }
     __syncthreads();
-    if (!BATCH && p.debug_stall) {
+    if (BATCH ? ba.debug_stall : p.debug_stall) {
         // failure-detection test: wait on a barrier that nothing arrives on, before any copy is
         // issued; the bounded wait runs out, the block raises the error flag and returns
         if (tid == 0 && !mbar_wait(smem_addr(&bars[S]), 0, 1LL << 22)) {
             *flag = 1;
-            atomicExch(p.err, 1);
+            atomicExch(BATCH ? ba.err : p.err, 1);
         }
         __syncthreads();
         if (*flag) return;

@@ -146,6 +146,7 @@ struct TmaBatchArgs {
     const int2 *items;
     const int *nitems;
     int *err;
+    int debug_stall;   // test hook, as DevProblem::debug_stall
 };
 bool tma_batch_shape_supported(int ty);   // tile heights of the batched TMA kernel (22, 30)
 cudaError_t launch_tma_batch(const TmaBatchArgs &ba, const DevProblem &first, int ty, int max_tiles, int src,

@@ -103,3 +103,17 @@ def test_batch_argument_errors():
     bad[1].noise_var[0] = -1.0
     with pytest.raises(GabpError, match="problem 1"):
         Batch(bad)
+
+
+def test_batched_tma_bounded_wait_reports_timeout():
+    """Failure detection without a GPU fault in the batched TMA kernel: its first wait is on a
+    barrier that nothing completes; the bounded wait runs out and the call reports
+    GABP_ERR_TIMEOUT; a fresh batch runs normally."""
+    from paper_2404_12968_gb300 import Batch, GabpError, GABP_KERNEL_TMA
+    probs = gabp_synth.config_batch(seed=7, count=3, lo=40, hi=90)
+    with Batch(probs, kernel=GABP_KERNEL_TMA, tile_y=30, debug_flags=1) as b:
+        with pytest.raises(GabpError, match="TIMEOUT"):
+            b.iterate(2, 0.3)
+    with Batch(probs, kernel=GABP_KERNEL_TMA, tile_y=30) as b:
+        b.iterate(2, 0.3)
+        assert np.all(np.isfinite(b.residuals()))
