@@ -318,16 +318,18 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
         if (bad_kind[(size_t)ch] == 2) return fail(c, GABP_ERR_ARG, "observation " + std::to_string(k) + " outside the grid");
         return fail(c, GABP_ERR_ARG, "noise variance must be > 0");
     }
-    // stable LSD radix sort of the observations by base cell (two 15-bit digits: base < 2^30):
-    // per chunk digit counts, offsets in (digit, chunk) order, then each chunk places its own
-    // elements in order, so the result is the stable order whatever the chunking; the per-cell
-    // index optr is then built on the GPU from the sorted base cells
+    // stable LSD radix sort of the observations by base cell (two digits of half the key width,
+    // base < n <= 2^30): per chunk digit counts, offsets in (digit, chunk) order, then each
+    // chunk places its own elements in order, so the result is the stable order whatever the
+    // chunking; the per-cell index optr is then built on the GPU from the sorted base cells
     std::vector<int> perm((size_t)m), tmp((size_t)m);
     parallel_chunks(m, nchunk, [&](int, int64_t k0, int64_t k1) {
         for (int64_t k = k0; k < k1; ++k) perm[(size_t)k] = (int)k;
     });
     {
-        constexpr int DIG = 15, NB = 1 << DIG;
+        int bits = 1;
+        while (bits < 30 && ((int64_t)1 << bits) < n) ++bits;
+        const int DIG = bits < 16 ? 8 : (bits + 1) / 2, NB = 1 << DIG;   // fewer buckets: cache-friendly scatter
         std::vector<int64_t> cnt((size_t)nchunk * NB);
         for (int pass = 0; pass < 2; ++pass) {
             const int shift = pass * DIG;
@@ -369,10 +371,25 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
 
     c->kappa = kappa;
     if (m >= 2) {
-        double mean = 0.0, sq = 0.0;
-        for (int64_t k = 0; k < m; ++k) mean += y[k];
-        mean /= (double)m;
-        for (int64_t k = 0; k < m; ++k) sq += (y[k] - mean) * (y[k] - mean);
+        // sample standard deviation of y: partial sums over a fixed partition (64 parts,
+        // whatever the thread count), added in part order
+        constexpr int PARTS = 64;
+        std::vector<double> part((size_t)PARTS);
+        auto sum_parts = [&](auto term) {
+            parallel_chunks(PARTS, host_chunks(m) > 1 ? (int)std::min<int64_t>(PARTS, host_chunks(m)) : 1,
+                            [&](int, int64_t q0, int64_t q1) {
+                                for (int64_t q = q0; q < q1; ++q) {
+                                    double acc = 0.0;
+                                    for (int64_t k = m * q / PARTS; k < m * (q + 1) / PARTS; ++k) acc += term(k);
+                                    part[(size_t)q] = acc;
+                                }
+                            });
+            double total = 0.0;
+            for (double v : part) total += v;
+            return total;
+        };
+        const double mean = sum_parts([&](int64_t k) { return y[k]; }) / (double)m;
+        const double sq = sum_parts([&](int64_t k) { return (y[k] - mean) * (y[k] - mean); });
         const double sd = std::sqrt(sq / (double)(m - 1));
         c->yscale = sd > 0.0 ? sd : 1.0;
     }
