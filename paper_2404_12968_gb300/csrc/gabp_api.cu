@@ -9,7 +9,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "gabp.h"
@@ -33,7 +35,7 @@ struct gabp_ctx {
     int64_t edges = 0;
     double bytes_per_iter = 0.0;
     std::string err;
-    std::vector<void *> allocs;
+    std::vector<std::pair<void *, bool>> allocs;   // device buffers (pointer, from the pool)
     double *stage = nullptr;      // 2 n doubles of device staging for host <-> device transfers
     double *hscal = nullptr;      // pinned host copy of p.scal
     cudaGraphExec_t gexec = nullptr;
@@ -81,12 +83,40 @@ int cuda_fail(gabp_ctx *c, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
+// Device memory of contexts comes from one stream-ordered pool per device, which keeps up to
+// 8 GiB of freed memory for the next context: repeated create / destroy of a problem (a new
+// analysis window on the same grid) reuses it instead of mapping and unmapping pages.
+cudaMemPool_t context_pool(int dev) {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0) return nullptr;
+    if ((int)pools.size() <= dev) pools.resize((size_t)dev + 1, nullptr);
+    if (!pools[(size_t)dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = (uint64_t)8 << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[(size_t)dev] = pool;
+    }
+    return pools[(size_t)dev];
+}
+
 int dalloc(gabp_ctx *c, void **ptr, size_t bytes, const char *what) {
     *ptr = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(ptr, bytes);
+    cudaMemPool_t pool = context_pool(c->dev);
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(ptr, bytes, pool, c->stream) : cudaMalloc(ptr, bytes);
     if (e != cudaSuccess) return cuda_fail(c, e, what);
-    c->allocs.push_back(*ptr);
+    c->allocs.push_back({*ptr, pool != nullptr});
     return GABP_OK;
 }
 
@@ -213,7 +243,11 @@ void free_all(gabp_ctx *c) {
     drop_graph(c);
     if (c->ws_x) cudaFree(c->ws_x);
     c->ws_x = nullptr;
-    for (void *q : c->allocs) cudaFree(q);
+    for (const auto &a : c->allocs) {
+        if (a.second) cudaFreeAsync(a.first, c->stream);
+        else cudaFree(a.first);
+    }
+    if (!c->allocs.empty() && c->stream) cudaStreamSynchronize(c->stream);   // freed before reuse
     c->allocs.clear();
     if (c->hscal) cudaFreeHost(c->hscal);
     c->hscal = nullptr;
