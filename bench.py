@@ -391,11 +391,29 @@ def _oracle_rate(p, iters: int):
     return p.n * iters / dt, dt, cores
 
 
+def _single_core_rate(timeout_s: float = 120.0):
+    """One oracle GaBP iteration of the full workload on one host core (a child process with
+    OMP_NUM_THREADS=1); None if it does not finish in time."""
+    import subprocess
+    code = ("import sys, time; sys.path.insert(0, %r); import bench, oracle; p = bench.make_problem(0); "
+            "fl = oracle.build_factors(p.nx, p.ny, p.kappa, p.obs_x, p.obs_y, p.y, p.noise_var); "
+            "me, ml = oracle.init_messages(fl, 'cold'); t = time.perf_counter(); "
+            "oracle.gabp(fl, bench.DAMPING, 1, messages=(me, ml)); print(p.n / (time.perf_counter() - t))" % ROOT)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=timeout_s)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        return None
+
+
 def cpu_baseline(p):
     rate, dt, cores = _oracle_rate(p, 2)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"2 oracle GaBP iterations (FP64, C + OpenMP over factors) on the full "
-                      f"{p.nx}x{p.ny} workload, {dt:.1f} s"}
+                      f"{p.nx}x{p.ny} workload, {dt:.1f} s",
+            "single_core": {"value": _single_core_rate(), "unit": UNIT, "cores": 1,
+                            "sample": "one oracle GaBP iteration of the full workload, OMP_NUM_THREADS=1"}}
 
 
 def reference_arm(args):
