@@ -1233,7 +1233,7 @@ int batch_create_impl(gabp_batch *b, int count, const gabp_problem *problems) {
     io.device = b->dev;
     for (int i = 0; i < count; ++i) {
         const gabp_problem &pr = problems[i];
-        gabp_prior prior{pr.gamma > 0.0 ? pr.gamma : 1.0, 0};
+        gabp_prior prior{pr.gamma > 0.0 ? pr.gamma : 1.0, 0, 2};
         gabp_ctx *c = nullptr;
         const int rc = gabp_create(&c, pr.grid, pr.kappa, &prior, pr.m, pr.obs_xy, pr.y, pr.noise_var, &io);
         if (rc) return bfail(b, rc, "problem " + std::to_string(i) + ": " + gabp_create_error());
@@ -1544,7 +1544,7 @@ int gabp_mg_create(gabp_mg **out, gabp_ctx *ctx, int levels) {
             xy[2 * i + 1] = std::min(ctx->hxy[2 * i + 1] / s, (double)(nyk - 1));
         }
         gabp_grid gk{nxk, nyk, 1.0};
-        gabp_prior pk{ctx->p.gamma / ((double)s * s), 0};
+        gabp_prior pk{ctx->p.gamma / ((double)s * s), 0, 2};
         gabp_options ok = ctx->opt;
         ok.kernel = GABP_KERNEL_AUTO;
         ok.tile_x = ok.tile_y = 0;
