@@ -92,3 +92,41 @@ def test_pairwise_argument_errors():
         for args in [(-1, 10.0, 0.6), (5, 0.0, 0.6), (5, 10.0, 0.0), (5, 10.0, 1.5)]:
             with pytest.raises(GabpError):
                 pw.iterate(*args)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_reproduces_the_papers_grid_search_on_the_gpu(orc, prec):
+    """The App. D grid search (golden table, 128^2, 5 % observed, the paper's synthetic
+    setting) on the GPU kernels: the same cells diverge, and the converging cells' errors
+    follow the order of the paper's ratios (see the oracle's test of the same table)."""
+    import os
+    from paper_2404_12968_gb300 import Pairwise
+    path = os.path.join(os.path.dirname(__file__), "golden", "pairwise_grid_search_128.txt")
+    rows = [ln.split(":") for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    cs = [float(v) for v in rows[0][1].split()]
+    table = {float(k): [None if v == "-" else float(v) for v in vals.split()] for k, vals in rows[1:]}
+    p = gabp_synth.paper_synthetic(128, 0.05, 0)
+    fl = orc.build_factors(p.nx, p.ny, p.kappa, p.obs_x, p.obs_y, p.y, p.noise_var, gamma=p.gamma)
+    exact = orc.exact_mean(fl, p.nx)
+    nrm = np.linalg.norm(exact)
+    with solver(p, prec, gamma=p.gamma) as s, Pairwise(s) as pw:
+        for eta, paper in table.items():
+            ours = []
+            for c in cs:
+                pw.reset()
+                err = None
+                for _ in range(4):
+                    pw.iterate(100, c, eta)
+                    mean, _ = pw.marginals(want_var=False)
+                    with np.errstate(all="ignore"):
+                        err = np.linalg.norm(mean - exact) / nrm
+                    if not np.isfinite(err) or err > 1.0:
+                        err = None
+                        break
+                ours.append(err)
+            assert [e is None for e in ours] == [v is None for v in paper], (eta, ours, paper)
+            conv = [i for i, v in enumerate(paper) if v is not None]
+            for i in conv:
+                for j in conv:
+                    if paper[i] < paper[j]:
+                        assert ours[i] < ours[j], (eta, cs[i], cs[j], ours[i], ours[j])

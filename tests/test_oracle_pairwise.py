@@ -78,3 +78,45 @@ def test_reproduces_the_papers_convergence_pattern():
         e1 = np.linalg.norm(m1 - exact) / np.linalg.norm(exact)
         e2 = np.linalg.norm(m2 - exact) / np.linalg.norm(exact)
         assert e2 < e1 < 1.0, (c, e1, e2)
+
+
+def _golden_grid_search():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "pairwise_grid_search_128.txt")
+    rows = [ln.split(":") for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    cs = [float(v) for v in rows[0][1].split()]
+    table = {float(k): [None if v == "-" else float(v) for v in vals.split()] for k, vals in rows[1:]}
+    return cs, table
+
+
+def test_reproduces_the_papers_grid_search_on_its_synthetic_setting():
+    """The paper's synthetic setting at 128^2 with 5 % of the grid observed (App. E data, the
+    App. D grid search): every (c, eta) cell diverges or converges as the paper's table says,
+    and among the converging cells the order of the errors is the order of the paper's RMSE
+    ratios wherever those differ.  Divergence here: the error exceeds that of mu = 0 (or a
+    message is not finite) within 400 iterations; the error is against the exact mean."""
+    cs, table = _golden_grid_search()
+    p = gabp_synth.paper_synthetic(128, 0.05, 0)
+    fl = oracle.build_factors(p.nx, p.ny, p.kappa, p.obs_x, p.obs_y, p.y, p.noise_var, gamma=p.gamma)
+    P, h = pw.assemble(fl)
+    exact = oracle.exact_mean(fl, p.nx)
+    nrm = np.linalg.norm(exact)
+
+    def error(c, eta):
+        msg = None
+        for _ in range(4):   # 4 x 100 iterations, stopping at the first sign of divergence
+            mean, _, msg, ok = pw.run(P, h, c, eta, 100, messages=msg)
+            with np.errstate(all="ignore"):
+                err = np.linalg.norm(mean - exact) / nrm
+            if not ok or not np.isfinite(err) or err > 1.0:
+                return None
+        return err
+
+    for eta, paper in table.items():
+        ours = [error(c, eta) for c in cs]
+        assert [e is None for e in ours] == [v is None for v in paper], (eta, ours, paper)
+        conv = [i for i, v in enumerate(paper) if v is not None]
+        for i in conv:
+            for j in conv:
+                if paper[i] < paper[j]:
+                    assert ours[i] < ours[j], (eta, cs[i], cs[j], ours[i], ours[j])
