@@ -168,7 +168,7 @@ def scaled_config(side: int, kappa: float, seed: int, n_tracks: int, *, n_unifor
                         per_track=per_track, sigma=sigma)
 
 
-def paper_synthetic(side: int, frac: float, seed: int, *, sigma_y: float = 0.1, length: float = 0.15,
+def paper_synthetic(side: int, frac: float, seed: int, *, sigma_y: float = 0.01, length: float = 0.15,
                     sigma: float = 1.1) -> Problem:
     """The synthetic setting of the grid-size / observation-density comparison (Sec. 4.1 with
     the hyperparameters of App. E): Matern prior with alpha = 2, nu = 1, lengthscale

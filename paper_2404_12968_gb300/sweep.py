@@ -5,7 +5,8 @@
 
 Data (App. E, "Synthetic data"): a ground truth drawn from the Matern prior (alpha = 2, nu = 1,
 lengthscale 0.15, marginal standard deviation 1.1 on the unit square), a fraction of the grid
-points observed with noise standard deviation 0.1, and the same prior for inference.
+points observed with noise standard deviation 0.01 (the paper does not state it; this value
+reproduces its R-INLA RMSEs), and the same prior for inference.
 
 Method, as the paper runs message passing there: a multigrid warm start with a 32 x 32 base grid
 (Sec. 3.2; every coarse level iterated to relative residual 1e-4), then synchronous GaBP on the
