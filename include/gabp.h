@@ -370,6 +370,22 @@ int gabp_pw_marginals(gabp_pw *pw, double *mean, double *var);
 int gabp_pw_residual(gabp_pw *pw, double *rel_residual);
 int gabp_pw_reset(gabp_pw *pw);
 int64_t gabp_pw_iterations(const gabp_pw *pw);
+/* Alg. 2 around the pairwise form (Sec. 3.2 "Multigrid", App. B "Early Stop"):
+ * gabp_pw_message_change: mean |m_t - m_{t-1}| over both components (a, b) of every directed
+ *   pair-factor message (pairs within the 13-point pattern); GABP_ERR_STATE before the first
+ *   iteration after a reset.
+ * gabp_pw_iterate_early_stop: iterate under the early-stopping rule: after iterations 1 and 2 of
+ *   the call the change is the reference; stop after the first t >= 3 whose change is below
+ *   tau times it (*stopped_at = t).  GABP_ERR_TIMEOUT after max_iters (>= 3), GABP_ERR_DIVERGED
+ *   if a change is not finite.
+ * gabp_pw_upscale: "Upscale Messages": fine's messages = coarse's current messages on the same
+ *   directions, node (i, j) of fine taking those of (floor(i/2), floor(j/2)) of coarse (clamped
+ *   to its grid), (0, 0) where either level lacks the pair; same precision and device;
+ *   resets fine's iteration count. */
+int gabp_pw_message_change(gabp_pw *pw, double *mean_abs_change);
+int gabp_pw_iterate_early_stop(gabp_pw *pw, int max_iters, double c, double learning_rate, double tau,
+                               int64_t *stopped_at);
+int gabp_pw_upscale(gabp_pw *fine, const gabp_pw *coarse);
 const char *gabp_pw_last_error(const gabp_pw *pw);
 void gabp_pw_destroy(gabp_pw *pw);
 

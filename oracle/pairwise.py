@@ -16,6 +16,16 @@ b with the opposite sign; this follows the integral that defines the message (th
 as for the rank-1 form), with every message in the information convention exp(-a f^2/2 + b f)
 (so the marginal is (h_i + c sum_k b_ki) / (P_ii + c sum_k a_ki)).  Damping with the paper's
 learning rate eta: m <- (1 - eta) m_old + eta m_new.  Messages start at zero.
+
+Alg. 2 in full ("Re-weighted message passing with multigrid, damping, and early stopping"):
+``run_early_stop`` iterates one level under the early-stopping rule of App. B (the reading of
+the rank-1 form: reference = mean change between iterations 1 and 2 of the run, stop after the
+first t >= 3 whose change is below tau times it), ``upscale`` initialises a finer level's
+edge values from the coarser level's ("Upscale Messages"), and ``multigrid`` runs the levels
+from the coarsest to the target grid.  Level k has spacing 2^k (kappa_k = 2^k kappa,
+gamma_k = gamma / 4^k, the multigrid reading of the rank-1 form), and an observation at a grid
+point enters level k only where its location coincides with a level-k grid point (the
+paper's rule; grid-point observations only).
 """
 from __future__ import annotations
 
@@ -62,11 +72,12 @@ def factor_message(alpha, beta, pij, c):
     return -(q * q) / alpha, -beta * q / alpha
 
 
-def run(P, h, c: float, eta: float, iters: int, messages=None):
+def run(P, h, c: float, eta: float, iters: int, messages=None, E=None):
     """``iters`` synchronous damped iterations; returns (mean, precision, (a, b), finite).
-    Mean and precision are the marginal formulas of App. A with the current messages."""
+    Mean and precision are the marginal formulas of App. A with the current messages.
+    ``E``: the result of ``edges(P)``, if already computed."""
     n = P.shape[0]
-    src, dst, pij, rev = edges(P)
+    src, dst, pij, rev = edges(P) if E is None else E
     Pd = P.diagonal()
     a = np.zeros(src.size) if messages is None else np.array(messages[0], np.float64, copy=True)
     b = np.zeros(src.size) if messages is None else np.array(messages[1], np.float64, copy=True)
@@ -89,3 +100,91 @@ def run(P, h, c: float, eta: float, iters: int, messages=None):
         prec = Pd + c * S
         mean = (h + c * T) / prec
     return mean, prec, (a, b), ok
+
+
+def message_change(new, old) -> float:
+    """mean |m_new - m_old| over both components of every directed edge."""
+    da = np.abs(np.asarray(new[0]) - np.asarray(old[0]))
+    db = np.abs(np.asarray(new[1]) - np.asarray(old[1]))
+    return float((da.sum() + db.sum()) / (da.size + db.size))
+
+
+def run_early_stop(P, h, c: float, eta: float, tau: float, max_iters: int, messages=None):
+    """Iterate one level under the early-stopping rule (App. B).  Returns (t, mean, precision,
+    messages, finite): t = the stopping iteration (None if max_iters came first or the run
+    stopped being finite)."""
+    E = edges(P)
+    msg = messages if messages is not None else (np.zeros(E[0].size), np.zeros(E[0].size))
+    _, _, m1, ok1 = run(P, h, c, eta, 1, messages=msg, E=E)
+    mean, prec, m2, ok2 = run(P, h, c, eta, 1, messages=m1, E=E)
+    if not (ok1 and ok2):
+        return None, mean, prec, m2, False
+    ref = message_change(m2, m1)
+    t, cur = 2, m2
+    while t < max_iters:
+        prev = cur
+        mean, prec, cur, ok = run(P, h, c, eta, 1, messages=prev, E=E)
+        t += 1
+        if not ok:
+            return None, mean, prec, cur, False
+        if message_change(cur, prev) < tau * ref:
+            return t, mean, prec, cur, True
+    return None, mean, prec, cur, True
+
+
+def upscale(msg_c, Pc, nxc: int, nyc: int, Pf, nxf: int, nyf: int):
+    """Edge values of the finer level from the coarser level's ("Upscale Messages"): the
+    message on the fine edge from node v towards v + o takes the value of the coarse edge
+    from v's parent (floor(i/2), floor(j/2)) towards parent + o, or 0 where that coarse edge
+    does not exist."""
+    sc, dc, _, _ = edges(Pc)
+    sf, df, _, _ = edges(Pf)
+    fy, fx = np.divmod(sf, nxf)
+    ty, tx = np.divmod(df, nxf)
+    dy, dx = ty - fy, tx - fx
+    py = np.minimum(fy // 2, nyc - 1)
+    px = np.minimum(fx // 2, nxc - 1)
+    qy, qx = py + dy, px + dx
+    inside = (qx >= 0) & (qx < nxc) & (qy >= 0) & (qy < nyc)
+    nc = nxc * nyc
+    keys = dc.astype(np.int64) * nc + sc          # edges() sorts by (dst, src)
+    want = (qy * nxc + qx).astype(np.int64) * nc + (py * nxc + px)
+    pos = np.minimum(np.searchsorted(keys, want), keys.size - 1)
+    found = inside & (keys[pos] == want)
+    a = np.where(found, np.asarray(msg_c[0])[pos], 0.0)
+    b = np.where(found, np.asarray(msg_c[1])[pos], 0.0)
+    return a, b
+
+
+def level_observations(ox, oy, y, noise_var, k: int):
+    """The grid-point observations that coincide with level-k grid points, in level-k
+    coordinates."""
+    s = 1 << k
+    ox = np.asarray(ox, np.float64)
+    oy = np.asarray(oy, np.float64)
+    if np.any(ox != np.round(ox)) or np.any(oy != np.round(oy)):
+        raise ValueError("the paper's multigrid rule is for grid-point observations")
+    sel = (np.mod(ox, s) == 0) & (np.mod(oy, s) == 0)
+    return ox[sel] / s, oy[sel] / s, np.asarray(y)[sel], np.asarray(noise_var)[sel]
+
+
+def multigrid(nx, ny, kappa, gamma, ox, oy, y, noise_var, levels: int, c: float, eta: float, tau: float,
+              max_iters: int):
+    """Alg. 2: levels - 1 coarse levels and the target, each iterated under the early-stopping
+    rule from the upscaled edge values of the level below it (zero on the coarsest).  Returns
+    (mean, precision, stop) on the target grid, stop[k] = the stopping iteration of level k."""
+    prev = None
+    stop = {}
+    mean = prec = None
+    for k in range(levels - 1, -1, -1):
+        s = 1 << k
+        nxk, nyk = -(-nx // s), -(-ny // s)
+        lox, loy, ly, lv = level_observations(ox, oy, y, noise_var, k)
+        from . import build_factors
+        fl = build_factors(nxk, nyk, kappa * s, lox, loy, ly, lv, gamma=gamma / (s * s))
+        P, h = assemble(fl)
+        msg = None if prev is None else upscale(prev[0], prev[1], prev[2], prev[3], P, nxk, nyk)
+        t, mean, prec, msg, ok = run_early_stop(P, h, c, eta, tau, max_iters, msg)
+        stop[k] = t
+        prev = (msg, P, nxk, nyk)
+    return mean, prec, stop

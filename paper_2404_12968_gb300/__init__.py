@@ -334,6 +334,24 @@ class Pairwise:
         gabp_pw_marginals(self.handle, mean, var)
         return mean, var
 
+    def message_change(self) -> float:
+        """mean |m_t - m_{t-1}| over every pair-factor message (the early-stopping quantity)."""
+        d = ctypes.c_double()
+        _pcheck(_lib.load().gabp_pw_message_change(self.handle, ctypes.byref(d)), self.handle)
+        return d.value
+
+    def iterate_early_stop(self, max_iters: int, c: float = 10.0, learning_rate: float = 0.6,
+                           tau: float = 1e-3) -> int:
+        """Iterate under the early-stopping rule (App. B); returns the stopping iteration."""
+        t = ctypes.c_int64()
+        _pcheck(_lib.load().gabp_pw_iterate_early_stop(self.handle, int(max_iters), float(c), float(learning_rate),
+                                                        float(tau), ctypes.byref(t)), self.handle)
+        return t.value
+
+    def upscale_from(self, coarse: "Pairwise") -> None:
+        """Initialise this level's messages from the coarser level's ("Upscale Messages")."""
+        _pcheck(_lib.load().gabp_pw_upscale(self.handle, coarse.handle), self.handle)
+
     def residual(self) -> float:
         return gabp_pw_residual(self.handle)
 

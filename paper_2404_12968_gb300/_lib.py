@@ -112,6 +112,13 @@ def load():
     L.gabp_pw_reset.restype = ctypes.c_int
     L.gabp_pw_iterations.argtypes = [_vp]
     L.gabp_pw_iterations.restype = ctypes.c_int64
+    L.gabp_pw_message_change.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+    L.gabp_pw_message_change.restype = ctypes.c_int
+    L.gabp_pw_iterate_early_stop.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_int64)]
+    L.gabp_pw_iterate_early_stop.restype = ctypes.c_int
+    L.gabp_pw_upscale.argtypes = [_vp, _vp]
+    L.gabp_pw_upscale.restype = ctypes.c_int
     L.gabp_pw_last_error.argtypes = [_vp]
     L.gabp_pw_last_error.restype = ctypes.c_char_p
     L.gabp_pw_destroy.argtypes = [_vp]

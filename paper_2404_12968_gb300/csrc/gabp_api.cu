@@ -1780,6 +1780,61 @@ int gabp_pw_reset(gabp_pw *w) {
 
 int64_t gabp_pw_iterations(const gabp_pw *w) { return w ? w->iters : -1; }
 
+int gabp_pw_message_change(gabp_pw *w, double *out) {
+    if (!w || !out) return w ? pfail(w, GABP_ERR_ARG, "mean_abs_change must not be NULL") : GABP_ERR_ARG;
+    if (w->iters < 1) return pfail(w, GABP_ERR_STATE, "no iteration since the last reset");
+    gabp_ctx *ctx = w->ctx;
+    DeviceGuard dg(ctx->dev);
+    CK_PW(gabp::pw_change(ctx->p, w->msg[0], w->msg[1], ctx->p.part, gabp::RES_BLOCKS, ctx->p.scal + 3, ctx->stream),
+          "pairwise message change");
+    CK_PW(cudaMemcpyAsync(ctx->hscal + 3, ctx->p.scal + 3, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+          "copy change");
+    CK_PW(cudaStreamSynchronize(ctx->stream), "pairwise change sync");
+    const int64_t e = gabp::pw_edge_count(ctx->p.nx, ctx->p.ny);
+    *out = e > 0 ? ctx->hscal[3] / (2.0 * (double)e) : 0.0;
+    return GABP_OK;
+}
+
+int gabp_pw_iterate_early_stop(gabp_pw *w, int max_iters, double c, double learning_rate, double tau,
+                               int64_t *stopped_at) {
+    if (!w) return GABP_ERR_ARG;
+    if (!(tau > 0.0) || max_iters < 3) return pfail(w, GABP_ERR_ARG, "tau > 0 and max_iters >= 3 required");
+    if (stopped_at) *stopped_at = 0;
+    int rc = gabp_pw_iterate(w, 2, c, learning_rate);
+    if (rc) return rc;
+    double ref = 0.0, d = 0.0;
+    if ((rc = gabp_pw_message_change(w, &ref))) return rc;
+    if (!std::isfinite(ref)) return pfail(w, GABP_ERR_DIVERGED, "message change is not finite");
+    for (int64_t t = 2;;) {
+        if (t >= max_iters) return pfail(w, GABP_ERR_TIMEOUT, "max_iters reached before the early-stopping rule held");
+        if ((rc = gabp_pw_iterate(w, 1, c, learning_rate))) return rc;
+        ++t;
+        if ((rc = gabp_pw_message_change(w, &d))) return rc;
+        if (!std::isfinite(d)) return pfail(w, GABP_ERR_DIVERGED, "message change is not finite");
+        if (d < tau * ref) {
+            if (stopped_at) *stopped_at = t;
+            return GABP_OK;
+        }
+    }
+}
+
+int gabp_pw_upscale(gabp_pw *fine, const gabp_pw *coarse) {
+    if (!fine || !coarse) return fine ? pfail(fine, GABP_ERR_ARG, "coarse must not be NULL") : GABP_ERR_ARG;
+    gabp_pw *w = fine;   // error reporting (CK_PW)
+    gabp_ctx *fc = fine->ctx, *cc = coarse->ctx;
+    if (fc->p.prec != cc->p.prec || fc->dev != cc->dev)
+        return pfail(fine, GABP_ERR_ARG, "levels of different precision or device");
+    DeviceGuard dg(fc->dev);
+    // the coarse level's messages are complete on its stream before the fine level reads them
+    CK_PW(cudaStreamSynchronize(cc->stream), "coarse sync");
+    CK_PW(gabp::pw_upscale(fc->p, cc->p, coarse->msg[coarse->cur], fine->msg[0], fc->stream), "pairwise upscale");
+    CK_PW(cudaStreamSynchronize(fc->stream), "pairwise upscale sync");
+    fine->cur = 0;
+    fine->iters = 0;
+    fine->c = coarse->c;   // the messages carry the coarse level's weight until the next iteration
+    return GABP_OK;
+}
+
 const char *gabp_pw_last_error(const gabp_pw *w) { return w ? w->err.c_str() : ""; }
 
 void gabp_pw_destroy(gabp_pw *w) {

@@ -77,6 +77,14 @@ cudaError_t launch_l2_iteration(const DevProblem &p, int src, double beta, cudaS
 // 12 n (a, b) pairs per buffer
 cudaError_t pw_setup(const DevProblem &p, void *Pd, void *hv, void *Pn, cudaStream_t st);
 cudaError_t pw_zero(const DevProblem &p, void *msg, cudaStream_t st);
+// Alg. 2 around the pairwise form: directed edges (pairs within the 12 offsets); the mean
+// |m_a - m_b| numerator over both message buffers (nparts partial sums in part, total in *out);
+// "Upscale Messages" from a coarse level's messages to the next finer level's
+int64_t pw_edge_count(int nx, int ny);
+cudaError_t pw_change(const DevProblem &p, const void *a, const void *b, double *part, int nparts, double *out,
+                      cudaStream_t st);
+cudaError_t pw_upscale(const DevProblem &fine, const DevProblem &coarse, const void *coarse_msg, void *fine_msg,
+                       cudaStream_t st);
 cudaError_t pw_iterate(const DevProblem &p, const void *Pd, const void *hv, const void *Pn, const void *src, void *dst,
                        double c, double eta, cudaStream_t st);
 // marginals into mean / var (FP64, var may be NULL), or (to_residual) the mean into p.mu64

@@ -19,7 +19,9 @@
 // neighbour hold (0, 0).  Node i reads its incoming messages from plane d at i - off_d, and
 // the pair factor's message back to itself from plane opp(d) at i + off_d.  Coefficients per
 // node: P_ii, h_i and P_{i, i + off_d}.
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "gabp_device.cuh"
 #include "gabp_internal.h"
@@ -231,6 +233,90 @@ cudaError_t pw_iterate(const DevProblem &p, const void *Pd, const void *hv, cons
     else
         k_pw_iter<float><<<nblk(p.n), PW_TPB, 0, st>>>(p, (const float *)Pd, (const float *)hv, (const float *)Pn,
                                                        (const float2 *)src, (float2 *)dst, (float)c, (float)eta);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// ---- Alg. 2 around the pairwise form: early stopping and upscaling ----
+
+// Partial sums of |m_new - m_old| over both components of every stored message (slots without
+// a neighbour hold (0, 0) in both buffers and add nothing), per-thread sums in T, block sums in
+// FP64 in a fixed order; part[blockIdx.x] receives the block's sum.
+template <typename T> __global__ void k_pw_change(int64_t count, const T *a, const T *b, double *part) {
+    __shared__ double sh[PW_TPB];
+    T acc = T(0);
+    for (int64_t i = gtid(); i < count; i += (int64_t)gridDim.x * PW_TPB) acc += fabs(a[i] - b[i]);
+    sh[threadIdx.x] = (double)acc;
+    __syncthreads();
+    for (int s2 = PW_TPB / 2; s2 > 0; s2 >>= 1) {
+        if (threadIdx.x < s2) sh[threadIdx.x] += sh[threadIdx.x + s2];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_pw_sum(const double *part, int count, double *out) {
+    __shared__ double sh[PW_TPB];
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < count; q += PW_TPB) acc += part[q];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s2 = PW_TPB / 2; s2 > 0; s2 >>= 1) {
+        if (threadIdx.x < s2) sh[threadIdx.x] += sh[threadIdx.x + s2];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// "Upscale Messages": fine plane d at node v = coarse plane d at v's parent (floor(i/2),
+// floor(j/2)) when the fine node has that neighbour and the parent has it too, else (0, 0).
+template <typename T>
+__global__ void k_pw_upscale(int nxc, int nyc, int nxf, int nyf, const T2<T> *coarse, T2<T> *fine) {
+    const int64_t v = gtid();
+    const int64_t nf = (int64_t)nxf * nyf, nc = (int64_t)nxc * nyc;
+    if (v >= nf) return;
+    const int i = (int)(v / nxf), j = (int)(v - (int64_t)i * nxf);
+    const int pi = min(i / 2, nyc - 1), pj = min(j / 2, nxc - 1);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        T2<T> m;
+        m.x = T(0);
+        m.y = T(0);
+        const int ti = i + DY(d), tj = j + DX(d), ci = pi + DY(d), cj = pj + DX(d);
+        if (ti >= 0 && ti < nyf && tj >= 0 && tj < nxf && ci >= 0 && ci < nyc && cj >= 0 && cj < nxc)
+            m = coarse[(int64_t)d * nc + (int64_t)pi * nxc + pj];
+        fine[(int64_t)d * nf + v] = m;
+    }
+}
+
+}  // namespace
+
+// directed edges of the pairwise form on an nx x ny grid (pairs within the 12 offsets)
+int64_t pw_edge_count(int nx, int ny) {
+    int64_t e = 0;
+    for (int d = 0; d < ND; ++d) e += (int64_t)std::max(0, nx - std::abs(DX(d))) * std::max(0, ny - std::abs(DY(d)));
+    return e;
+}
+
+cudaError_t pw_change(const DevProblem &p, const void *a, const void *b, double *part, int nparts, double *out,
+                      cudaStream_t st) {
+    const int64_t count = 2 * (int64_t)ND * p.n;
+    if (p.prec) k_pw_change<double><<<nparts, PW_TPB, 0, st>>>(count, (const double *)a, (const double *)b, part);
+    else k_pw_change<float><<<nparts, PW_TPB, 0, st>>>(count, (const float *)a, (const float *)b, part);
+    k_pw_sum<<<1, PW_TPB, 0, st>>>(part, nparts, out);
+    return cudaGetLastError();
+}
+
+cudaError_t pw_upscale(const DevProblem &fine, const DevProblem &coarse, const void *coarse_msg, void *fine_msg,
+                       cudaStream_t st) {
+    if (fine.prec != coarse.prec) return cudaErrorInvalidValue;
+    if (fine.prec)
+        k_pw_upscale<double><<<nblk(fine.n), PW_TPB, 0, st>>>(coarse.nx, coarse.ny, fine.nx, fine.ny,
+                                                              (const double2 *)coarse_msg, (double2 *)fine_msg);
+    else
+        k_pw_upscale<float><<<nblk(fine.n), PW_TPB, 0, st>>>(coarse.nx, coarse.ny, fine.nx, fine.ny,
+                                                             (const float2 *)coarse_msg, (float2 *)fine_msg);
     return cudaGetLastError();
 }
 

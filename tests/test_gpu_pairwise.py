@@ -130,3 +130,61 @@ def test_reproduces_the_papers_grid_search_on_the_gpu(orc, prec):
                 for j in conv:
                     if paper[i] < paper[j]:
                         assert ours[i] < ours[j], (eta, cs[i], cs[j], ours[i], ours[j])
+
+
+def test_early_stop_and_message_change_match_oracle(orc):
+    from paper_2404_12968_gb300 import Pairwise
+    p = _grid_point_problem(40, 0.3, 0.1)
+    fl = oracle_factors(orc, p)
+    P, h = opw.assemble(fl)
+    t_o, mean_o, _, _, ok = opw.run_early_stop(P, h, 10.0, 0.6, 1e-2, 5000)
+    assert ok
+    _, _, m1 = opw.run(P, h, 10.0, 0.6, 5)[:3]
+    _, _, m2 = opw.run(P, h, 10.0, 0.6, 1, messages=m1)[:3]
+    with solver(p, "fp64") as s, Pairwise(s) as pw:
+        pw.iterate(6, 10.0, 0.6)
+        assert pw.message_change() == pytest.approx(opw.message_change(m2, m1), rel=1e-10)
+        pw.reset()
+        t = pw.iterate_early_stop(5000, 10.0, 0.6, 1e-2)
+        mean, _ = pw.marginals(want_var=False)
+    assert t == t_o
+    assert rel_l2(mean, mean_o) < 1e-10
+
+
+def test_upscale_matches_oracle(orc):
+    from paper_2404_12968_gb300 import Pairwise
+    pf = gabp_synth.paper_synthetic(48, 0.1, 2)
+    ox, oy, yk, vk = opw.level_observations(pf.obs_x, pf.obs_y, pf.y, pf.noise_var, 1)
+    flc = orc.build_factors(24, 24, pf.kappa * 2, ox, oy, yk, vk, gamma=pf.gamma / 4)
+    flf = orc.build_factors(48, 48, pf.kappa, pf.obs_x, pf.obs_y, pf.y, pf.noise_var, gamma=pf.gamma)
+    Pc, hc = opw.assemble(flc)
+    Pf, hf = opw.assemble(flf)
+    _, _, mc, _ = opw.run(Pc, hc, 10.0, 0.6, 30)
+    mf = opw.upscale(mc, Pc, 24, 24, Pf, 48, 48)
+    mean_o = opw.run(Pf, hf, 10.0, 0.6, 0, messages=mf)[0]
+    mean3_o = opw.run(Pf, hf, 10.0, 0.6, 3, messages=mf)[0]
+    from paper_2404_12968_gb300 import Solver
+    with Solver(nx=24, ny=24, kappa=pf.kappa * 2, obs_xy=np.stack([ox, oy], 1), y=yk, noise_var=vk,
+                gamma=pf.gamma / 4, precision="fp64") as sc, Pairwise(sc) as pwc, \
+            solver(pf, "fp64", gamma=pf.gamma) as sf, Pairwise(sf) as pwf:
+        pwc.iterate(30, 10.0, 0.6)
+        pwf.upscale_from(pwc)
+        mean, _ = pwf.marginals(want_var=False)
+        pwf.iterate(3, 10.0, 0.6)
+        mean3, _ = pwf.marginals(want_var=False)
+    assert rel_l2(mean, mean_o) < 1e-12
+    assert rel_l2(mean3, mean3_o) < 1e-11
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-4)])
+def test_papers_algorithm_matches_oracle(orc, prec, tol):
+    """Alg. 2 in full (pairwise form, c = 10, learning rate 0.6, multigrid with the paper's
+    observation rule, early stopping with tau = 1e-3) against the oracle's multigrid."""
+    from paper_2404_12968_gb300 import paper_mp
+    p = gabp_synth.paper_synthetic(64, 0.1, 3)
+    mean_o, _, stop_o = opw.multigrid(p.nx, p.ny, p.kappa, p.gamma, p.obs_x, p.obs_y, p.y, p.noise_var,
+                                      3, 10.0, 0.6, 1e-3, 10000)
+    mean, _, stop = paper_mp.solve(p, levels=3, precision=prec)
+    if prec == "fp64":
+        assert stop == stop_o
+    assert rel_l2(mean, mean_o) < tol

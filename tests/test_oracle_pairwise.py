@@ -120,3 +120,57 @@ def test_reproduces_the_papers_grid_search_on_its_synthetic_setting():
             for j in conv:
                 if paper[i] < paper[j]:
                     assert ours[i] < ours[j], (eta, cs[i], cs[j], ours[i], ours[j])
+
+
+def test_upscale_copies_the_parent_edge_in_the_same_direction():
+    # brute force over the fine edges: the coarse edge from the parent of the source towards
+    # the same offset, or 0 where the coarse level lacks it
+    fc = oracle.build_factors(3, 4, 0.3, [0.5], [1.5], [0.2], [0.1])
+    ff = oracle.build_factors(6, 7, 0.15, [1.0], [3.0], [0.2], [0.1])
+    Pc, _ = pw.assemble(fc)
+    Pf, _ = pw.assemble(ff)
+    sc, dc, _, _ = pw.edges(Pc)
+    rng = np.random.default_rng(0)
+    a_c, b_c = rng.standard_normal(sc.size), rng.standard_normal(sc.size)
+    lookup = {(int(s), int(d)): k for k, (s, d) in enumerate(zip(sc, dc))}
+    a_f, b_f = pw.upscale((a_c, b_c), Pc, 3, 4, Pf, 6, 7)
+    sf, df, _, _ = pw.edges(Pf)
+    for k, (s, d) in enumerate(zip(sf, df)):
+        (fy, fx), (ty, tx) = divmod(int(s), 6), divmod(int(d), 6)
+        py, px = min(fy // 2, 3), min(fx // 2, 2)
+        qy, qx = py + ty - fy, px + tx - fx
+        key = (py * 3 + px, qy * 3 + qx) if 0 <= qy < 4 and 0 <= qx < 3 else None
+        want = (a_c[lookup[key]], b_c[lookup[key]]) if key in lookup else (0.0, 0.0)
+        assert (a_f[k], b_f[k]) == want
+
+
+def test_early_stop_rule_matches_a_step_by_step_run():
+    fl = _grid_point_problem(24, 0.3, 0.1)
+    P, h = pw.assemble(fl)
+    t, mean, _, _, ok = pw.run_early_stop(P, h, 10.0, 0.6, 1e-2, 5000)
+    assert ok and t is not None
+    # independent loop: one iteration at a time, the rule of App. B by hand
+    msgs = [(np.zeros(pw.edges(P)[0].size),) * 2]
+    for _ in range(t):
+        msgs.append(pw.run(P, h, 10.0, 0.6, 1, messages=msgs[-1])[2])
+    change = [pw.message_change(msgs[i], msgs[i - 1]) for i in range(1, t + 1)]
+    ref = change[1]
+    first = next(i + 1 for i in range(2, t) if change[i] < 1e-2 * ref)
+    assert first == t
+    np.testing.assert_allclose(mean, pw.run(P, h, 10.0, 0.6, 0, messages=msgs[-1])[0], rtol=1e-14)
+
+
+def test_multigrid_levels_and_fixed_point():
+    p = gabp_synth.paper_synthetic(64, 0.1, 1)
+    # the paper's rule: level k sees the observations on multiples of 2^k
+    for k in (1, 2):
+        ox, oy, _, _ = pw.level_observations(p.obs_x, p.obs_y, p.y, p.noise_var, k)
+        expect = np.sum((np.mod(p.obs_x, 1 << k) == 0) & (np.mod(p.obs_y, 1 << k) == 0))
+        assert ox.size == expect and np.all(ox == np.round(ox))
+    # with a strict rule the levels converge, and the target reaches the exact mean
+    mean, _, stop = pw.multigrid(p.nx, p.ny, p.kappa, p.gamma, p.obs_x, p.obs_y, p.y, p.noise_var,
+                                 3, 10.0, 0.6, 1e-9, 20000)
+    fl = oracle.build_factors(p.nx, p.ny, p.kappa, p.obs_x, p.obs_y, p.y, p.noise_var, gamma=p.gamma)
+    exact = oracle.exact_mean(fl, p.nx)
+    assert all(t is not None for t in stop.values())
+    assert np.linalg.norm(mean - exact) / np.linalg.norm(exact) < 1e-6
