@@ -115,6 +115,11 @@ typedef struct {
                          GABP_ERR_TIMEOUT without having changed the messages; for a batch
                          the batched TMA kernel does the same and gabp_batch_iterate
                          returns GABP_ERR_TIMEOUT (its messages are then unspecified). */
+    int tile_run;     /* GABP_KERNEL_TMA: tiles per run of its schedule, 1..8 (the tile rows are cut
+                         into bands of tile_run rows and a block walks one band's tile column top
+                         to bottom, reusing two belief rows from tile to tile); 0 (default) = the
+                         length in 1..4 that balances the blocks best.  Results do not depend on
+                         it.  Other kernels ignore it; values outside 0..8: GABP_ERR_ARG. */
 } gabp_options;
 
 typedef struct {
@@ -128,6 +133,7 @@ typedef struct {
     int tile_x, tile_y;     /* tile shape in use by the fused kernel */
     double bytes_per_iter;  /* algorithmic HBM bytes of one iteration (messages read and
                                written once, plus the static observation data) */
+    int tile_run;           /* tiles per run of the TMA kernel's schedule (0 for other kernels) */
 } gabp_stats;
 
 /* Fill *opt with the defaults listed above. */

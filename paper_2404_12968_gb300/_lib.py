@@ -44,14 +44,14 @@ class gabp_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("init", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("tol", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("max_iters", ctypes.c_int), ("device", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("debug_flags", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("debug_flags", ctypes.c_int), ("tile_run", ctypes.c_int)]
 
 
 class gabp_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("last_residual", ctypes.c_double),
                 ("n", ctypes.c_int64), ("m", ctypes.c_int64), ("edges", ctypes.c_int64),
                 ("precision", ctypes.c_int), ("kernel", ctypes.c_int), ("tile_x", ctypes.c_int),
-                ("tile_y", ctypes.c_int), ("bytes_per_iter", ctypes.c_double)]
+                ("tile_y", ctypes.c_int), ("bytes_per_iter", ctypes.c_double), ("tile_run", ctypes.c_int)]
 
 
 MG_MAX_LEVELS = 16

@@ -302,6 +302,7 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     if (o.init != GABP_INIT_COLD && o.init != GABP_INIT_PAPER) return fail(c, GABP_ERR_ARG, "bad init mode");
     if (o.kernel < GABP_KERNEL_AUTO || o.kernel > GABP_KERNEL_SWEEP) return fail(c, GABP_ERR_ARG, "bad kernel");
     if (!(o.tol > 0.0) || o.check_every < 1 || o.max_iters < 1) return fail(c, GABP_ERR_ARG, "bad tol/check_every/max_iters");
+    if (o.tile_run < 0 || o.tile_run > 8) return fail(c, GABP_ERR_ARG, "tile_run must be 0..8");
     if (alpha == 4 && ((o.kernel != GABP_KERNEL_AUTO && o.kernel != GABP_KERNEL_SPLIT) || o.tile_x || o.tile_y))
         return fail(c, GABP_ERR_ARG, "the alpha = 4 prior runs the split kernels (kernel AUTO or SPLIT, no tile shape)");
     if (alpha == 4) {
@@ -528,6 +529,7 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     } else if (c->kernel == GABP_KERNEL_TMA) {
         c->shape = o.tile_x ? gabp::FusedShape{o.tile_x, o.tile_y} : gabp::FusedShape{30, 14};
         CK(gabp::make_tma_maps(p, c->shape.tx, c->shape.ty, c->maps), "tensor map encode");
+        c->maps.run = o.tile_run ? o.tile_run : gabp::tma_choose_run(p, c->shape.ty);
     } else if (p.order == 2) {
         c->shape = {0, 0};
     } else if (o.tile_x) {
@@ -809,6 +811,7 @@ int gabp_get_stats(const gabp_ctx *c, gabp_stats *s) {
     s->tile_x = c->shape.tx;
     s->tile_y = c->shape.ty;
     s->bytes_per_iter = c->bytes_per_iter;
+    s->tile_run = c->kernel == GABP_KERNEL_TMA ? c->maps.run : 0;
     return GABP_OK;
 }
 

@@ -9,10 +9,14 @@
 //   B. updates the tile's cell factors (warp w takes tile row w, lanes 0..29) and
 //      the observation factors based in the tile (one per thread), writing the damped messages
 //      to the other ping-pong buffer.
-// Two barriers per tile.  Staging: each block is persistent and walks the tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ... in row-major order (tiles in flight are spatial neighbours, so
-// halo re-reads hit L2).  One thread issues, per tile, two TMA tensor loads into an S-stage ring
-// of shared-memory buffers, completion tracked by one mbarrier per stage:
+// One block barrier per tile (beliefs are double-buffered).  Schedule: the tile rows are cut
+// into bands of `run` rows; a run is one tile column of one band, and the runs are dealt to
+// the persistent blocks round-robin in band-major order, so that all blocks sweep the grid
+// together (tiles in flight are spatial neighbours and halo re-reads hit L2) and every block
+// walks down its run tile by tile.  Inside a run the two top rows of a tile's belief window are
+// the two bottom rows of the previous tile's window: they are copied, not recomputed.  One
+// thread issues, per tile, two TMA tensor loads into an S-stage ring of shared-memory buffers,
+// completion tracked by one mbarrier per stage:
 //   * the 5 message planes over the tile plus a 2-cell halo, one 3-D box of
 //     2 x 34 floats x (TY+4) rows x 5 planes, zero-filled outside the grid;
 //   * the observation index (observations before each base cell) over a 40 x (TY+3) box whose
@@ -25,7 +29,10 @@
 // Requirements (checked on the host): FP32 messages, nx a multiple of 4.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <algorithm>
+#include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "gabp_device.cuh"
 #include "gabp_internal.h"
@@ -35,6 +42,37 @@ namespace gabp {
 namespace {
 
 constexpr int TTX = 30;   // tile width in cells: window width 32
+
+// Schedule of a single-problem launch: runs of `run` tiles (one tile column of a band of `run`
+// tile rows; the last band may be shorter), run u = band * ntx + column, dealt round-robin over
+// the G blocks; step_x = G % ntx and step_b = G / ntx advance a block to its next run.
+struct TileRuns {
+    int run, ntx, nty, step_x, step_b;
+};
+
+// A block's position on its schedule: run (cx, band), tile r of len in that run; len = 0 once
+// the block has no run left.
+struct TileWalk {
+    int cx, band, r, len;
+    __device__ __forceinline__ void start(int u, const TileRuns &tr) {
+        cx = u % tr.ntx;
+        band = u / tr.ntx;
+        r = 0;
+        len = max(0, min(tr.run, tr.nty - band * tr.run));
+    }
+    __device__ __forceinline__ void next(const TileRuns &tr) {
+        if (++r < len) return;
+        r = 0;
+        cx += tr.step_x;
+        band += tr.step_b;
+        if (cx >= tr.ntx) {
+            cx -= tr.ntx;
+            ++band;
+        }
+        len = max(0, min(tr.run, tr.nty - band * tr.run));
+    }
+    __device__ __forceinline__ int ty(const TileRuns &tr) const { return band * tr.run + r; }
+};
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -245,7 +283,8 @@ template <int TY, int S, int RW> struct TileLayout {
 template <int TY, int S, int RW, bool BATCH>
 __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, RW>::MINB)
     k_fused_tma(const __grid_constant__ CUtensorMap mplanes, const __grid_constant__ CUtensorMap moptr,
-                const __grid_constant__ DevProblem p, const __grid_constant__ TmaBatchArgs ba, int src, float beta) {
+                const __grid_constant__ DevProblem p, const __grid_constant__ TmaBatchArgs ba, const TileRuns tr,
+                int src, float beta) {
     using LY = TileLayout<TY, S, RW>;
     constexpr int RX = LY::RX, RY = LY::RY, BX = LY::BX, BY = LY::BY, OXW = LY::OXW;
     constexpr int TW = LY::TW, TNT = LY::TNT;
@@ -253,8 +292,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + LY::bar_off);
     int *flag = reinterpret_cast<int *>(smem + LY::ints_off) + 2 * LY::NI;
 
-    const int ntx1 = (p.nx + TTX - 1) / TTX;   // single problem: tiles per row
-    const int ntiles = BATCH ? *ba.nitems : ntx1 * ((p.ny + TY - 1) / TY);
+    const int ntiles = BATCH ? *ba.nitems : 0;   // BATCH: work items
     const int G = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float2 beta2 = f2(beta, beta);
@@ -266,11 +304,11 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         tile = it.y;
     };
 
-    // single problem (thread 0): the tile's two tensor loads
-    auto issue = [&](int stage, int item) {
+    // single problem (thread 0): the two tensor loads of tile (cx, cy)
+    auto issue = [&](int stage, int cx, int cy) {
         unsigned char *base = smem + stage * LY::stage;
         const uint32_t bar = smem_addr(&bars[stage]);
-        const int x0 = (item % ntx1) * TTX, y0 = (item / ntx1) * TY;
+        const int x0 = cx * TTX, y0 = cy * TY;
         mbar_expect_tx(bar, LY::plane_bytes + LY::optr_bytes);
         tma_load_3d(smem_addr(base), &mplanes, 2 * (x0 - 2), y0 - 2, 0, bar);
         tma_load_2d(smem_addr(base + a128(LY::plane_bytes)), &moptr, (x0 - 2) & ~3, y0 - 2, bar);
@@ -357,32 +395,36 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         __syncthreads();
         if (*flag) return;
     }
-    for (int s = 0; s < S; ++s) {
-        const int t = blockIdx.x + s * G;
-        if (t >= ntiles) break;
-        if constexpr (BATCH) fill(s, t);
-        else if (tid == 0) issue(s, t);
+    TileWalk wk{0, 0, 0, 0};   // single problem: this block's tile
+    if constexpr (BATCH) {
+        for (int s = 0; s < S; ++s) {
+            const int t = blockIdx.x + s * G;
+            if (t >= ntiles) break;
+            fill(s, t);
+        }
+    } else {
+        wk.start(blockIdx.x, tr);
+        if (tid == 0) {
+            TileWalk w = wk;
+            for (int s = 0; s < S && w.len > 0; ++s, w.next(tr)) issue(s, w.cx, w.ty(tr));
+        }
     }
 
-    // tile coordinates advance by G tiles per step without a division
-    const int step_x = G % ntx1, step_y = G / ntx1;
-    int tcx = (int)blockIdx.x % ntx1, tcy = (int)blockIdx.x / ntx1;
     int it = 0;
     bool failed = false;
     for (;; ++it) {
-        if (it > 0) {
-            tcx += step_x;
-            tcy += step_y;
-            if (tcx >= ntx1) {
-                tcx -= ntx1;
-                ++tcy;
-            }
-        }
-        const int tile = blockIdx.x + it * G;
-        if (tile >= ntiles) break;
         // the tile's problem: the kernel parameter, or (BATCH) the table entry of its problem
-        int prob = 0, t = tile;
-        if constexpr (BATCH) locate(tile, prob, t);
+        int prob = 0, t = 0;
+        if constexpr (BATCH) {
+            const int tile = blockIdx.x + it * G;
+            if (tile >= ntiles) break;
+            locate(tile, prob, t);
+        } else {
+            if (it > 0) wk.next(tr);
+            if (wk.len == 0) break;
+        }
+        // inside a run: window rows 0 and 1 are rows TY and TY + 1 of the previous tile's window
+        const bool carry = !BATCH && wk.r > 0;
         const DevProblem &cur = BATCH ? ba.table[prob] : p;
         const int nx = cur.nx, ny = cur.ny;
         const int64_t n = cur.n, m = cur.m;
@@ -396,18 +438,20 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         // barrier after phase A stops the whole block
         const bool ok = mbar_wait(smem_addr(&bars[stage]), (uint32_t)((it / S) & 1));
         Belief2 *sb = reinterpret_cast<Belief2 *>(smem + LY::bel_off + (it & 1) * LY::bel_bytes);
+        const Belief2 *sbp = reinterpret_cast<const Belief2 *>(smem + LY::bel_off + ((it & 1) ^ 1) * LY::bel_bytes);
         int *rstart = reinterpret_cast<int *>(smem + LY::ints_off) + (it & 1) * LY::NI;   // [TY]
         int *rpre = rstart + TY;                                                          // [TY + 1]
 
-        const int x0 = (BATCH ? t % ((nx + TTX - 1) / TTX) : tcx) * TTX;
-        const int y0 = (BATCH ? t / ((nx + TTX - 1) / TTX) : tcy) * TY;
+        const int x0 = (BATCH ? t % ((nx + TTX - 1) / TTX) : wk.cx) * TTX;
+        const int y0 = (BATCH ? t / ((nx + TTX - 1) / TTX) : wk.ty(tr)) * TY;
         const int xs = (x0 - 2) & ~3;
         const float2 *sm = reinterpret_cast<const float2 *>(smem + stage * LY::stage);   // [5][RY][RX]
         const int *W = reinterpret_cast<const int *>(smem + stage * LY::stage + a128(LY::plane_bytes));
         auto wptr = [&](int x, int y) { return W[(y - y0 + 2) * OXW + (x - xs)]; };
 
-        // ---- A: observation ranges of the tile's rows (last warp), beliefs of the window ----
-        if (ok && m > 0 && warp == TW - 1) {
+        // ---- A: observation ranges of the tile's rows (last warp, or the first when it only
+        // copies its row), beliefs of the window ----
+        if (ok && m > 0 && warp == (carry ? 0 : TW - 1)) {
             int st = 0, cnt = 0;
             const int gy = y0 + lane;
             if (lane < TY && gy < ny) {
@@ -430,7 +474,9 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         for (int ly = warp; ly < BY; ly += TW) {
             const int gx = x0 - 1 + lane, gy = y0 - 1 + ly;
             Belief2 b;
-            if (ok && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+            if (carry && ly < 2) {
+                b = sbp[(ly + TY) * BX + lane];
+            } else if (ok && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
                 const int rx = lane + 1, ry = ly + 1;
                 // observation ranges of the node: base row gy (corners 1, 0) and base row gy-1
                 // (corners 3, 2); the first message of each range is loaded before the prior
@@ -484,11 +530,19 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         }
         // every thread has finished tile it-1: refill its stage with tile it-1+S
         if (it > 0) {
-            const int t2 = blockIdx.x + (it - 1 + S) * G;
-            if (t2 < ntiles) {
-                if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if constexpr (BATCH) fill((it - 1) % S, t2);
-                else if (tid == 0) issue((it - 1) % S, t2);
+            if constexpr (BATCH) {
+                const int t2 = blockIdx.x + (it - 1 + S) * G;
+                if (t2 < ntiles) {
+                    if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    fill((it - 1) % S, t2);
+                }
+            } else if (tid == 0) {
+                TileWalk w = wk;
+                for (int j = 1; j < S; ++j) w.next(tr);
+                if (w.len > 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue((it - 1) % S, w.cx, w.ty(tr));
+                }
             }
         }
 
@@ -555,9 +609,14 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         // drain this block's outstanding copies (bounded): the prologue issued tiles 0 .. S-1 and
         // the barrier of tile i >= 1 tile i-1+S, so tiles it .. jmax may be in flight
         const int jmax = it == 0 ? S - 1 : it + S - 2;
+        TileWalk w = wk;
         for (int j = it; j <= jmax; ++j) {
-            const int t = blockIdx.x + j * G;
-            if (t >= ntiles) break;
+            if constexpr (BATCH) {
+                if (blockIdx.x + j * G >= ntiles) break;
+            } else {
+                if (w.len == 0) break;
+                w.next(tr);
+            }
             mbar_wait(smem_addr(&bars[j % S]), (uint32_t)((j / S) & 1));
         }
     }
@@ -594,13 +653,20 @@ cudaError_t launch_cfg(const DevProblem &p, const TmaMaps &maps, int src, double
     // the tensor maps' boxes must have been encoded for this tile height (the smem layout and
     // the expected transaction bytes depend on it)
     if (maps.tx != TTX || maps.ty != TY) return cudaErrorInvalidValue;
+    if (maps.run < 1) return cudaErrorInvalidValue;
     int grid = 0;
     cudaError_t e = persistent_grid<TY, S, RW, false>(grid);
     if (e != cudaSuccess) return e;
-    const int ntiles = ((p.nx + TTX - 1) / TTX) * ((p.ny + TY - 1) / TY);
-    if (ntiles < grid) grid = ntiles;
+    TileRuns tr;
+    tr.run = maps.run;
+    tr.ntx = (p.nx + TTX - 1) / TTX;
+    tr.nty = (p.ny + TY - 1) / TY;
+    const int64_t runs = (int64_t)tr.ntx * ((tr.nty + tr.run - 1) / tr.run);
+    if (runs < grid) grid = (int)runs;
+    tr.step_x = grid % tr.ntx;
+    tr.step_b = grid / tr.ntx;
     const TmaBatchArgs none{};
-    k_fused_tma<TY, S, RW, false><<<grid, LY::TNT, LY::bytes, st>>>(maps.planes[src], maps.optr, p, none, src,
+    k_fused_tma<TY, S, RW, false><<<grid, LY::TNT, LY::bytes, st>>>(maps.planes[src], maps.optr, p, none, tr, src,
                                                                      (float)beta);
     return cudaGetLastError();
 }
@@ -655,8 +721,41 @@ cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps, in
     }
     maps.tx = tx;
     maps.ty = ty;
+    maps.run = 1;
     maps.valid = true;
     return cudaSuccess;
+}
+
+namespace {
+// Run length of the single-problem schedule on grid x ty-row tiles: among 1..4 the one whose
+// busiest block has the fewest tiles (ties: the longer run, which recomputes fewer belief rows).
+template <int TY> int choose_run(int nx, int ny) {
+    int grid = 0;
+    if (persistent_grid<TY, 2, 1, false>(grid) != cudaSuccess || grid < 1) return 1;
+    const int ntx = (nx + TTX - 1) / TTX, nty = (ny + TY - 1) / TY;
+    int best = 1;
+    int64_t best_load = INT64_MAX;
+    std::vector<int64_t> load;
+    for (int run = 1; run <= 4; ++run) {
+        const int64_t nb = (nty + run - 1) / run, runs = (int64_t)ntx * nb;
+        const int64_t g = runs < grid ? runs : grid;
+        load.assign((size_t)g, 0);
+        for (int64_t u = 0; u < runs; ++u) load[(size_t)(u % g)] += std::min<int64_t>(run, nty - (u / ntx) * run);
+        const int64_t worst = *std::max_element(load.begin(), load.end());
+        if (worst <= best_load) {
+            best_load = worst;
+            best = run;
+        }
+    }
+    return best;
+}
+}  // namespace
+
+int tma_choose_run(const DevProblem &p, int ty) {
+    if (ty == 14) return choose_run<14>(p.nx, p.ny);
+    if (ty == 22) return choose_run<22>(p.nx, p.ny);
+    if (ty == 30) return choose_run<30>(p.nx, p.ny);
+    return 1;
 }
 
 template <int TY>
@@ -669,7 +768,8 @@ cudaError_t launch_batch_cfg(const TmaBatchArgs &ba, const DevProblem &first, in
     if (max_tiles < grid) grid = max_tiles;
     CUtensorMap unused;
     std::memset(&unused, 0, sizeof unused);
-    k_fused_tma<TY, 2, 1, true><<<grid, LY::TNT, LY::bytes, st>>>(unused, unused, first, ba, src, (float)beta);
+    const TileRuns none{1, 1, 1, 0, 0};
+    k_fused_tma<TY, 2, 1, true><<<grid, LY::TNT, LY::bytes, st>>>(unused, unused, first, ba, none, src, (float)beta);
     return cudaGetLastError();
 }
 

@@ -138,6 +138,7 @@ struct TmaMaps {
     CUtensorMap planes[2];   // message planes of buffer 0 / 1
     CUtensorMap optr;        // observations-by-base-cell index
     int tx = 0, ty = 0;
+    int run = 1;             // tiles per run of the single-problem schedule (1..8)
     bool valid = false;
 };
 // Batched TMA iteration: the work items are the tiles of the active problems, item k being
@@ -165,6 +166,9 @@ bool tma_problem_supported(const DevProblem &p);
 constexpr int TMA_MAP_PLANES = 1, TMA_MAP_OPTR = 2;
 cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps, int parts = TMA_MAP_PLANES | TMA_MAP_OPTR);
 size_t tma_smem_bytes(int tx, int ty);
+// Tiles per run for a problem on 30 x ty tiles: the length in 1..4 that balances the
+// persistent blocks best (longest on ties).
+int tma_choose_run(const DevProblem &p, int ty);
 cudaError_t launch_tma_iteration(const DevProblem &p, const TmaMaps &maps, int src, double beta,
                                  cudaStream_t st);
 

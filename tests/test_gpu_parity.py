@@ -115,16 +115,39 @@ def test_split_and_fused_bit_identical(prec, shape):
                                 n_uniform=max(nx * ny // 20, 2) if obs else 0, sigma=(0.02, 0.1))
     variants = [(2, (0, 0)), (1, (32, 8)), (1, (64, 16)), (1, (128, 8)), (1, (32, 32))]
     if prec == "fp32" and nx % 4 == 0:
-        variants += [(3, (30, 14)), (3, (30, 22)), (3, (30, 30))]
+        # TMA tiles, each with runs of 1 (no belief rows reused) and longer runs (ragged last band)
+        variants += [(3, (30, 14), 1), (3, (30, 14), 2), (3, (30, 14), 3), (3, (30, 14), 8), (3, (30, 22), 1),
+                     (3, (30, 22), 4), (3, (30, 30), 1), (3, (30, 30), 5)]
     if prec == "fp32":
         variants += [(4, (30, 16)), (4, (30, 32)), (4, (30, 64)), (4, (30, 128))]
     bufs = []
-    for kernel, tile in variants:
-        with solver(p, prec, kernel=kernel, tile_x=tile[0], tile_y=tile[1]) as s:
+    for kernel, tile, *run in variants:
+        with solver(p, prec, kernel=kernel, tile_x=tile[0], tile_y=tile[1], tile_run=run[0] if run else 0) as s:
             s.iterate(41, 0.3)        # odd: exercises the ping-pong parity and the graph chunking
             bufs.append(s.get_messages())
     for b in bufs[1:]:
         assert np.array_equal(b, bufs[0])
+
+
+def test_tma_tile_runs():
+    """The TMA schedule's run length: chosen in 1..4 by default, settable in 1..8, reported by the
+    stats, refused outside 0..8; every length gives the bits of runs of 1 at a size with
+    thousands of tiles."""
+    p = gabp_synth.make_problem(1024, 700, 0.05, 3, n_tracks=8, per_track=1024, n_uniform=20000)
+    bufs = []
+    for run in (0, 1, 4, 7):
+        with solver(p, "fp32", kernel=3, tile_run=run) as s:
+            st = s.stats()
+            assert 1 <= st["tile_run"] <= (4 if run == 0 else run) and (run == 0 or st["tile_run"] == run)
+            s.iterate(25, 0.3)
+            bufs.append(s.get_messages())
+    for b in bufs[1:]:
+        assert np.array_equal(b, bufs[0])
+    from paper_2404_12968_gb300 import GabpError
+    with solver(p, "fp32", kernel=2) as s:
+        assert s.stats()["tile_run"] == 0
+    with pytest.raises(GabpError):
+        solver(p, "fp32", kernel=3, tile_run=9)
 
 
 def test_deterministic_repeat():
