@@ -190,7 +190,8 @@ def own_arm(args):
 
     p = make_problem(rank, args.size)
     stream = torch.cuda.current_stream(dev)
-    s = Solver(p, precision="fp32", stream=stream.cuda_stream, device=local, kernel=args.kernel)
+    s = Solver(p, precision="fp32", stream=stream.cuda_stream, device=local, kernel=args.kernel,
+               tile_run=args.tile_run)
     st = s.stats()
     n = p.n
     mean_dev = torch.empty(n, dtype=torch.float64, device=dev)
@@ -276,7 +277,7 @@ def own_arm(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.size == 4096 else f"profiling_{args.size}", "nx": p.nx, "ny": p.ny, "kappa": p.kappa, "m": p.m,
                    "iters_per_step": ITERS_PER_STEP, "damping": DAMPING, "kernel": KERNEL_NAMES[st["kernel"]],
-                   "tile": [st["tile_x"], st["tile_y"]], "parallelism": f"replicas{world}",
+                   "tile": [st["tile_x"], st["tile_y"]], "tile_run": st["tile_run"], "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (message planes 1.3 GB ping-pong)"},
         "hbm_gbs": achieved, "rel_residual_last_step": residuals[-1],
         "clocks": clocks,
@@ -455,6 +456,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--size", type=int, default=4096, help="grid side; 4096 is the benchmark workload")
     ap.add_argument("--kernel", type=int, default=0, help="iteration kernel (gabp.h GABP_KERNEL_*); 0 = auto")
+    ap.add_argument("--tile-run", type=int, default=0,
+                    help="tiles per run of the TMA kernel's schedule (1..8); 0 = the library's choice")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
