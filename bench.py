@@ -326,8 +326,9 @@ def batch_rate(device: int):
 
 def pairwise_rate(p, device: int):
     """Iteration rate of the paper's pairwise re-weighted form (13-point pair factors, App. A)
-    on the same workload: 12 incoming + 12 outgoing (a, b) pairs read, 12 written, and 14
-    coefficients per node per iteration (FP32: 344 B/node)."""
+    on the same workload.  Algorithmic bytes: every stored message read once (12 (a, b) pairs
+    per node; a node's incoming messages are other nodes' stored ones) and written once, plus
+    14 coefficients per node per iteration (FP32: 248 B/node)."""
     import torch
     from paper_2404_12968_gb300 import Pairwise, Solver
     with Solver(p, precision="fp32", device=device) as s, Pairwise(s) as pw:
@@ -336,10 +337,10 @@ def pairwise_rate(p, device: int):
         t = time.perf_counter()
         pw.iterate(50, 20.0, 0.6)
         dt = (time.perf_counter() - t) / 50
-    nbytes = 344.0 * p.n
+    nbytes = 248.0 * p.n
     peak, _ = measured_peak_gbs()
     return {"ms_per_iter": dt * 1e3, "node_updates_per_s": p.n / dt, "algorithmic_gbs": nbytes / dt / 1e9,
-            "frac_of_measured_hbm": nbytes / dt / 1e9 / peak, "bytes_per_node": 344}
+            "frac_of_measured_hbm": nbytes / dt / 1e9 / peak, "bytes_per_node": 248}
 
 
 def alpha4_rate(p, device: int):

@@ -112,28 +112,27 @@ __global__ void k_pw_zero(T *m, int64_t count) {
     if (q < count) m[q] = T(0);
 }
 
-// One synchronous iteration: node j reads its 12 incoming messages, forms the leave-one-out sums
-// by prefix and suffix sums, and writes its 12 outgoing messages (damped).
-template <typename T>
-__global__ void k_pw_iter(DevProblem p, const T *Pd, const T *hv, const T *Pn, const T2<T> *src, T2<T> *dst, T c,
-                          T eta) {
-    const int64_t v = gtid();
-    if (v >= p.n) return;
+// One node's update (INTERIOR: all 12 neighbours exist, no bounds tests).  FP32: 1 / c is
+// passed in (q = P_ij * (1 / c)) and 1 / alpha is the approximate reciprocal (as in the rank-1
+// kernels); FP64: IEEE divisions.
+template <typename T, bool INTERIOR>
+__device__ __forceinline__ void pw_node(const DevProblem &p, int64_t v, int i, int j, const T *Pd, const T *hv,
+                                        const T *Pn, const T2<T> *src, T2<T> *dst, T c, T inv_c, T eta) {
     const int nx = p.nx, ny = p.ny;
     const int64_t n = p.n;
-    const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
     bool ex[ND];
     T ina[ND], inb[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
         const int ti = i + DY(d), tj = j + DX(d);
-        ex[d] = ti >= 0 && ti < ny && tj >= 0 && tj < nx;
+        ex[d] = INTERIOR || (ti >= 0 && ti < ny && tj >= 0 && tj < nx);
         // incoming from the neighbour at -off_d: plane d there
         const int si = i - DY(d), sj = j - DX(d);
         T2<T> m;
         m.x = T(0);
         m.y = T(0);
-        if (si >= 0 && si < ny && sj >= 0 && sj < nx) m = src[(int64_t)d * n + (int64_t)si * nx + sj];
+        if (INTERIOR || (si >= 0 && si < ny && sj >= 0 && sj < nx))
+            m = src[(int64_t)d * n + v - ((int64_t)DY(d) * nx + DX(d))];
         ina[d] = m.x;
         inb[d] = m.y;
     }
@@ -154,7 +153,7 @@ __global__ void k_pw_iter(DevProblem p, const T *Pd, const T *hv, const T *Pn, c
         sa[d] = add_rn(sa[d + 1], ina[d]);
         sb[d] = add_rn(sb[d + 1], inb[d]);
     }
-    const T pjj = Pd[v], hj = hv[v];
+    const T pjj = Pd[v], hj = hv[v], cm1 = add_rn(c, T(-1)), keep = add_rn(T(1), -eta);
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
         T2<T> out;
@@ -164,18 +163,37 @@ __global__ void k_pw_iter(DevProblem p, const T *Pd, const T *hv, const T *Pn, c
             // the message of pair (j, i = j + off_d) back to f_j arrives from direction opp(d)
             const int r = OPP(d);
             const T loo_a = add_rn(pa[r], sa[r + 1]), loo_b = add_rn(pb[r], sb[r + 1]);
-            const T alpha = add_rn(add_rn(pjj, mul_rn(c, loo_a)), mul_rn(add_rn(c, T(-1)), ina[r]));
-            const T beta = add_rn(add_rn(hj, mul_rn(c, loo_b)), mul_rn(add_rn(c, T(-1)), inb[r]));
-            const T q = Pn[(int64_t)d * n + v] / c;
-            const T ra = T(1) / alpha;
+            const T alpha = add_rn(add_rn(pjj, mul_rn(c, loo_a)), mul_rn(cm1, ina[r]));
+            const T beta = add_rn(add_rn(hj, mul_rn(c, loo_b)), mul_rn(cm1, inb[r]));
+            T q, ra;
+            if constexpr (sizeof(T) == 4) {
+                q = mul_rn(Pn[(int64_t)d * n + v], inv_c);
+                ra = recip(alpha);
+            } else {
+                q = Pn[(int64_t)d * n + v] / c;
+                ra = T(1) / alpha;
+            }
             const T an = -mul_rn(mul_rn(q, q), ra), bn = -mul_rn(mul_rn(beta, q), ra);
             const T2<T> old = src[(int64_t)d * n + v];
             // (1 - eta) old + eta new, as new + (1 - eta)(old - new)
-            out.x = fma_rn(add_rn(T(1), -eta), add_rn(old.x, -an), an);
-            out.y = fma_rn(add_rn(T(1), -eta), add_rn(old.y, -bn), bn);
+            out.x = fma_rn(keep, add_rn(old.x, -an), an);
+            out.y = fma_rn(keep, add_rn(old.y, -bn), bn);
         }
-        dst[(int64_t)d * n + v] = out;
+        __stcs(reinterpret_cast<T2<T> *>(dst) + (int64_t)d * n + v, out);
     }
+}
+
+// One synchronous iteration: node j reads its 12 incoming messages, forms the leave-one-out sums
+// by prefix and suffix sums, and writes its 12 outgoing messages (damped).
+template <typename T>
+__global__ void k_pw_iter(DevProblem p, const T *Pd, const T *hv, const T *Pn, const T2<T> *src, T2<T> *dst, T c,
+                          T inv_c, T eta) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const int nx = p.nx, ny = p.ny;
+    const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
+    if (i >= 2 && i < ny - 2 && j >= 2 && j < nx - 2) pw_node<T, true>(p, v, i, j, Pd, hv, Pn, src, dst, c, inv_c, eta);
+    else pw_node<T, false>(p, v, i, j, Pd, hv, Pn, src, dst, c, inv_c, eta);
 }
 
 // marginals (mean, precision) into mean / var arrays (FP64) or the residual's mean slot
@@ -229,10 +247,11 @@ cudaError_t pw_iterate(const DevProblem &p, const void *Pd, const void *hv, cons
                        double c, double eta, cudaStream_t st) {
     if (p.prec)
         k_pw_iter<double><<<nblk(p.n), PW_TPB, 0, st>>>(p, (const double *)Pd, (const double *)hv, (const double *)Pn,
-                                                        (const double2 *)src, (double2 *)dst, c, eta);
+                                                        (const double2 *)src, (double2 *)dst, c, 1.0 / c, eta);
     else
         k_pw_iter<float><<<nblk(p.n), PW_TPB, 0, st>>>(p, (const float *)Pd, (const float *)hv, (const float *)Pn,
-                                                       (const float2 *)src, (float2 *)dst, (float)c, (float)eta);
+                                                       (const float2 *)src, (float2 *)dst, (float)c,
+                                                       (float)(1.0 / c), (float)eta);
     return cudaGetLastError();
 }
 
