@@ -113,6 +113,12 @@ __host__ __device__ constexpr int l2_dy(int d) {
     return d == 3 || d == 5 || d == 6 ? -1 : d == 4 || d == 7 || d == 8 ? 1 : d == 11 ? -2 : d == 12 ? 2 : 0;
 }
 
+// slot d of cell (i, j)'s factor has its node inside the grid
+__device__ __forceinline__ bool l2_in(const DevProblem &p, int i, int j, int d) {
+    const int y = i + l2_dy(d), x = j + l2_dx(d);
+    return x >= 0 && x < p.nx && y >= 0 && y < p.ny;
+}
+
 // coefficient of slot d of cell (i, j)'s factor; 0 if the slot's node is outside the grid
 __device__ __forceinline__ double l2_coef(const DevProblem &p, int i, int j, int d) {
     const int nx = p.nx, ny = p.ny;
@@ -126,13 +132,28 @@ __device__ __forceinline__ double l2_coef(const DevProblem &p, int i, int j, int
     return d <= 8 ? 2.0 : 1.0;
 }
 
+// The same coefficient in the kernel's precision.  FP32: from the float tables rounded once on
+// the host (the value of l2_coef rounded to float), so the FP32 kernels hold no FP64
+// instruction; INTERIOR: every slot's node exists and every degree is 4.
+template <typename T, bool INTERIOR>
+__device__ __forceinline__ T l2_coef_t(const DevProblem &p, int i, int j, int d) {
+    if constexpr (sizeof(T) == 8) {
+        return l2_coef(p, i, j, d);
+    } else {
+        if (d >= 9) return INTERIOR ? 1.f : (l2_in(p, i, j, d) ? 1.f : 0.f);
+        if (d >= 5) return INTERIOR ? 2.f : (l2_in(p, i, j, d) ? 2.f : 0.f);
+        if (INTERIOR) return d == 0 ? p.l2c_f[4] : p.l2n_f[24];
+        if (!l2_in(p, i, j, d)) return 0.f;
+        const int dc = grid_degree(i, j, p.nx, p.ny);
+        if (d == 0) return p.l2c_f[dc];
+        return p.l2n_f[5 * dc + grid_degree(i + l2_dy(d), j + l2_dx(d), p.nx, p.ny)];
+    }
+}
+
 // beliefs of order-2 contexts: node v receives slot d of the factor of cell v - offset(d),
 // summed in slot order, then the observation messages as for order 1
-template <typename T> __global__ void k_beliefs_l2(DevProblem p, int src) {
-    const int64_t v = gtid();
-    if (v >= p.n) return;
+template <typename T, bool INTERIOR> __device__ __forceinline__ void beliefs_l2(const DevProblem &p, int64_t v, int i, int j, int src) {
     const int nx = p.nx, ny = p.ny;
-    const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
     const T2<T> *P = (const T2<T> *)p.P[src];
     const T *O = (const T *)p.O[src];
     const int64_t n = p.n;
@@ -141,8 +162,8 @@ template <typename T> __global__ void k_beliefs_l2(DevProblem p, int src) {
 #pragma unroll
     for (int d = 1; d < L2_SLOTS; ++d) {
         const int ci = i - l2_dy(d), cj = j - l2_dx(d);
-        if (ci >= 0 && ci < ny && cj >= 0 && cj < nx) {
-            q = P[d * n + (int64_t)ci * nx + cj];
+        if (INTERIOR || (ci >= 0 && ci < ny && cj >= 0 && cj < nx)) {
+            q = P[d * n + v - ((int64_t)l2_dy(d) * nx + l2_dx(d))];
             se.add(q.x);
             sl.add(q.y);
         }
@@ -159,14 +180,19 @@ template <typename T> __global__ void k_beliefs_l2(DevProblem p, int src) {
     ((BeliefStore<T> *)p.belief)[v] = b;
 }
 
-// order-2 cell factors: a = row c of L^2, var = 1/gamma, r = 0 (FP32: registers bounded for 3
-// resident blocks of 256 threads per SM, measured 3.5 % faster than the unbounded 103)
-template <typename T> __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 3 : 1)
-    k_prior_l2(DevProblem p, int src, T beta) {
-    const int64_t c = gtid();
-    if (c >= p.n) return;
+template <typename T> __global__ void k_beliefs_l2(DevProblem p, int src) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    const int nx = p.nx, ny = p.ny;
+    const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
+    if (i >= 2 && i < ny - 2 && j >= 2 && j < nx - 2) beliefs_l2<T, true>(p, v, i, j, src);
+    else beliefs_l2<T, false>(p, v, i, j, src);
+}
+
+// order-2 cell factors: a = row c of L^2, var = 1/gamma, r = 0
+template <typename T, bool INTERIOR>
+__device__ __forceinline__ void prior_l2(const DevProblem &p, int64_t c, int i, int j, int src, T beta) {
     const int nx = p.nx;
-    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
     const int64_t n = p.n;
     const T2<T> *P = (const T2<T> *)p.P[src];
     T2<T> *Q = (T2<T> *)p.P[src ^ 1];
@@ -174,9 +200,9 @@ template <typename T> __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 3 
     T2<T> own[L2_SLOTS];
 #pragma unroll
     for (int d = 0; d < L2_SLOTS; ++d) {
-        a[d] = (T)l2_coef(p, i, j, d);
+        a[d] = l2_coef_t<T, INTERIOR>(p, i, j, d);
         own[d] = P[d * n + c];
-        if (a[d] != T(0)) {
+        if (INTERIOR || a[d] != T(0)) {
             cavity(load_belief<T>(p, c + (int64_t)l2_dy(d) * nx + l2_dx(d)), own[d].x, own[d].y, eta[d], lam[d]);
         } else {
             lam[d] = T(1);
@@ -188,7 +214,7 @@ template <typename T> __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 3 
 #pragma unroll
     for (int d = 0; d < L2_SLOTS; ++d) {
         T2<T> out;
-        if (a[d] != T(0)) {
+        if (INTERIOR || a[d] != T(0)) {
             out.x = damp(own[d].x, E[d], beta);
             out.y = damp(own[d].y, L[d], beta);
         } else {
@@ -197,6 +223,18 @@ template <typename T> __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 3 
         }
         Q[d * n + c] = out;
     }
+}
+
+// (FP32: registers bounded for 3 resident blocks of 256 threads per SM, measured 3.5 % faster
+// than the unbounded 103)
+template <typename T> __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 3 : 1)
+    k_prior_l2(DevProblem p, int src, T beta) {
+    const int64_t c = gtid();
+    if (c >= p.n) return;
+    const int nx = p.nx, ny = p.ny;
+    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    if (i >= 2 && i < ny - 2 && j >= 2 && j < nx - 2) prior_l2<T, true>(p, c, i, j, src, beta);
+    else prior_l2<T, false>(p, c, i, j, src, beta);
 }
 
 // cold / paper initialisation of the 13 planes (as k_init_prior)
