@@ -849,7 +849,7 @@ struct gabp_batch {
     int *d_prefix = nullptr;     // sweep: count + 1 strip offsets
     int *d_active = nullptr;     // sweep: count active flags
     int *h_active = nullptr;     // pinned: count active flags
-    int *d_items = nullptr;      // TMA: [nitems, pad, (problem, tile) x all_tiles]
+    int *d_items = nullptr;      // TMA: [nitems, pad x 3, (problem, column, row, carry) x all_tiles]
     int *h_items = nullptr;      // pinned mirror
     int *d_err = nullptr;        // TMA: a bounded wait in the batched kernel gave up
     gabp::TmaMapsGlobal *d_maps = nullptr;   // TMA: the problems' tensor maps
@@ -911,7 +911,7 @@ cudaError_t batch_launch(gabp_batch *b, int src, double beta, cudaStream_t st) {
         ba.maps = b->d_maps;
         ba.table = b->d_table;
         ba.nitems = b->d_items;
-        ba.items = reinterpret_cast<const int2 *>(b->d_items + 2);
+        ba.items = reinterpret_cast<const int4 *>(b->d_items + 4);
         ba.err = b->d_err;
         ba.debug_stall = (b->opt.debug_flags & 1) ? 1 : 0;
         // the grid does not depend on the active set, so captured graphs stay valid when it changes
@@ -923,21 +923,59 @@ cudaError_t batch_launch(gabp_batch *b, int src, double beta, cudaStream_t st) {
 
 // Upload the active set (h_active[0 .. count)): flags for the sweep kernel; for the TMA kernel
 // the (problem, tile) work items of the active problems.
+// Work items of the active problems for the batched TMA kernel.  The tiles of every problem
+// form runs of up to BATCH_RUN tiles down a tile column (bands of BATCH_RUN tile rows,
+// band-major, problems in order); block b of the G blocks takes items b, b + G, ..., and each
+// block, when its run is used up, takes the next run from the queue, so that most items sit
+// directly below the same block's previous item (flag w = 1: two belief rows carry over).
+// When the queue is empty a block takes the last tile of the longest remaining run.
+constexpr int BATCH_RUN = 4;
 int batch_upload_active(gabp_batch *b) {
     const int count = (int)b->inst.size();
     if (b->kernel == GABP_KERNEL_TMA) {
-        int k = 0;
-        for (int i = 0; i < count; ++i)
-            if (b->h_active[i]) {
-                const int t = tma_tiles(b->inst[i]->p, b->H);
-                for (int j = 0; j < t; ++j, ++k) {
-                    b->h_items[2 + 2 * k] = i;
-                    b->h_items[3 + 2 * k] = j;
-                }
+        const int G = gabp::tma_batch_grid(b->H, b->all_tiles);
+        if (G < 1) return bfail(b, GABP_ERR_CUDA, "batched TMA kernel grid");
+        struct Run {
+            int prob, cx, cy, left;   // next tile (cx, cy), tiles left
+        };
+        std::vector<Run> runs;
+        int64_t total = 0;
+        for (int i = 0; i < count; ++i) {
+            if (!b->h_active[i]) continue;
+            const int ntx = (b->inst[i]->p.nx + 29) / 30, nty = (b->inst[i]->p.ny + b->H - 1) / b->H;
+            for (int band = 0; band * BATCH_RUN < nty; ++band)
+                for (int cx = 0; cx < ntx; ++cx)
+                    runs.push_back({i, cx, band * BATCH_RUN, std::min(BATCH_RUN, nty - band * BATCH_RUN)});
+            total += (int64_t)ntx * nty;
+        }
+        int4 *items = reinterpret_cast<int4 *>(b->h_items + 4);
+        std::vector<Run> lane((size_t)G, Run{-1, 0, 0, 0});
+        size_t next = 0;
+        for (int64_t k = 0; k < total; ++k) {
+            Run &r = lane[(size_t)(k % G)];
+            int4 it;
+            if (r.left == 0 && next < runs.size()) r = runs[next++];
+            if (r.left > 0) {
+                it = make_int4(r.prob, r.cx, r.cy, 0);
+                ++r.cy;
+                --r.left;
+            } else {   // queue empty: the last tile of the longest remaining run
+                size_t best = 0;
+                for (size_t q = 1; q < lane.size(); ++q)
+                    if (lane[q].left > lane[best].left) best = q;
+                Run &o = lane[best];
+                it = make_int4(o.prob, o.cx, o.cy + o.left - 1, 0);
+                --o.left;
             }
-        b->h_items[0] = k;
-        b->h_items[1] = 0;
-        BK(cudaMemcpyAsync(b->d_items, b->h_items, sizeof(int) * (2 + 2 * (size_t)k), cudaMemcpyHostToDevice,
+            if (k >= G) {
+                const int4 &pv = items[k - G];
+                it.w = pv.x == it.x && pv.y == it.y && pv.z + 1 == it.z ? 1 : 0;
+            }
+            items[k] = it;
+        }
+        b->h_items[0] = (int)total;
+        b->h_items[1] = b->h_items[2] = b->h_items[3] = 0;
+        BK(cudaMemcpyAsync(b->d_items, b->h_items, sizeof(int) * (4 + 4 * (size_t)total), cudaMemcpyHostToDevice,
                            b->stream),
            "upload work items");
         return GABP_OK;
@@ -1261,8 +1299,8 @@ int batch_create_impl(gabp_batch *b, int count, const gabp_problem *problems) {
     int max_tiles = 0;
     for (int i = 0; i < count; ++i) max_tiles += tma_tiles(b->inst[i]->p, TMA_MIN_TY);
     BK(cudaMalloc((void **)&b->d_maps, sizeof(gabp::TmaMapsGlobal) * count), "alloc tensor maps");
-    BK(cudaMalloc((void **)&b->d_items, sizeof(int) * (2 + 2 * (size_t)max_tiles)), "alloc work items");
-    BK(cudaMallocHost((void **)&b->h_items, sizeof(int) * (2 + 2 * (size_t)max_tiles)), "alloc pinned items");
+    BK(cudaMalloc((void **)&b->d_items, sizeof(int) * (4 + 4 * (size_t)max_tiles)), "alloc work items");
+    BK(cudaMallocHost((void **)&b->h_items, sizeof(int) * (4 + 4 * (size_t)max_tiles)), "alloc pinned items");
     BK(cudaMalloc((void **)&b->d_err, sizeof(int)), "alloc error flag");
     BK(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream), "memset");
     b->iters.assign(count, 0);

@@ -297,12 +297,8 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float2 beta2 = f2(beta, beta);
 
-    // BATCH: work item -> (problem, tile of that problem)
-    auto locate = [&](int item, int &prob, int &tile) {
-        const int2 it = ba.items[item];
-        prob = it.x;
-        tile = it.y;
-    };
+    // BATCH: work item -> (problem, tile column, tile row, carry flag)
+    auto locate = [&](int item) { return ba.items[item]; };
 
     // single problem (thread 0): the two tensor loads of tile (cx, cy)
     auto issue = [&](int stage, int cx, int cy) {
@@ -323,12 +319,11 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
     auto fill = [&](int stage, int item) {
         unsigned char *base = smem + stage * LY::stage;
         const uint32_t bar = smem_addr(&bars[stage]);
-        int prob, tile;
-        locate(item, prob, tile);
+        const int4 w = locate(item);
+        const int prob = w.x;
         const DevProblem &q = ba.table[prob];
         const int qnx = q.nx, qny = q.ny;
-        const int qtx = (qnx + TTX - 1) / TTX;
-        const int x0 = (tile % qtx) * TTX, y0 = (tile / qtx) * TY;
+        const int x0 = w.y * TTX, y0 = w.z * TY;
         const bool tma_planes = qnx % 2 == 0, tma_optr = qnx % 4 == 0;
         if (tid == 0 && tma_planes) {
             mbar_expect_tx_only(bar, LY::plane_bytes + (tma_optr ? LY::optr_bytes : 0u));
@@ -414,18 +409,18 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
     bool failed = false;
     for (;; ++it) {
         // the tile's problem: the kernel parameter, or (BATCH) the table entry of its problem
-        int prob = 0, t = 0;
+        int4 w = make_int4(0, 0, 0, 0);   // BATCH: the work item
         if constexpr (BATCH) {
             const int tile = blockIdx.x + it * G;
             if (tile >= ntiles) break;
-            locate(tile, prob, t);
+            w = locate(tile);
         } else {
             if (it > 0) wk.next(tr);
             if (wk.len == 0) break;
         }
         // inside a run: window rows 0 and 1 are rows TY and TY + 1 of the previous tile's window
-        const bool carry = !BATCH && wk.r > 0;
-        const DevProblem &cur = BATCH ? ba.table[prob] : p;
+        const bool carry = BATCH ? w.w != 0 : wk.r > 0;
+        const DevProblem &cur = BATCH ? ba.table[w.x] : p;
         const int nx = cur.nx, ny = cur.ny;
         const int64_t n = cur.n, m = cur.m;
         float2 *const Q = (float2 *)cur.P[src ^ 1];
@@ -442,8 +437,8 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         int *rstart = reinterpret_cast<int *>(smem + LY::ints_off) + (it & 1) * LY::NI;   // [TY]
         int *rpre = rstart + TY;                                                          // [TY + 1]
 
-        const int x0 = (BATCH ? t % ((nx + TTX - 1) / TTX) : wk.cx) * TTX;
-        const int y0 = (BATCH ? t / ((nx + TTX - 1) / TTX) : wk.ty(tr)) * TY;
+        const int x0 = (BATCH ? w.y : wk.cx) * TTX;
+        const int y0 = (BATCH ? w.z : wk.ty(tr)) * TY;
         const int xs = (x0 - 2) & ~3;
         const float2 *sm = reinterpret_cast<const float2 *>(smem + stage * LY::stage);   // [5][RY][RX]
         const int *W = reinterpret_cast<const int *>(smem + stage * LY::stage + a128(LY::plane_bytes));
@@ -774,6 +769,14 @@ cudaError_t launch_batch_cfg(const TmaBatchArgs &ba, const DevProblem &first, in
 }
 
 bool tma_batch_shape_supported(int ty) { return ty == 22 || ty == 30; }
+
+int tma_batch_grid(int ty, int max_tiles) {
+    int grid = 0;
+    if (ty == 22 && persistent_grid<22, 2, 1, true>(grid) != cudaSuccess) return 0;
+    if (ty == 30 && persistent_grid<30, 2, 1, true>(grid) != cudaSuccess) return 0;
+    if (ty != 22 && ty != 30) return 0;
+    return max_tiles < grid ? max_tiles : grid;
+}
 
 // Batched iteration over the 30 x ty tiles of the active problems.  `first` is any one problem
 // of the batch (it stands in for the kernel's single-problem parameters, of which batch mode

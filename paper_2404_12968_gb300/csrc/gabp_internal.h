@@ -143,9 +143,11 @@ struct TmaMaps {
     int run = 1;             // tiles per run of the single-problem schedule (1..8)
     bool valid = false;
 };
-// Batched TMA iteration: the work items are the tiles of the active problems, item k being
-// tile items[k].y of problem items[k].x (k < *nitems); every problem's tensor maps sit in a
-// global array (CUtensorMap's own alignment; zero for a problem whose rows are not 16-byte
+// Batched TMA iteration: the work items are the tiles of the active problems, item k (k <
+// *nitems) being tile column items[k].y, tile row items[k].z of problem items[k].x; items[k].w
+// = 1 when item k - G (the same block's previous item, G blocks) is the tile directly above it
+// in the same problem, so that two belief rows carry over.  Every problem's tensor maps sit in
+// a global array (CUtensorMap's own alignment; zero for a problem whose rows are not 16-byte
 // strided).  *err is raised if a bounded wait ran out.
 struct TmaMapsGlobal {
     CUtensorMap planes[2];
@@ -154,12 +156,13 @@ struct TmaMapsGlobal {
 struct TmaBatchArgs {
     const TmaMapsGlobal *maps;
     const DevProblem *table;
-    const int2 *items;
+    const int4 *items;
     const int *nitems;
     int *err;
     int debug_stall;   // test hook, as DevProblem::debug_stall
 };
 bool tma_batch_shape_supported(int ty);   // tile heights of the batched TMA kernel (22, 30)
+int tma_batch_grid(int ty, int max_tiles);  // blocks of its launch (0 on error)
 cudaError_t launch_tma_batch(const TmaBatchArgs &ba, const DevProblem &first, int ty, int max_tiles, int src,
                              double beta, cudaStream_t st);
 bool tma_shape_supported(int tx, int ty);
