@@ -4,6 +4,7 @@
 // kernel (gabp_fused.cu) computes the same messages in one pass.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "gabp_device.cuh"
@@ -22,6 +23,9 @@ template <typename T> struct __align__(4 * sizeof(T)) BeliefStore {
 __device__ __forceinline__ int64_t gtid() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }
 
 inline unsigned nblocks(int64_t count) { return (unsigned)((count + TPB - 1) / TPB); }
+// Row-wise launch over an nx x ny grid: blocks of TPB columns of one row (no division on the
+// device), rows strided by gridDim.y (at most 65535)
+inline dim3 row_grid(int nx, int ny) { return dim3((unsigned)((nx + TPB - 1) / TPB), (unsigned)std::min(ny, 65535)); }
 
 // ---- beliefs (App. A, state update): sum of every incoming message, compensated ----
 template <typename T> __global__ void k_beliefs(DevProblem p, int src) {
@@ -181,12 +185,14 @@ template <typename T, bool INTERIOR> __device__ __forceinline__ void beliefs_l2(
 }
 
 template <typename T> __global__ void k_beliefs_l2(DevProblem p, int src) {
-    const int64_t v = gtid();
-    if (v >= p.n) return;
     const int nx = p.nx, ny = p.ny;
-    const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
-    if (i >= 2 && i < ny - 2 && j >= 2 && j < nx - 2) beliefs_l2<T, true>(p, v, i, j, src);
-    else beliefs_l2<T, false>(p, v, i, j, src);
+    const int j = blockIdx.x * TPB + threadIdx.x;
+    if (j >= nx) return;
+    for (int i = blockIdx.y; i < ny; i += gridDim.y) {
+        const int64_t v = (int64_t)i * nx + j;
+        if (i >= 2 && i < ny - 2 && j >= 2 && j < nx - 2) beliefs_l2<T, true>(p, v, i, j, src);
+        else beliefs_l2<T, false>(p, v, i, j, src);
+    }
 }
 
 // order-2 cell factors: a = row c of L^2, var = 1/gamma, r = 0
@@ -229,12 +235,14 @@ __device__ __forceinline__ void prior_l2(const DevProblem &p, int64_t c, int i, 
 // than the unbounded 103)
 template <typename T> __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 3 : 1)
     k_prior_l2(DevProblem p, int src, T beta) {
-    const int64_t c = gtid();
-    if (c >= p.n) return;
     const int nx = p.nx, ny = p.ny;
-    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
-    if (i >= 2 && i < ny - 2 && j >= 2 && j < nx - 2) prior_l2<T, true>(p, c, i, j, src, beta);
-    else prior_l2<T, false>(p, c, i, j, src, beta);
+    const int j = blockIdx.x * TPB + threadIdx.x;
+    if (j >= nx) return;
+    for (int i = blockIdx.y; i < ny; i += gridDim.y) {
+        const int64_t c = (int64_t)i * nx + j;
+        if (i >= 2 && i < ny - 2 && j >= 2 && j < nx - 2) prior_l2<T, true>(p, c, i, j, src, beta);
+        else prior_l2<T, false>(p, c, i, j, src, beta);
+    }
 }
 
 // cold / paper initialisation of the 13 planes (as k_init_prior)
@@ -799,12 +807,12 @@ cudaError_t launch_split_iteration(const DevProblem &p, int src, double beta, cu
 cudaError_t launch_l2_iteration(const DevProblem &p, int src, double beta, cudaStream_t st) {
     if (p.order != 2) return cudaErrorInvalidValue;
     if (p.prec) {
-        k_beliefs_l2<double><<<nblocks(p.n), TPB, 0, st>>>(p, src);
-        k_prior_l2<double><<<nblocks(p.n), TPB, 0, st>>>(p, src, beta);
+        k_beliefs_l2<double><<<row_grid(p.nx, p.ny), TPB, 0, st>>>(p, src);
+        k_prior_l2<double><<<row_grid(p.nx, p.ny), TPB, 0, st>>>(p, src, beta);
         if (p.m > 0) k_obs<double><<<nblocks(p.m), TPB, 0, st>>>(p, src, beta);
     } else {
-        k_beliefs_l2<float><<<nblocks(p.n), TPB, 0, st>>>(p, src);
-        k_prior_l2<float><<<nblocks(p.n), TPB, 0, st>>>(p, src, (float)beta);
+        k_beliefs_l2<float><<<row_grid(p.nx, p.ny), TPB, 0, st>>>(p, src);
+        k_prior_l2<float><<<row_grid(p.nx, p.ny), TPB, 0, st>>>(p, src, (float)beta);
         if (p.m > 0) k_obs<float><<<nblocks(p.m), TPB, 0, st>>>(p, src, (float)beta);
     }
     return cudaGetLastError();
@@ -812,8 +820,8 @@ cudaError_t launch_l2_iteration(const DevProblem &p, int src, double beta, cudaS
 
 cudaError_t launch_beliefs(const DevProblem &p, int src, cudaStream_t st) {
     if (p.order == 2) {
-        if (p.prec) k_beliefs_l2<double><<<nblocks(p.n), TPB, 0, st>>>(p, src);
-        else k_beliefs_l2<float><<<nblocks(p.n), TPB, 0, st>>>(p, src);
+        if (p.prec) k_beliefs_l2<double><<<row_grid(p.nx, p.ny), TPB, 0, st>>>(p, src);
+        else k_beliefs_l2<float><<<row_grid(p.nx, p.ny), TPB, 0, st>>>(p, src);
         return cudaGetLastError();
     }
     if (p.prec) k_beliefs<double><<<nblocks(p.n), TPB, 0, st>>>(p, src);
