@@ -184,9 +184,11 @@ __device__ __forceinline__ void pw_node(const DevProblem &p, int64_t v, int i, i
 }
 
 // One synchronous iteration: node j reads its 12 incoming messages, forms the leave-one-out sums
-// by prefix and suffix sums, and writes its 12 outgoing messages (damped).
+// by prefix and suffix sums, and writes its 12 outgoing messages (damped).  FP32: registers
+// bounded for 6 resident blocks of 256 threads per SM; the spills land in L1 and the extra
+// loads in flight outweigh them (0.89 ms against 1.14 ms at 3 blocks, 4096^2).
 template <typename T>
-__global__ void k_pw_iter(DevProblem p, const T *Pd, const T *hv, const T *Pn, const T2<T> *src, T2<T> *dst, T c,
+__global__ void __launch_bounds__(PW_TPB, sizeof(T) == 4 ? 6 : 1) k_pw_iter(DevProblem p, const T *Pd, const T *hv, const T *Pn, const T2<T> *src, T2<T> *dst, T c,
                           T inv_c, T eta) {
     const int64_t v = gtid();
     if (v >= p.n) return;
