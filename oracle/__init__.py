@@ -76,6 +76,9 @@ def lib():
         L.orc_band_solve.argtypes = [ctypes.c_int64, ctypes.c_int64, _i64p, _i64p, _f64p, _f64p,
                                      ctypes.c_int64, _f64p]
         L.orc_band_solve.restype = ctypes.c_int
+        L.orc_iterate_factors.argtypes = [ctypes.c_int64, ctypes.c_int64, _i64p, _i64p, _f64p, _f64p, _f64p,
+                                          ctypes.c_double, ctypes.c_int64, _i64p, _f64p, _f64p, _f64p, _f64p]
+        L.orc_iterate_factors.restype = ctypes.c_int
         _LIB = L
     return _LIB
 

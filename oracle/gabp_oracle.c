@@ -157,38 +157,70 @@ static int build_node_slots(int64_t n, int64_t nf, const int64_t *ptr, const int
 }
 
 /*
- * One synchronous damped iteration: new messages from the old ones only.
- * msg_* are read, out_* written (distinct buffers).  beta = weight on the old message.
+ * New damped messages of factor f from the old messages: the cavity of each slot j = (f, x_u)
+ * is the product of every message into x_u except the one from f (App. A, variable-to-factor
+ * message), summed directly over the other slots in slot order; then the factor-to-variable
+ * messages and damping.  msg_* are read, out_* written (distinct buffers); beta = weight on
+ * the old message.
  */
+static void factor_step(int64_t f, const int64_t *ptr, const int64_t *var, const double *coef,
+                        const double *s, const double *r, double beta, const int64_t *nptr,
+                        const int64_t *nslot, const double *msg_eta, const double *msg_lam,
+                        double *out_eta, double *out_lam) {
+    double lam_c[64], eta_c[64], lam_h[64], eta_h[64];
+    int k = (int)(ptr[f + 1] - ptr[f]);
+    const int64_t j0 = ptr[f];
+    for (int u = 0; u < k; ++u) {
+        const int64_t j = j0 + u, i = var[j];
+        double lc = 0.0, ec = 0.0;
+        for (int64_t q = nptr[i]; q < nptr[i + 1]; ++q) {
+            if (nslot[q] == j) continue;
+            lc += msg_lam[nslot[q]];
+            ec += msg_eta[nslot[q]];
+        }
+        lam_c[u] = lc;
+        eta_c[u] = ec;
+    }
+    orc_factor_update(k, coef + j0, s[f], r[f], lam_c, eta_c, lam_h, eta_h);
+    for (int u = 0; u < k; ++u) {
+        out_lam[j0 + u] = beta * msg_lam[j0 + u] + (1.0 - beta) * lam_h[u];
+        out_eta[j0 + u] = beta * msg_eta[j0 + u] + (1.0 - beta) * eta_h[u];
+    }
+}
+
+/* One synchronous damped iteration: new messages of every factor from the old ones only. */
 static void one_iteration(int64_t nf, const int64_t *ptr, const int64_t *var,
                           const double *coef, const double *s, const double *r, double beta,
                           const int64_t *nptr, const int64_t *nslot,
                           const double *msg_eta, const double *msg_lam, double *out_eta,
                           double *out_lam) {
 #pragma omp parallel for schedule(static)
-    for (int64_t f = 0; f < nf; ++f) {
-        double lam_c[64], eta_c[64], lam_h[64], eta_h[64];
-        int k = (int)(ptr[f + 1] - ptr[f]);
-        const int64_t j0 = ptr[f];
-        /* cavity of slot j = (f, x_u): the product of every message into x_u except the one
-         * from f (App. A, variable-to-factor message), summed directly over the other slots */
-        for (int u = 0; u < k; ++u) {
-            const int64_t j = j0 + u, i = var[j];
-            double lc = 0.0, ec = 0.0;
-            for (int64_t q = nptr[i]; q < nptr[i + 1]; ++q) {
-                if (nslot[q] == j) continue;
-                lc += msg_lam[nslot[q]];
-                ec += msg_eta[nslot[q]];
-            }
-            lam_c[u] = lc;
-            eta_c[u] = ec;
-        }
-        orc_factor_update(k, coef + j0, s[f], r[f], lam_c, eta_c, lam_h, eta_h);
-        for (int u = 0; u < k; ++u) {
-            out_lam[j0 + u] = beta * msg_lam[j0 + u] + (1.0 - beta) * lam_h[u];
-            out_eta[j0 + u] = beta * msg_eta[j0 + u] + (1.0 - beta) * eta_h[u];
-        }
+    for (int64_t f = 0; f < nf; ++f)
+        factor_step(f, ptr, var, coef, s, r, beta, nptr, nslot, msg_eta, msg_lam, out_eta, out_lam);
+}
+
+/*
+ * One synchronous damped iteration of the factors fids[0..nsub) only (a subdomain's factors,
+ * Sec. 3.2.1 domain decomposition): the arithmetic of one_iteration, reading msg_* at the slots
+ * of the variables those factors touch and writing out_* at their own slots.
+ */
+int orc_iterate_factors(int64_t n, int64_t nf, const int64_t *ptr, const int64_t *var,
+                        const double *coef, const double *s, const double *r, double beta,
+                        int64_t nsub, const int64_t *fids, const double *msg_eta,
+                        const double *msg_lam, double *out_eta, double *out_lam) {
+    if (n < 0 || nf < 0 || nsub < 0) return ORC_ERR_ARG;
+    for (int64_t q = 0; q < nsub; ++q) {
+        const int64_t f = fids[q];
+        if (f < 0 || f >= nf || ptr[f + 1] - ptr[f] > 64 || ptr[f + 1] < ptr[f] || !(s[f] > 0.0))
+            return ORC_ERR_ARG;
     }
+    int64_t *nptr = NULL, *nslot = NULL;
+    if (build_node_slots(n, nf, ptr, var, &nptr, &nslot) != ORC_OK) return ORC_ERR_OOM;
+    for (int64_t q = 0; q < nsub; ++q)
+        factor_step(fids[q], ptr, var, coef, s, r, beta, nptr, nslot, msg_eta, msg_lam, out_eta, out_lam);
+    free(nptr);
+    free(nslot);
+    return ORC_OK;
 }
 
 /*
