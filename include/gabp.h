@@ -181,7 +181,9 @@ int gabp_iterate(gabp_ctx *ctx, int n_iters, double damping);
 
 /*
  * Marginals from the current messages (App. A, marginal extraction, c = 1):
- * mean = eta / Lambda and var = 1 / Lambda per node, written as FP64.
+ * mean = eta / Lambda and var = 1 / Lambda per node, written as FP64.  FP32 contexts form
+ * the mean from the compensated (hi + lo) beliefs as a double-float quotient (about 46
+ * significant bits, the value the residual uses); FP64 contexts divide in FP64.
  *   mean  nx*ny doubles, host or device; must not be NULL.
  *   var   nx*ny doubles, host or device; may be NULL.
  */

@@ -656,9 +656,21 @@ template <typename T> __global__ void k_marg(DevProblem p, double *mean, double 
     const int64_t v = gtid();
     if (v >= p.n) return;
     const BeliefStore<T> b = ((const BeliefStore<T> *)p.belief)[v];
-    const double L = (double)b.lhi + (double)b.llo;
-    mean[v] = ((double)b.ehi + (double)b.elo) / L;
-    if (var) var[v] = 1.0 / L;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 beliefs (hi + lo pairs): the mean as the residual forms it, a double-float
+        // quotient with one correction from the exact remainder, widened to FP64 once (no FP64
+        // division: FP64 throughput is a small fraction of FP32 here)
+        const dfl eta = {b.ehi, b.elo}, lam = {b.lhi, b.llo};
+        const float q1 = __fdiv_rn(eta.hi, lam.hi);
+        const dfl r = df_add(eta, df_neg(df_mul(lam, {q1, 0.f})));
+        const dfl q = df_fast2sum(q1, __fdiv_rn(r.hi, lam.hi));
+        mean[v] = (double)q.hi + (double)q.lo;
+        if (var) var[v] = 1.0 / ((double)b.lhi + (double)b.llo);
+    } else {
+        const double L = (double)b.lhi + (double)b.llo;
+        mean[v] = ((double)b.ehi + (double)b.elo) / L;
+        if (var) var[v] = 1.0 / L;
+    }
 }
 
 // ---- learned warm start: network inputs, training targets, decoded initial beliefs ----
