@@ -446,6 +446,8 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *pri
     }
     p.gam_hi = (float)gamma;
     p.gam_lo = (float)(gamma - (double)p.gam_hi);
+    for (int d = 0; d <= 4; ++d) p.init_c_f[d] = (float)(gamma * p.aC[d] * p.aC[d]);
+    p.init_n_f = (float)(gamma * -1.0 * -1.0);
     for (int dc = 0; dc <= 4; ++dc) {   // alpha = 4 coefficients of FP32 contexts, rounded once
         p.l2c_f[dc] = (float)(p.aC[dc] * p.aC[dc] + (double)dc);
         for (int du = 0; du <= 4; ++du) p.l2n_f[5 * dc + du] = (float)(-(p.aC[dc] + p.aC[du]));

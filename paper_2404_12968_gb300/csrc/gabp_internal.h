@@ -22,6 +22,8 @@ struct DevProblem {
     float gam_hi, gam_lo;   // gamma as a double-float pair
     float l2c_f[5];      // alpha = 4: centre coefficient (kappa^2 + d)^2 + d of a cell of degree d, as float
     float l2n_f[25];     // alpha = 4: neighbour coefficient -(aC[dc] + aC[du]) for degrees (dc, du), as float
+    float init_c_f[5];   // cold-start precision gamma aC[d]^2 of a centre slot of degree d, as float
+    float init_n_f;      // cold-start precision gamma (-1)^2 of a neighbour slot, as float
     const float2 *owdf;  // FP32 contexts: 4 * m observation weights as double-float (hi, lo) pairs
     const float2 *oysdf; // FP32 contexts: 2 * m (y, 1/sigma^2) as double-float pairs
     void *P[2];          // prior messages, ping-pong: 5 * n (eta, Lambda) pairs

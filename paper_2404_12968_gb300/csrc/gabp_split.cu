@@ -23,6 +23,19 @@ template <typename T> struct __align__(4 * sizeof(T)) BeliefStore {
 __device__ __forceinline__ int64_t gtid() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }
 
 inline unsigned nblocks(int64_t count) { return (unsigned)((count + TPB - 1) / TPB); }
+
+// Grid coordinates (row i, column j) of node v: a 32-bit division while the index fits (a 64-bit
+// division is a long instruction sequence)
+__device__ __forceinline__ void node_rc(int64_t v, int nx, int &i, int &j) {
+    if (v <= 0x7fffffff) {
+        const unsigned q = (unsigned)v / (unsigned)nx;
+        i = (int)q;
+        j = (int)((unsigned)v - q * (unsigned)nx);
+    } else {
+        i = (int)(v / nx);
+        j = (int)(v - (int64_t)i * nx);
+    }
+}
 // Row-wise launch over an nx x ny grid: blocks of TPB columns of one row (no division on the
 // device), rows strided by gridDim.y (at most 65535)
 inline dim3 row_grid(int nx, int ny) { return dim3((unsigned)((nx + TPB - 1) / TPB), (unsigned)std::min(ny, 65535)); }
@@ -32,7 +45,8 @@ template <typename T> __global__ void k_beliefs(DevProblem p, int src) {
     const int64_t v = gtid();
     if (v >= p.n) return;
     const int nx = p.nx, ny = p.ny;
-    const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
+    int i, j;
+    node_rc(v, nx, i, j);
     const T2<T> *P = (const T2<T> *)p.P[src];
     const T *O = (const T *)p.O[src];
     const int64_t n = p.n;
@@ -67,7 +81,8 @@ template <typename T> __global__ void k_prior(DevProblem p, int src, T beta) {
     const int64_t c = gtid();
     if (c >= p.n) return;
     const int nx = p.nx, ny = p.ny;
-    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    int i, j;
+    node_rc(c, nx, i, j);
     const int64_t n = p.n;
     const T2<T> *P = (const T2<T> *)p.P[src];
     T2<T> *Q = (T2<T> *)p.P[src ^ 1];
@@ -250,7 +265,8 @@ template <typename T> __global__ void k_init_prior_l2(DevProblem p, int dst, int
     const int64_t c = gtid();
     if (c >= p.n) return;
     const int nx = p.nx;
-    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    int i, j;
+    node_rc(c, nx, i, j);
     T2<T> *Q = (T2<T> *)p.P[dst];
 #pragma unroll
     for (int d = 0; d < L2_SLOTS; ++d) {
@@ -295,16 +311,19 @@ template <typename T> __global__ void k_init_prior(DevProblem p, int dst, int pa
     const int64_t c = gtid();
     if (c >= p.n) return;
     const int nx = p.nx, ny = p.ny;
-    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    int i, j;
+    node_rc(c, nx, i, j);
     const int deg = grid_degree(i, j, nx, ny);
-    const double a[5] = {p.aC[deg], j > 0 ? -1.0 : 0.0, j < nx - 1 ? -1.0 : 0.0, i > 0 ? -1.0 : 0.0,
-                         i < ny - 1 ? -1.0 : 0.0};
+    const bool has[5] = {true, j > 0, j < nx - 1, i > 0, i < ny - 1};
     T2<T> *Q = (T2<T> *)p.P[dst];
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
         T2<T> o;
         o.x = T(0);
-        o.y = a[u] == 0.0 ? T(0) : (paper ? T(1e-8) : T(p.gamma * a[u] * a[u]));
+        T cold;   // gamma a_u^2: FP32 from the host-rounded table (no FP64 instruction)
+        if constexpr (sizeof(T) == 4) cold = u == 0 ? p.init_c_f[deg] : p.init_n_f;
+        else cold = u == 0 ? p.gamma * p.aC[deg] * p.aC[deg] : p.gamma * -1.0 * -1.0;
+        o.y = !has[u] ? T(0) : (paper ? T(1e-8) : cold);
         Q[u * p.n + c] = o;
     }
 }
@@ -324,7 +343,8 @@ template <typename T> __global__ void k_init_obs(DevProblem p, int dst, int pape
 // number of factor slots touching node v (prior factors + observation corners)
 __device__ __forceinline__ int node_slots(const DevProblem &p, int64_t v) {
     const int nx = p.nx, ny = p.ny;
-    const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
+    int i, j;
+    node_rc(v, nx, i, j);
     int d = 1 + grid_degree(i, j, nx, ny);
     if (p.m > 0) {
         const int *o = p.optr;
@@ -341,7 +361,8 @@ __global__ void k_init_warm_prior(DevProblem p, int dst, const double *mu0, cons
     const int64_t c = gtid();
     if (c >= p.n) return;
     const int nx = p.nx, ny = p.ny;
-    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    int i, j;
+    node_rc(c, nx, i, j);
     const bool exists[5] = {true, j > 0, j < nx - 1, i > 0, i < ny - 1};
     const int64_t node[5] = {c, c - 1, c + 1, c - nx, c + nx};
     T2<T> *Q = (T2<T> *)p.P[dst];
@@ -453,7 +474,8 @@ __global__ void k_rhs_norm(DevProblem p) {
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
     for (int64_t v = gtid(); v < p.n; v += stride) {
-        const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+        int i, j;
+        node_rc(v, p.nx, i, j);
         double bv = 0.0;
         if (p.m > 0) {
             // w * (s * y): gather w_kc * y_k * s_k
@@ -562,7 +584,8 @@ __device__ __forceinline__ dfl apply_L_df(const DevProblem &p, const float2 *x, 
 __global__ void k_Lmu_df(DevProblem p) {
     const int64_t v = gtid();
     if (v >= p.n) return;
-    const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+    int i, j;
+    node_rc(v, p.nx, i, j);
     df_st((float2 *)p.z64, v, apply_L_df(p, (const float2 *)p.mu64, v, i, j));
 }
 
@@ -575,7 +598,8 @@ __global__ void k_res_df(DevProblem p) {
     const int *o = p.optr;
     const int nx = p.nx;
     for (int64_t v = gtid(); v < p.n; v += stride) {
-        const int i = (int)(v / nx), j = (int)(v - (int64_t)i * nx);
+        int i, j;
+        node_rc(v, nx, i, j);
         dfl r = df_neg(df_mul({p.gam_hi, p.gam_lo}, apply_L_df(p, (const float2 *)p.z64, v, i, j)));
         if (p.m > 0) {
             for (int k = o[v]; k < o[v + 1]; ++k) r = df_add(r, df_neg(df_mul(df_ld(p.owdf, 4 * (int64_t)k), df_ld(e, k))));
@@ -627,14 +651,16 @@ __device__ __forceinline__ double apply_L(const DevProblem &p, const double *x, 
 __global__ void k_Lx(DevProblem p, const double *x, double *y) {
     const int64_t v = gtid();
     if (v >= p.n) return;
-    const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+    int i, j;
+    node_rc(v, p.nx, i, j);
     y[v] = apply_L(p, x, v, i, j);
 }
 
 __global__ void k_Lmu(DevProblem p) {
     const int64_t v = gtid();
     if (v >= p.n) return;
-    const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+    int i, j;
+    node_rc(v, p.nx, i, j);
     p.z64[v] = apply_L(p, p.mu64, v, i, j);
 }
 
@@ -643,7 +669,8 @@ __global__ void k_res(DevProblem p) {
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
     for (int64_t v = gtid(); v < p.n; v += stride) {
-        const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+        int i, j;
+        node_rc(v, p.nx, i, j);
         double r = -p.gamma * apply_L(p, p.z64, v, i, j);
         if (p.m > 0) r -= obs_gather64(p, v, i, j, p.e64, 1, 0);
         acc += r * r;
@@ -684,7 +711,8 @@ template <typename T>
 __global__ void k_ws_input(DevProblem p, T inv_scale, float kfeat, int Hp, int Wp, __nv_bfloat16 *x) {
     const int64_t q = gtid();
     if (q >= (int64_t)Hp * Wp) return;
-    const int i = (int)(q / Wp), j = (int)(q - (int64_t)i * Wp);
+    int i, j;
+    node_rc(q, Wp, i, j);
     const T *ow = (const T *)p.ow;    // 4 weights per observation
     const T *oyv = (const T *)p.ovar; // (y, variance) per observation
     T sum = T(0);
@@ -721,7 +749,8 @@ __global__ void k_ws_input(DevProblem p, T inv_scale, float kfeat, int Hp, int W
 template <typename T> __global__ void k_ws_target(DevProblem p, double inv_scale, int Hp, int Wp, float *t) {
     const int64_t q = gtid();
     if (q >= (int64_t)Hp * Wp) return;
-    const int i = (int)(q / Wp), j = (int)(q - (int64_t)i * Wp);
+    int i, j;
+    node_rc(q, Wp, i, j);
     float a = 0.f, b = 0.f;
     if (i < p.ny && j < p.nx) {
         const BeliefStore<T> s = ((const BeliefStore<T> *)p.belief)[(int64_t)i * p.nx + j];
@@ -740,7 +769,8 @@ template <typename T> __global__ void k_ws_target(DevProblem p, double inv_scale
 __global__ void k_ws_node_msg(DevProblem p, float scale, int Wp, const float *out, float2 *nm) {
     const int64_t v = gtid();
     if (v >= p.n) return;
-    const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+    int i, j;
+    node_rc(v, p.nx, i, j);
     const int64_t q = (int64_t)i * Wp + j;
     const float lg = fminf(fmaxf(out[2 * q + 1], -10.f), 15.f);
     const float L = expf(lg) / (float)node_slots(p, v);
@@ -763,7 +793,8 @@ __global__ void k_upscale_marg(const double *mu_c, const double *q_c, int q_is_v
                                int nxf, int nyf, double *mu_f, double *lam_f) {
     const int64_t v = gtid();
     if (v >= (int64_t)nxf * nyf) return;
-    const int i = (int)(v / nxf), j = (int)(v - (int64_t)i * nxf);
+    int i, j;
+    node_rc(v, nxf, i, j);
     const int ic = min(i >> shift, nyc - 1), jc = min(j >> shift, nxc - 1);
     const int64_t c = (int64_t)ic * nxc + jc;
     mu_f[v] = mu_c[c];
@@ -774,7 +805,8 @@ __global__ void k_init_nodes_prior(DevProblem p, int dst, const float2 *nm) {
     const int64_t c = gtid();
     if (c >= p.n) return;
     const int nx = p.nx, ny = p.ny;
-    const int i = (int)(c / nx), j = (int)(c - (int64_t)i * nx);
+    int i, j;
+    node_rc(c, nx, i, j);
     const bool exists[5] = {true, j > 0, j < nx - 1, i > 0, i < ny - 1};
     const int64_t node[5] = {c, c - 1, c + 1, c - nx, c + nx};
     float2 *Q = (float2 *)p.P[dst];
@@ -794,7 +826,8 @@ __global__ void k_init_nodes_obs(DevProblem p, int dst, const float2 *nm) {
 __global__ void k_ws_decode(DevProblem p, double scale, int Wp, const float *out, double *mu0, double *lam0) {
     const int64_t v = gtid();
     if (v >= p.n) return;
-    const int i = (int)(v / p.nx), j = (int)(v - (int64_t)i * p.nx);
+    int i, j;
+    node_rc(v, p.nx, i, j);
     const int64_t q = (int64_t)i * Wp + j;
     double lg = (double)out[2 * q + 1];
     lg = lg < -10.0 ? -10.0 : (lg > 15.0 ? 15.0 : lg);
