@@ -855,6 +855,8 @@ struct gabp_batch {
     int *h_items = nullptr;      // pinned mirror
     int *d_err = nullptr;        // TMA: a bounded wait in the batched kernel gave up
     gabp::TmaMapsGlobal *d_maps = nullptr;   // TMA: the problems' tensor maps
+    std::vector<int *> optr_pad;  // TMA: observation index with rows padded to a multiple of 4 ints
+                                  // (problems whose nx is not one; nullptr otherwise)
     int all_tiles = 0;           // TMA: tiles of all problems at the current height (grid bound)
     int maps_ty = 0;             // TMA: tile height the tensor maps were encoded for
     double *h_scal = nullptr;    // pinned, 2 per problem
@@ -987,19 +989,27 @@ int batch_upload_active(gabp_batch *b) {
     return GABP_OK;
 }
 
-// Tensor maps with boxes for 30 x ty tiles: the message planes of the problems with nx even and
-// the observation index of those with nx a multiple of 4 (16-byte row strides); the batched
-// TMA kernel copies the other parts with cp.async.
+// Tensor maps with boxes for 30 x ty tiles: the message planes of the problems with nx even
+// (16-byte row strides; the batched TMA kernel copies the others with cp.async) and the
+// observation index of every problem, from a copy whose rows are padded to a multiple of 4
+// ints where nx is not one (made once, the index is fixed at creation).
 int batch_encode_maps(gabp_batch *b, int ty) {
     const int count = (int)b->inst.size();
     std::vector<gabp::TmaMapsGlobal> maps(count);
     std::memset((void *)maps.data(), 0, sizeof(gabp::TmaMapsGlobal) * count);
+    b->optr_pad.resize((size_t)count, nullptr);
     for (int i = 0; i < count; ++i) {
-        const int nxi = b->inst[i]->p.nx;
-        const int parts = (nxi % 2 == 0 ? gabp::TMA_MAP_PLANES : 0) | (nxi % 4 == 0 ? gabp::TMA_MAP_OPTR : 0);
-        if (!parts) continue;
+        const gabp::DevProblem &pi = b->inst[i]->p;
+        const int nxi = pi.nx, pitch = (nxi + 3) & ~3;
+        if (nxi % 4 != 0 && !b->optr_pad[i]) {
+            BK(cudaMalloc((void **)&b->optr_pad[i], sizeof(int) * (size_t)pitch * pi.ny), "alloc padded index");
+            BK(cudaMemcpy2DAsync(b->optr_pad[i], sizeof(int) * (size_t)pitch, pi.optr, sizeof(int) * (size_t)nxi,
+                                 sizeof(int) * (size_t)nxi, pi.ny, cudaMemcpyDeviceToDevice, b->stream),
+               "padded index copy");
+        }
+        const int parts = (nxi % 2 == 0 ? gabp::TMA_MAP_PLANES : 0) | gabp::TMA_MAP_OPTR;
         gabp::TmaMaps m{};
-        BK(gabp::make_tma_maps(b->inst[i]->p, 30, ty, m, parts), "tensor map encode");
+        BK(gabp::make_tma_maps(pi, 30, ty, m, parts, b->optr_pad[i], pitch), "tensor map encode");
         maps[i].planes[0] = m.planes[0];
         maps[i].planes[1] = m.planes[1];
         maps[i].optr = m.optr;
@@ -1248,6 +1258,9 @@ void batch_free(gabp_batch *b) {
     if (b->h_items) cudaFreeHost(b->h_items);
     b->d_items = b->h_items = nullptr;
     if (b->d_maps) cudaFree(b->d_maps);
+    for (int *q : b->optr_pad)
+        if (q) cudaFree(q);
+    b->optr_pad.clear();
     b->d_err = nullptr;
     b->d_maps = nullptr;
     if (b->h_active) cudaFreeHost(b->h_active);

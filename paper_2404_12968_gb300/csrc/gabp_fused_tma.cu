@@ -311,11 +311,12 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
     };
 
     // BATCH (every thread; a stage barrier counts one arrival per warp, made by its lane 0 after
-    // the warp's own copies): the message planes of a problem with nx even (16-byte row
-    // strides) and the observation index of one with nx a multiple of 4 come by the tensor
-    // copies of its own maps (thread 0 registers their bytes first); the other parts by
-    // cp.async copies of the same boxes (a warp per box row), zero-filled outside the grid as
-    // the tensor copies are, each thread's copies tracked by the barrier
+    // the warp's own copies): the observation index of every problem (its rows padded to a
+    // 16-byte pitch where nx is not a multiple of 4) and the message planes of a problem with nx
+    // even (16-byte row strides) come by the tensor copies of its own maps (thread 0 registers
+    // their bytes first); the planes of an odd width by cp.async copies of the same box (a warp
+    // per box row), zero-filled outside the grid as the tensor copies are, each thread's copies
+    // tracked by the barrier
     auto fill = [&](int stage, int item) {
         unsigned char *base = smem + stage * LY::stage;
         const uint32_t bar = smem_addr(&bars[stage]);
@@ -324,13 +325,11 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         const DevProblem &q = ba.table[prob];
         const int qnx = q.nx, qny = q.ny;
         const int x0 = w.y * TTX, y0 = w.z * TY;
-        const bool tma_planes = qnx % 2 == 0, tma_optr = qnx % 4 == 0;
-        if (tid == 0 && tma_planes) {
-            mbar_expect_tx_only(bar, LY::plane_bytes + (tma_optr ? LY::optr_bytes : 0u));
-            tma_load_3d(smem_addr(base), &ba.maps[prob].planes[src], 2 * (x0 - 2), y0 - 2, 0, bar);
-            if (tma_optr)
-                tma_load_2d(smem_addr(base + a128(LY::plane_bytes)), &ba.maps[prob].optr, (x0 - 2) & ~3, y0 - 2,
-                            bar);
+        const bool tma_planes = qnx % 2 == 0;
+        if (tid == 0) {
+            mbar_expect_tx_only(bar, (tma_planes ? LY::plane_bytes : 0u) + LY::optr_bytes);
+            if (tma_planes) tma_load_3d(smem_addr(base), &ba.maps[prob].planes[src], 2 * (x0 - 2), y0 - 2, 0, bar);
+            tma_load_2d(smem_addr(base + a128(LY::plane_bytes)), &ba.maps[prob].optr, (x0 - 2) & ~3, y0 - 2, bar);
         }
         if (!tma_planes) {
             const float2 *P = (const float2 *)q.P[src];
@@ -346,23 +345,6 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                     if (cx < RX) {
                         const bool in = rin && gx >= 0 && gx < qnx;
                         cp_async_zfill<8>(dp + 8u * (row * RX + cx), in ? src_row + gx : P, in ? 8u : 0u);
-                    }
-                }
-            }
-        }
-        if (!tma_optr) {
-            const int xs = (x0 - 2) & ~3;
-            const uint32_t dw = smem_addr(base + a128(LY::plane_bytes));
-            for (int r = warp; r < LY::OY; r += TW) {   // [OY][OXW] indices from (xs, y0 - 2)
-                const int gy = y0 - 2 + r;
-                const bool rin = gy >= 0 && gy < qny;
-                const int *src_row = q.optr + (int64_t)(rin ? gy : 0) * qnx;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int cx = lane + 32 * h, gx = xs + cx;
-                    if (cx < OXW) {
-                        const bool in = rin && gx >= 0 && gx < qnx;
-                        cp_async_zfill<4>(dw + 4u * (r * OXW + cx), in ? src_row + gx : q.optr, in ? 4u : 0u);
                     }
                 }
             }
@@ -689,7 +671,8 @@ bool tma_problem_supported(const DevProblem &p) { return p.prec == 0 && p.nx % 4
 
 // Tensor maps of both message buffers (3-D: 2 nx floats x ny rows x 5 planes) and of the
 // observation index (2-D: nx x ny int32 of optr[0..n)), with boxes for the tile shape.
-cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps, int parts) {
+cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps, int parts, const int *optr,
+                          int optr_pitch) {
     maps.valid = false;
     if (!tma_shape_supported(tx, ty)) return cudaErrorInvalidValue;
     auto enc = encoder();
@@ -706,10 +689,10 @@ cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps, in
     }
     if (parts & TMA_MAP_OPTR) {
         cuuint64_t dims[2] = {(cuuint64_t)p.nx, (cuuint64_t)p.ny};
-        cuuint64_t strides[1] = {(cuuint64_t)p.nx * 4};
+        cuuint64_t strides[1] = {(cuuint64_t)(optr ? optr_pitch : p.nx) * 4};
         cuuint32_t box[2] = {40, (cuuint32_t)(ty + 3)};
         cuuint32_t es[2] = {1, 1};
-        CUresult r = enc(&maps.optr, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, (void *)p.optr, dims, strides, box, es,
+        CUresult r = enc(&maps.optr, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, (void *)(optr ? optr : p.optr), dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;

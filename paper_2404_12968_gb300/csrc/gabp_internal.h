@@ -171,7 +171,10 @@ bool tma_shape_supported(int tx, int ty);
 bool tma_problem_supported(const DevProblem &p);
 // parts: which maps to encode (planes need nx even, the observation index nx a multiple of 4)
 constexpr int TMA_MAP_PLANES = 1, TMA_MAP_OPTR = 2;
-cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps, int parts = TMA_MAP_PLANES | TMA_MAP_OPTR);
+// optr / optr_pitch: a copy of the observation index with rows optr_pitch ints apart (a multiple
+// of 4) to encode instead of p.optr (whose rows are nx ints apart).
+cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps, int parts = TMA_MAP_PLANES | TMA_MAP_OPTR,
+                          const int *optr = nullptr, int optr_pitch = 0);
 size_t tma_smem_bytes(int tx, int ty);
 // Tiles per run for a problem on 30 x ty tiles: the length in 1..4 that balances the
 // persistent blocks best (longest on ties).
