@@ -268,7 +268,9 @@ def own_arm(args):
     peak, peak_kind = measured_peak_gbs()
     achieved = st["bytes_per_iter"] / (iter_ms / 1e3) / 1e9
     traffic = profiled_traffic(KERNEL_NAMES[st["kernel"]])
-    h2d = 32 * p.m + 4 * p.m + 4 * (n + 1)   # obs (x, y, value, variance) + base cells + cell pointers
+    # what gabp_create copies to the device: the sorted observations (x, y, value, variance as
+    # doubles) and their base cells (int32); the per-cell index is built on the device
+    h2d = 32 * p.m + 4 * p.m
     d2h = 8 * n + 16                          # marginal means + residual scalars
     launches_per_step = ITERS_PER_STEP + 6 + 2
     line = {
