@@ -411,13 +411,28 @@ def _single_core_rate(timeout_s: float = 120.0):
         return None
 
 
+def _exact_solve_time(size: int = 256):
+    """Wall time of the oracle's exact posterior mean (A x = b by scipy's sparse LU, a library
+    step) on the workload generator scaled to size^2; the full 4096^2 system is out of reach of
+    a direct solve within the bench's time bound."""
+    import oracle
+    q = make_problem(0, size)
+    fl = oracle.build_factors(q.nx, q.ny, q.kappa, q.obs_x, q.obs_y, q.y, q.noise_var)
+    t = time.perf_counter()
+    x = oracle.exact_mean(fl, q.nx, "sparse")
+    dt = time.perf_counter() - t
+    return {"grid": [q.nx, q.ny], "unknowns": q.n, "observations": q.m, "seconds": dt,
+            "relative_residual": oracle.residual(fl, x), "method": "sparse LU (scipy), FP64"}
+
+
 def cpu_baseline(p):
     rate, dt, cores = _oracle_rate(p, 2)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"2 oracle GaBP iterations (FP64, C + OpenMP over factors) on the full "
                       f"{p.nx}x{p.ny} workload, {dt:.1f} s",
             "single_core": {"value": _single_core_rate(), "unit": UNIT, "cores": 1,
-                            "sample": "one oracle GaBP iteration of the full workload, OMP_NUM_THREADS=1"}}
+                            "sample": "one oracle GaBP iteration of the full workload, OMP_NUM_THREADS=1"},
+            "exact_solve": _exact_solve_time()}
 
 
 def reference_arm(args):
