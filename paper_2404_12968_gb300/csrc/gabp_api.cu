@@ -5,9 +5,11 @@
 // of fused (or split) iteration kernels on the context's stream.
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <mutex>
 #include <thread>
@@ -269,17 +271,77 @@ int host_chunks(int64_t count) {
     return (int)(t < by_size ? t : by_size);
 }
 
+// Host worker pool for the set-up chunks: up to hardware_concurrency - 1 threads, made on first
+// use and kept for the process (detached, parked on a condition variable), so that a region
+// costs a wake-up instead of a thread creation per chunk.  One region runs on the pool at a
+// time; a region that finds it busy (another host thread's) spawns its own threads.
+struct HostPool {
+    std::mutex run_mu;   // held by the region using the pool
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::function<void(int)> job;   // runs chunk ch of the current region
+    int nchunk = 0, next = 0, done = 0;
+    int workers = 0;
+};
+
+HostPool *host_pool() {
+    static HostPool *pool = new HostPool();   // never destroyed: its threads outlive static destruction
+    return pool;
+}
+
+void host_pool_worker(HostPool *p) {
+    std::unique_lock<std::mutex> lk(p->mu);
+    for (;;) {
+        p->cv_work.wait(lk, [p] { return p->next < p->nchunk; });
+        const int ch = p->next++;
+        lk.unlock();
+        p->job(ch);
+        lk.lock();
+        if (++p->done == p->nchunk) p->cv_done.notify_one();
+    }
+}
+
 template <typename F> void parallel_chunks(int64_t count, int nchunk, F f) {
     if (nchunk <= 1) {
         f(0, (int64_t)0, count);
         return;
     }
-    std::vector<std::thread> th;
-    th.reserve((size_t)nchunk - 1);
-    for (int ch = 1; ch < nchunk; ++ch)
-        th.emplace_back([&, ch]() { f(ch, count * ch / nchunk, count * (ch + 1) / nchunk); });
-    f(0, (int64_t)0, count / nchunk);
-    for (std::thread &t : th) t.join();
+    auto chunk = [&](int ch) { f(ch, count * ch / nchunk, count * (ch + 1) / nchunk); };
+    HostPool *p = host_pool();
+    std::unique_lock<std::mutex> run(p->run_mu, std::try_to_lock);
+    if (!run.owns_lock()) {
+        std::vector<std::thread> th;
+        th.reserve((size_t)nchunk - 1);
+        for (int ch = 1; ch < nchunk; ++ch) th.emplace_back(chunk, ch);
+        chunk(0);
+        for (std::thread &t : th) t.join();
+        return;
+    }
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        while (p->workers < nchunk - 1) {
+            std::thread(host_pool_worker, p).detach();
+            ++p->workers;
+        }
+        p->job = chunk;
+        p->done = 0;
+        p->next = 0;
+        p->nchunk = nchunk;
+    }
+    p->cv_work.notify_all();
+    // this thread takes chunks too, then waits for the others
+    std::unique_lock<std::mutex> lk(p->mu);
+    while (p->next < p->nchunk) {
+        const int ch = p->next++;
+        lk.unlock();
+        chunk(ch);
+        lk.lock();
+        ++p->done;
+    }
+    p->cv_done.wait(lk, [p] { return p->done == p->nchunk; });
+    p->nchunk = 0;
+    p->next = 0;
+    p->job = nullptr;
 }
 
 int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *prior, int64_t m,
