@@ -274,27 +274,27 @@ void orc_rhs(int64_t n, int64_t nf, const int64_t *ptr, const int64_t *var, cons
 }
 
 /*
- * Exact posterior mean: solve A x = b with a banded Cholesky factorisation in the natural
- * (row-major) ordering.  `bw` is the half bandwidth; every pair of variables sharing a
- * factor must be within bw of each other (checked).  Band storage: B[i*(bw+1) + d] holds
- * A[i][i-d] for d = 0..bw (lower band).  The solution overwrites b.
+ * Banded Cholesky of A = sum_f s_f a_f a_f^T in the natural (row-major) ordering.  `bw` is the
+ * half bandwidth; every pair of variables sharing a factor must be within bw of each other
+ * (checked).  Band storage: B[i*(bw+1) + d] holds A[i][i-d] for d = 0..bw (lower band); on
+ * success it holds the lower Cholesky factor G (A = G G^T) in the same places.
  */
-int orc_band_solve(int64_t n, int64_t nf, const int64_t *ptr, const int64_t *var,
-                   const double *coef, const double *s, int64_t bw, double *b) {
-    if (bw < 0 || n <= 0) return ORC_ERR_ARG;
+static int band_assemble(int64_t n, int64_t nf, const int64_t *ptr, const int64_t *var,
+                         const double *coef, const double *s, int64_t bw, double *B) {
     const int64_t w = bw + 1;
-    double *B = (double *)calloc((size_t)(n * w), sizeof(double));
-    if (!B) return ORC_ERR_OOM;
-    /* assemble the lower band of A */
     for (int64_t f = 0; f < nf; ++f)
         for (int64_t p = ptr[f]; p < ptr[f + 1]; ++p)
             for (int64_t q = ptr[f]; q < ptr[f + 1]; ++q) {
                 int64_t i = var[p], j = var[q];
                 if (j > i) continue;
-                if (i - j > bw) { free(B); return ORC_ERR_ARG; }
+                if (i - j > bw) return ORC_ERR_ARG;
                 B[i * w + (i - j)] += s[f] * coef[p] * coef[q];
             }
-    /* Cholesky A = G G^T, G lower, stored in place: G[i][j] at B[i*w + (i-j)] */
+    return ORC_OK;
+}
+
+static int band_cholesky(int64_t n, int64_t bw, double *B) {
+    const int64_t w = bw + 1;
     for (int64_t i = 0; i < n; ++i) {
         int64_t jlo = i - bw > 0 ? i - bw : 0;
         for (int64_t j = jlo; j <= i; ++j) {
@@ -303,13 +303,27 @@ int orc_band_solve(int64_t n, int64_t nf, const int64_t *ptr, const int64_t *var
             if (klo < 0) klo = 0;
             for (int64_t k = klo; k < j; ++k) sum -= B[i * w + (i - k)] * B[j * w + (j - k)];
             if (j == i) {
-                if (!(sum > 0.0)) { free(B); return ORC_ERR_NOTPD; }
+                if (!(sum > 0.0)) return ORC_ERR_NOTPD;
                 B[i * w] = sqrt(sum);
             } else {
                 B[i * w + (i - j)] = sum / B[j * w];
             }
         }
     }
+    return ORC_OK;
+}
+
+/* Exact posterior mean: solve A x = b by the banded Cholesky above, then the two triangular
+ * solves.  The solution overwrites b. */
+int orc_band_solve(int64_t n, int64_t nf, const int64_t *ptr, const int64_t *var,
+                   const double *coef, const double *s, int64_t bw, double *b) {
+    if (bw < 0 || n <= 0) return ORC_ERR_ARG;
+    const int64_t w = bw + 1;
+    double *B = (double *)calloc((size_t)(n * w), sizeof(double));
+    if (!B) return ORC_ERR_OOM;
+    int rc = band_assemble(n, nf, ptr, var, coef, s, bw, B);
+    if (rc == ORC_OK) rc = band_cholesky(n, bw, B);
+    if (rc != ORC_OK) { free(B); return rc; }
     /* forward: G z = b */
     for (int64_t i = 0; i < n; ++i) {
         double sum = b[i];
@@ -325,5 +339,133 @@ int orc_band_solve(int64_t n, int64_t nf, const int64_t *ptr, const int64_t *var
         b[i] = sum / B[i * w];
     }
     free(B);
+    return ORC_OK;
+}
+
+/*
+ * Exact marginal variances diag(A^-1) by selected inversion on the band (Takahashi, Fagan and
+ * Chen's recurrences, in the Cholesky form used for GMRFs).  With A = G G^T (G lower, band bw),
+ * S = A^-1 satisfies S G = G^-T; reading off the entries on and above the diagonal gives, for
+ * j >= i,
+ *     S_ij = delta_ij / G_ii^2 - (1 / G_ii) sum_{k = i+1..i+bw} G_ki S_kj,
+ * and every S_kj it needs has |k - j| <= bw, so the band of S is closed under the recurrence:
+ * rows are taken from the last to the first, and in each row j from the band's edge down to i.
+ * var_out[i] = S_ii.  Costs n bw^2 multiply-adds and two n x (bw+1) arrays.
+ */
+int orc_band_selinv(int64_t n, int64_t nf, const int64_t *ptr, const int64_t *var,
+                    const double *coef, const double *s, int64_t bw, double *var_out) {
+    if (bw < 0 || n <= 0) return ORC_ERR_ARG;
+    const int64_t w = bw + 1;
+    double *B = (double *)calloc((size_t)(n * w), sizeof(double));
+    double *S = (double *)calloc((size_t)(n * w), sizeof(double));   /* S[a*w + (a-b)] = S_ab, a >= b */
+    if (!B || !S) { free(B); free(S); return ORC_ERR_OOM; }
+    int rc = band_assemble(n, nf, ptr, var, coef, s, bw, B);
+    if (rc == ORC_OK) rc = band_cholesky(n, bw, B);
+    if (rc != ORC_OK) { free(B); free(S); return rc; }
+    for (int64_t i = n - 1; i >= 0; --i) {
+        const int64_t khi = i + bw < n - 1 ? i + bw : n - 1;
+        const double gii = B[i * w];
+        for (int64_t j = khi; j >= i; --j) {
+            double sum = 0.0;
+            for (int64_t k = i + 1; k <= khi; ++k) {
+                const double gki = B[k * w + (k - i)];
+                const double skj = k >= j ? S[k * w + (k - j)] : S[j * w + (j - k)];
+                sum += gki * skj;
+            }
+            const double sij = ((j == i ? 1.0 / gii : 0.0) - sum) / gii;
+            S[j * w + (j - i)] = sij;
+        }
+        var_out[i] = S[i * w];
+    }
+    free(B);
+    free(S);
+    return ORC_OK;
+}
+
+/*
+ * The posterior precision A = sum_f s_f a_f a_f^T as a CSR matrix with sorted column indices
+ * (the fine level of the iterative exact solve).  Pass rp = NULL to get only the row lengths:
+ * then row_len[i] = number of distinct columns of row i.  With rp given (rp[i+1] - rp[i] =
+ * row_len[i]), the columns and values of each row are written.  Rows are independent; entries
+ * are summed factor by factor in factor-list order.
+ */
+int orc_assemble_csr(int64_t n, int64_t nf, const int64_t *ptr, const int64_t *var,
+                     const double *coef, const double *s, int64_t *row_len, const int64_t *rp,
+                     int64_t *ci, double *val) {
+    int64_t *nptr = NULL, *nslot = NULL, *fac = NULL;
+    if (n < 0 || nf < 0) return ORC_ERR_ARG;
+    if (build_node_slots(n, nf, ptr, var, &nptr, &nslot) != ORC_OK) return ORC_ERR_OOM;
+    /* factor of each slot */
+    const int64_t ne = ptr[nf];
+    fac = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ne > 0 ? ne : 1));
+    if (!fac) { free(nptr); free(nslot); return ORC_ERR_OOM; }
+    for (int64_t f = 0; f < nf; ++f)
+        for (int64_t j = ptr[f]; j < ptr[f + 1]; ++j) fac[j] = f;
+    int err = 0;
+#pragma omp parallel reduction(| : err)
+    {
+        int64_t cols[512];
+        double vals[512];
+#pragma omp for schedule(dynamic, 4096)
+        for (int64_t i = 0; i < n; ++i) {
+            int nc = 0;
+            for (int64_t q = nptr[i]; q < nptr[i + 1] && !err; ++q) {
+                const int64_t jslot = nslot[q], f = fac[jslot];
+                for (int64_t p = ptr[f]; p < ptr[f + 1]; ++p) {
+                    const int64_t c = var[p];
+                    const double a = s[f] * coef[jslot] * coef[p];
+                    int t = 0;
+                    while (t < nc && cols[t] != c) ++t;
+                    if (t == nc) {
+                        if (nc == 512) { err = 1; break; }
+                        cols[nc] = c;
+                        vals[nc] = 0.0;
+                        ++nc;
+                    }
+                    vals[t] += a;
+                }
+            }
+            if (!rp) {
+                row_len[i] = nc;
+                continue;
+            }
+            /* insertion sort by column */
+            for (int a = 1; a < nc; ++a) {
+                int64_t c = cols[a];
+                double v = vals[a];
+                int b = a - 1;
+                while (b >= 0 && cols[b] > c) { cols[b + 1] = cols[b]; vals[b + 1] = vals[b]; --b; }
+                cols[b + 1] = c;
+                vals[b + 1] = v;
+            }
+            if (rp[i + 1] - rp[i] != nc) { err = 1; continue; }
+            for (int a = 0; a < nc; ++a) { ci[rp[i] + a] = cols[a]; val[rp[i] + a] = vals[a]; }
+        }
+    }
+    free(fac);
+    free(nptr);
+    free(nslot);
+    return err ? ORC_ERR_ARG : ORC_OK;
+}
+
+/*
+ * `sweeps` Gauss-Seidel sweeps on M x = b for a CSR matrix M (the smoother of the multigrid
+ * preconditioner): row by row, x_i = (b_i - sum_{j != i} M_ij x_j) / M_ii with the newest x_j,
+ * rows in increasing order (backward = 0) or decreasing order (backward = 1).  A forward sweep
+ * before the coarse correction and a backward sweep after it make the V-cycle symmetric.
+ */
+int orc_gs_sweep(int64_t n, const int64_t *rp, const int64_t *ci, const double *val,
+                 const double *b, double *x, int backward, int sweeps) {
+    for (int t = 0; t < sweeps; ++t)
+        for (int64_t ii = 0; ii < n; ++ii) {
+            const int64_t i = backward ? n - 1 - ii : ii;
+            double d = 0.0, sum = b[i];
+            for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+                if (ci[p] == i) d = val[p];
+                else sum -= val[p] * x[ci[p]];
+            }
+            if (!(d > 0.0)) return ORC_ERR_NOTPD;
+            x[i] = sum / d;
+        }
     return ORC_OK;
 }
