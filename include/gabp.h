@@ -464,8 +464,12 @@ int gabp_wsnet_warm_start(gabp_ctx *ctx, gabp_wsnet *net);
  *   obs_xy, y, noise_var  DEVICE arrays (2m, m, m doubles) of the current device, with the
  *                       observations SORTED by base cell (i0 * nx + j0 non-decreasing, base
  *                       cell as defined for gabp_create); GABP_ERR_ARG if they are not, or if an
- *                       observation lies outside the grid or has a variance <= 0.
+ *                       observation lies outside the grid or has a variance <= 0 (that reason
+ *                       is reported when both occur).
  *   mean                DEVICE array of nx*ny doubles (the field mu).
+ *   Pointers that are not device (or managed) memory of the current device are GABP_ERR_ARG
+ *   (checked with cudaPointerGetAttributes, which allocates nothing).  The sizes cannot be
+ *   checked through a pointer: arrays shorter than stated make the kernels read past them.
  *   rel_residual        HOST pointer to one double, written on success.  If ||b|| = 0 the
  *                       absolute norm ||A mu|| is returned instead.
  *   stream              cudaStream_t to run on (NULL = the legacy default stream); the call

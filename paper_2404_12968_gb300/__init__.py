@@ -134,6 +134,19 @@ def gabp_destroy(ctx: int) -> None:
         _lib.load().gabp_destroy(ctx)
 
 
+def _device_f64_count(t, name: str) -> int:
+    """Number of elements of ``t``, which must be a contiguous float64 CUDA tensor on the current
+    device (the allocation-free entry point reads it from the GPU as it is)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} must live on the current CUDA device")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 tensor")
+    return int(t.numel())
+
+
 def gabp_residual_noalloc(nx: int, ny: int, kappa: float, obs_xy, y, noise_var, mean, *,
                           gamma: float = 1.0, stream=None) -> float:
     """Relative residual of ``mean`` without any allocation by the library.
@@ -142,7 +155,11 @@ def gabp_residual_noalloc(nx: int, ny: int, kappa: float, obs_xy, y, noise_var, 
     tensors on the current device; the observations must be sorted by base cell.  ``stream`` is
     a ``cudaStream_t`` value (e.g. ``torch.cuda.current_stream().cuda_stream``) or None."""
     L = _lib.load()
-    m = int(y.numel()) if hasattr(y, "numel") else len(y)
+    m = _device_f64_count(y, "y")
+    if _device_f64_count(mean, "mean") != nx * ny:
+        raise ValueError(f"mean must hold nx * ny = {nx * ny} values")
+    if _device_f64_count(obs_xy, "obs_xy") != 2 * m or _device_f64_count(noise_var, "noise_var") != m:
+        raise ValueError("obs_xy must hold 2 m values and noise_var m values (m = len(y))")
     out = ctypes.c_double()
     rc = L.gabp_residual_noalloc(_lib.gabp_grid(nx, ny, 1.0), float(kappa), float(gamma), m,
                                  _ptr(obs_xy) if m else None, _ptr(y) if m else None,

@@ -83,12 +83,12 @@ __global__ void na_obs(NaArgs a) {
     if (k >= a.m) return;
     const double x = a.xy[2 * k], yy = a.xy[2 * k + 1];
     if (!(x >= 0.0 && x <= a.nx - 1.0 && yy >= 0.0 && yy <= a.ny - 1.0) || !(a.var[k] > 0.0)) {
-        atomicExch(a.flag, 2);
+        atomicMax(a.flag, 2);   // takes precedence over "unsorted"
         a.e[k] = 0.0;
         return;
     }
     const int64_t b = na_base(a, k);
-    if (k > 0 && na_base(a, k - 1) > b) atomicExch(a.flag, 1);
+    if (k > 0 && na_base(a, k - 1) > b) atomicMax(a.flag, 1);
     double w[4];
     na_weights(a, k, b, w);
     const double hm = w[0] * a.mu[b] + w[1] * a.mu[b + 1] + w[2] * a.mu[b + a.nx] + w[3] * a.mu[b + a.nx + 1];
@@ -219,6 +219,17 @@ extern "C" int gabp_residual_noalloc(gabp_grid grid, double kappa, double gamma,
     if (g_addr_err[dev] != cudaSuccess) return na_fail(GABP_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
     double *scratch = g_addr[dev];
     cudaStream_t st = (cudaStream_t)stream;
+    // every array the kernels read must be device (or managed) memory of this device
+    const void *ins[4] = {mean, obs_xy, y, noise_var};
+    for (int q = 0; q < (m > 0 ? 4 : 1); ++q) {
+        cudaPointerAttributes pa;
+        e = cudaPointerGetAttributes(&pa, ins[q]);
+        if (e != cudaSuccess || !(pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) ||
+            (pa.type == cudaMemoryTypeDevice && pa.device != dev)) {
+            cudaGetLastError();
+            return na_fail(GABP_ERR_ARG, "inputs must be device memory of the current device");
+        }
+    }
 
     NaArgs a;
     a.nx = grid.nx;
