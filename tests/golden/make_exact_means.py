@@ -95,7 +95,7 @@ def write(name: str, verbose: bool = True) -> str:
         f"# solve_seconds {dt:.1f}",
         "# node_index exact_mean",
     ]
-    lines += [f"{i} {x[i]!r}" for i in idx]
+    lines += [f"{int(i)} {float(x[i])!r}" for i in idx]
     with open(path_for(name), "w") as f:
         f.write("\n".join(lines) + "\n")
     if verbose:
