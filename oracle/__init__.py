@@ -7,7 +7,8 @@ library (no shared code, headers or constants) and never imports it.
 Contents
 --------
 * ``build_factors``: the factor graph of the posterior as a generic list of rank-1
-  factors ``exp(-(s/2)(a . x - r)^2)``:
+  factors ``exp(-(s/2)(a . x - r)^2)`` (with a prior mean f_b the cell factors' targets are
+  r = a . f_b, ``with_prior_mean``):
     - prior (Sec. 3.1, P = gamma L^T L with L the finite-difference operator of App. C,
       Eq. for the discretised operator, extended to 2-D): one factor per cell i with
       a = row i of L, s = gamma, r = 0.  Zero-Neumann boundary, read as a cell-centred
@@ -36,7 +37,7 @@ import numpy as np
 from .build import build_oracle, library_path
 
 __all__ = [
-    "FactorList", "build_factors", "prior_factors", "obs_factors", "bilinear_base_weights",
+    "FactorList", "build_factors", "prior_factors", "with_prior_mean", "obs_factors", "bilinear_base_weights",
     "concat", "gabp", "init_messages", "factor_update", "beliefs", "apply_A", "rhs",
     "residual", "exact_mean", "exact_variances", "dense_A", "band_solve", "half_bandwidth", "lib",
 ]
@@ -232,9 +233,28 @@ def obs_factors(nx: int, ny: int, ox, oy, y, noise_var) -> FactorList:
                       w.reshape(-1).copy(), 1.0 / nv, np.asarray(y, np.float64).copy())
 
 
-def build_factors(nx, ny, kappa, ox, oy, y, noise_var, gamma: float = 1.0, alpha: int = 2) -> FactorList:
-    """The posterior's factor list: prior cell factors first, then observations in input order."""
-    return concat(prior_factors(nx, ny, kappa, gamma, alpha), obs_factors(nx, ny, ox, oy, y, noise_var)).check()
+def with_prior_mean(fl: FactorList, prior_mean) -> FactorList:
+    """The cell factors of a prior with mean f_b (Sec. 2.2: the prior N(f_b, Sigma)): factor c
+    becomes exp(-(s/2)(a_c . f - a_c . f_b)^2), i.e. its target is r_c = a_c . f_b, written out
+    here as the dot product of the factor's coefficients with f_b at its variables."""
+    fb = np.asarray(prior_mean, np.float64).reshape(-1)
+    if fb.shape[0] != fl.n:
+        raise ValueError("prior mean must have one value per node")
+    r = np.zeros(fl.nf)
+    for f in range(fl.nf):
+        sl = slice(fl.ptr[f], fl.ptr[f + 1])
+        r[f] = float(np.dot(fl.coef[sl], fb[fl.var[sl]]))
+    return FactorList(fl.n, fl.ptr, fl.var, fl.coef, fl.s, r)
+
+
+def build_factors(nx, ny, kappa, ox, oy, y, noise_var, gamma: float = 1.0, alpha: int = 2,
+                  prior_mean=None) -> FactorList:
+    """The posterior's factor list: prior cell factors first, then observations in input order.
+    ``prior_mean`` (one value per node) gives the cell factors their targets (``with_prior_mean``)."""
+    pf = prior_factors(nx, ny, kappa, gamma, alpha)
+    if prior_mean is not None:
+        pf = with_prior_mean(pf, prior_mean)
+    return concat(pf, obs_factors(nx, ny, ox, oy, y, noise_var)).check()
 
 
 def factor_update(a, s, r, lam_c, eta_c):

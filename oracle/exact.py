@@ -193,8 +193,9 @@ def exact_mean_pcg(fl: FactorList, nx: int, ny: int, *, tol: float = 1e-13, maxi
     p = z.copy()
     rz = float(r @ z)
     it = 0
+    replaced = 0
     rel = float(np.linalg.norm(r)) / nb
-    while rel > tol and it < maxit:
+    while rel > tol and it < maxit and replaced <= 8:
         Ap = A @ p
         alpha = rz / float(p @ Ap)
         x += alpha * p
@@ -208,6 +209,7 @@ def exact_mean_pcg(fl: FactorList, nx: int, ny: int, *, tol: float = 1e-13, maxi
             # and carry on (restarting the search direction) until the true one is below tol
             r = b - A @ x
             rel = float(np.linalg.norm(r)) / nb
+            replaced += 1      # a tolerance below the rounding floor ends after a few of these
             if rel <= tol:
                 break
             z = M(r)
