@@ -5,7 +5,8 @@
 The full-size grids (4096^2 and the 2048^2 warm-start evaluation) are too large for the
 oracle to solve inside a GPU test or the benchmark's bounded run, so their exact posterior
 means A^-1 b are computed once here, by the oracle alone (``oracle.exact.exact_mean_pcg``,
-FP64 preconditioned conjugate gradients to ||b - A x|| / ||b|| <= 1e-13), and stored at a
+FP64 preconditioned conjugate gradients to ||b - A x|| / ||b|| <= 4e-15 where the iteration
+reaches it, else 1e-13), and stored at a
 seeded uniform sample of nodes together with the full field's L2 norm.  The inputs come from
 the shared seeded generator ``gabp_synth``; each file records checksums of them so that a
 reader can tell the generator still produces the same problem.  Nothing here touches the CUDA
@@ -78,14 +79,20 @@ def write(name: str, verbose: bool = True) -> str:
     p = make()
     fl = oracle.build_factors(p.nx, p.ny, p.kappa, p.obs_x, p.obs_y, p.y, p.noise_var, p.gamma, alpha)
     t = time.time()
-    x, info = exact.exact_mean_pcg(fl, p.nx, p.ny, tol=1e-13, maxit=20000, verbose=verbose)
+    # the solve's own error is about (condition number) x (relative residual): at 1024^2 the
+    # solutions at 1e-13 and 3e-15 differ by 2.4e-10, so the stored means are solved to 4e-15
+    # where the iteration gets there (1e-13 otherwise), well below the 1e-10 of the FP64 bar
+    try:
+        x, info = exact.exact_mean_pcg(fl, p.nx, p.ny, tol=4e-15, maxit=20000, verbose=verbose)
+    except RuntimeError:
+        x, info = exact.exact_mean_pcg(fl, p.nx, p.ny, tol=1e-13, maxit=20000, verbose=verbose)
     dt = time.time() - t
     idx = sample_indices(p.n, name)
     cs = input_checksums(p)
     lines = [
         f"# Exact posterior mean A^-1 b at {len(idx)} sampled nodes: {desc}.",
         "# Written by tests/golden/make_exact_means.py with the oracle alone (FP64 PCG with a",
-        "# multigrid preconditioner, run to ||b - A x|| / ||b|| <= 1e-13).",
+        f"# multigrid preconditioner, run to ||b - A x|| / ||b|| = {info['rel_residual']:.2e}).",
         f"# nx {p.nx}", f"# ny {p.ny}", f"# kappa {p.kappa!r}", f"# gamma {p.gamma!r}", f"# alpha {alpha}",
         f"# m {p.m}",
         *[f"# {k} {v!r}" for k, v in cs.items()],
