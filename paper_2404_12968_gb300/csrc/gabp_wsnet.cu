@@ -54,6 +54,8 @@ struct gabp_wsnet {
     __nv_bfloat16 *w16 = nullptr;    // BF16 copy (the flat vector, converted)
     __nv_bfloat16 *wt = nullptr;     // flipped/transposed weights scratch (largest layer)
     __nv_bfloat16 *wpk = nullptr;    // weights packed for the tensor-core forward (same offsets)
+    __nv_bfloat16 *wtpk = nullptr;   // flipped/transposed weights packed for the tensor-core backward (largest layer)
+    float *zbias = nullptr;          // 256 zeros: the backward-data convolution has no bias
     bool packed = false;             // wpk matches w16
     int *derr = nullptr;             // device flag of the tensor-core kernels (a bounded wait ran out)
     int kernels = GABP_WSNET_TCGEN05;
@@ -302,7 +304,25 @@ int conv_bwd(gabp_wsnet *net, int l, const Buf &g, const Buf &in, Buf *din, int 
     wa.T = s.taps;
     WK(gabp::nn::conv_wgrad(wa, net->g + net->woff[l], st), "conv wgrad");
     WK(gabp::nn::bias_grad(g.p, (int64_t)B * h * w, s.cout, net->g + net->boff[l], st), "bias grad");
-    if (din) {
+    if (din && net->kernels == GABP_WSNET_TCGEN05) {
+        // gradient w.r.t. the input: the forward convolution of g with the flipped, transposed
+        // weights (Cin and Cout exchanged), on the tcgen05 tensor cores like the forward pass
+        WK(gabp::nn::flip_transpose(net->w16 + net->woff[l], s.cout, s.taps, s.cin, net->wt, st), "flip");
+        WK(gabp::nn::tc_pack_weights(net->wt, s.cin, s.taps, s.cout, net->wtpk, st), "pack flipped weights");
+        gabp::nn::TcConvArgs a{};
+        a.wpk = net->wtpk;
+        a.bias = net->zbias;
+        a.out = din->p;
+        a.err = net->derr;
+        a.B = B;
+        a.H = h;
+        a.W = w;
+        a.Cin = s.cout;
+        a.Cout = s.cin;
+        a.T = s.taps;
+        a.relu = 0;
+        WK(gabp::nn::tc_conv(g.p, a, st), "tensor-core convolution backward data");
+    } else if (din) {
         WK(gabp::nn::flip_transpose(net->w16 + net->woff[l], s.cout, s.taps, s.cin, net->wt, st), "flip");
         ConvArgs a{};
         a.in = g.p;
@@ -476,6 +496,9 @@ int gabp_wsnet_create(gabp_wsnet **out, uint64_t seed, int device) {
     if (e == cudaSuccess) e = cudaMalloc((void **)&net->w16, sizeof(__nv_bfloat16) * off);
     if (e == cudaSuccess) e = cudaMalloc((void **)&net->wt, sizeof(__nv_bfloat16) * maxw);
     if (e == cudaSuccess) e = cudaMalloc((void **)&net->wpk, sizeof(__nv_bfloat16) * off);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&net->wtpk, sizeof(__nv_bfloat16) * maxw);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&net->zbias, sizeof(float) * 256);
+    if (e == cudaSuccess) e = cudaMemset(net->zbias, 0, sizeof(float) * 256);
     if (e == cudaSuccess) e = cudaMalloc((void **)&net->derr, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(net->derr, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(net->w, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice);
@@ -599,6 +622,8 @@ void gabp_wsnet_destroy(gabp_wsnet *net) {
     cudaFree(net->w16);
     cudaFree(net->wt);
     cudaFree(net->wpk);
+    cudaFree(net->wtpk);
+    cudaFree(net->zbias);
     cudaFree(net->derr);
     if (net->stream) cudaStreamDestroy(net->stream);
     if (prev >= 0) cudaSetDevice(prev);

@@ -90,6 +90,35 @@ def test_network_forward_and_gradients_match_reference():
     net.close()
 
 
+@pytest.mark.parametrize("B,H,W", [(2, 40, 72), (1, 64, 64)])
+def test_tensor_core_gradients_match_mma_sync_gradients(B, H, W):
+    """Training gradients with the tcgen05 kernels (forward and backward-data convolutions)
+    against the mma.sync kernels of the same network: the same BF16 arithmetic up to the
+    accumulation order, per layer within the BF16 bar of the reference comparison."""
+    torch = pytest.importorskip("torch")
+    from oracle import unet
+    from paper_2404_12968_gb300 import (GABP_WSNET_MMA_SYNC, GABP_WSNET_TCGEN05, WarmStartNet,
+                                        gabp_wsnet_gradients, gabp_wsnet_set_kernels)
+    net = WarmStartNet(seed=7, device=0)
+    rng = np.random.default_rng(8)
+    offs, head, total = unet.layout()
+    net.set_params((net.params() + rng.normal(size=total) * 0.02).astype(np.float32))
+    _, _, xs, ts = _case(torch, H, W, B, seed=10)
+    grads, losses = {}, {}
+    for k in (GABP_WSNET_TCGEN05, GABP_WSNET_MMA_SYNC):
+        gabp_wsnet_set_kernels(net.handle, k)
+        g = np.empty(total, np.float32)
+        losses[k] = gabp_wsnet_gradients(net.handle, xs, ts, H, W, g)
+        grads[k] = g
+    net.close()
+    a, b = grads[GABP_WSNET_TCGEN05], grads[GABP_WSNET_MMA_SYNC]
+    assert np.all(np.isfinite(a))
+    assert losses[GABP_WSNET_TCGEN05] == pytest.approx(losses[GABP_WSNET_MMA_SYNC], rel=1e-2)
+    for i, (wo, bo) in enumerate(offs):
+        e = np.linalg.norm(a[wo:bo] - b[wo:bo]) / (np.linalg.norm(b[wo:bo]) + 1e-12)
+        assert e < 6e-2, (i, e)
+
+
 @pytest.mark.parametrize("B,H,W", [(2, 40, 72), (1, 64, 64), (3, 16, 24)])
 def test_tensor_core_forward_matches_mma_sync_forward(B, H, W):
     """The tcgen05 forward (fused pooling, upsampling additions and head) against the mma.sync
