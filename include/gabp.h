@@ -212,6 +212,19 @@ int gabp_warm_start(gabp_ctx *ctx, const double *mu0, const double *lam0);
 int gabp_reset(gabp_ctx *ctx);
 
 /*
+ * Prior mean (Sec. 2.2: the Gaussian prior N(f_b, Sigma) has a mean f_b; Sec. 4.2 uses a
+ * climatology as f_b).  With the SPDE prior of Sec. 3.1 the prior factor of cell c becomes
+ * exp(-(gamma / 2) (l_c . f - l_c . f_b)^2): its target is r_c = (L f_b)_c instead of 0, and
+ * the posterior mean solves A mu = gamma L^T L f_b + H^T R^-1 y.  f_b: nx*ny doubles, host
+ * or device, copied; NULL restores the zero mean.  The targets are formed in FP64 and stored
+ * in the message precision; ||b|| is recomputed.  Messages are kept (iterating moves them to
+ * the new fixed point).  GABP_ERR_STATE for the alpha = 4 prior; a context with a prior mean
+ * refuses gabp_mg_create and gabp_pw_create (GABP_ERR_STATE).
+ */
+int gabp_set_prior_mean(gabp_ctx *ctx, const double *f_b);
+
+
+/*
  * Copy the current messages out / in (checkpoint and resume).  The buffer is opaque:
  * gabp_message_bytes() bytes (prior planes, 5 or 13 for alpha = 4, then the observation
  * messages), host or device, valid only for a context with the same problem and precision.

@@ -22,7 +22,8 @@ from ._lib import (GABP_ERR_ARG, GABP_ERR_CUDA, GABP_ERR_DIVERGED, GABP_ERR_OOM,
 
 __all__ = [
     "gabp_default_options", "gabp_create", "gabp_iterate", "gabp_marginals", "gabp_residual",
-    "gabp_warm_start", "gabp_reset", "gabp_message_bytes", "gabp_get_messages",
+    "gabp_warm_start", "gabp_reset", "gabp_set_prior_mean",
+    "gabp_message_bytes", "gabp_get_messages",
     "gabp_set_messages", "gabp_get_stats", "gabp_destroy", "gabp_residual_noalloc",
     "gabp_batch_create", "gabp_batch_iterate", "gabp_batch_residuals", "gabp_batch_marginals",
     "gabp_batch_get_stats", "gabp_batch_strip_height", "gabp_batch_destroy",
@@ -109,6 +110,11 @@ def gabp_warm_start(ctx: int, mu0, lam0) -> None:
 
 def gabp_reset(ctx: int) -> None:
     _check(_lib.load().gabp_reset(ctx), ctx)
+
+
+def gabp_set_prior_mean(ctx: int, f_b) -> None:
+    """Prior mean f_b (nx*ny float64, host array or CUDA tensor; None = zero)."""
+    _check(_lib.load().gabp_set_prior_mean(ctx, _ptr(f_b)), ctx)
 
 
 def gabp_message_bytes(ctx: int) -> int:
@@ -610,6 +616,10 @@ class Solver:
 
     def reset(self) -> None:
         gabp_reset(self.ctx)
+
+    def set_prior_mean(self, f_b) -> None:
+        gabp_set_prior_mean(self.ctx, np.ascontiguousarray(f_b, np.float64).reshape(-1)
+                            if isinstance(f_b, np.ndarray) else f_b)
 
     def message_change(self) -> float:
         return gabp_message_change(self.ctx)

@@ -207,6 +207,8 @@ def load():
     L.gabp_batch_wsnet_sample.restype = ctypes.c_int
     L.gabp_wsnet_warm_start.argtypes = [_vp, _vp]
     L.gabp_wsnet_warm_start.restype = ctypes.c_int
+    L.gabp_set_prior_mean.argtypes = [_vp, _vp]
+    L.gabp_set_prior_mean.restype = ctypes.c_int
     L.gabp_residual_noalloc.argtypes = [gabp_grid, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                         _vp, _vp, _vp, _vp, _dp, _vp]
     L.gabp_residual_noalloc.restype = ctypes.c_int

@@ -49,6 +49,11 @@ struct gabp_ctx {
     void *ws_x = nullptr;         // network input buffer (allocated on first use)
     // host copy of the observations (sorted by base cell): the multigrid levels are built from it
     std::vector<double> hxy, hy, hvar;
+    // prior mean (allocated on first use)
+    double *fb = nullptr;         // n: prior mean f_b (NULL: zero)
+    double *tgt64 = nullptr;      // n: cell-factor targets L f_b in FP64
+    void *tgtT = nullptr;         // n: the targets in the message precision
+    float2 *tgtdf = nullptr;      // n: the targets as double-float pairs (FP32 contexts)
 };
 
 namespace {
@@ -233,6 +238,37 @@ int compute_msg_change(gabp_ctx *c, double *out) {
     return GABP_OK;
 }
 
+size_t tsize(const gabp_ctx *c) { return c->p.prec ? sizeof(double) : sizeof(float); }
+
+// Cell-factor targets r = L f_b of the prior mean (none without one).  The iteration kernels
+// and the residual read them through the DevProblem, so the captured graph is dropped.
+int set_targets(gabp_ctx *c) {
+    gabp::DevProblem &p = c->p;
+    if (c->fb) CK(gabp::launch_cell_targets(p, c->fb, c->tgt64, c->tgtT, c->tgtdf, c->stream), "prior targets");
+    p.ptgt = c->fb ? c->tgtT : nullptr;
+    p.ptgt64 = c->fb ? c->tgt64 : nullptr;
+    p.ptgtdf = c->fb ? c->tgtdf : nullptr;
+    drop_graph(c);
+    return GABP_OK;
+}
+
+// Buffers of the prior mean (once per context).
+int alloc_targets(gabp_ctx *c) {
+    int rc;
+    void *q;
+    const int64_t n = c->p.n;
+    if (!c->tgt64) {
+        if ((rc = dalloc(c, &q, (size_t)n * sizeof(double), "alloc targets"))) return rc;
+        c->tgt64 = (double *)q;
+        if ((rc = dalloc(c, &c->tgtT, (size_t)n * tsize(c), "alloc targets"))) return rc;
+        if (c->p.prec == 0) {
+            if ((rc = dalloc(c, &q, (size_t)n * sizeof(float2), "alloc targets"))) return rc;
+            c->tgtdf = (float2 *)q;
+        }
+    }
+    return GABP_OK;
+}
+
 int init_messages(gabp_ctx *c) {
     CK(gabp::launch_init_cold(c->p, 0, c->opt.init == GABP_INIT_PAPER, c->stream), "init kernels");
     c->cur = 0;
@@ -259,7 +295,6 @@ void free_all(gabp_ctx *c) {
     c->stream = nullptr;
 }
 
-size_t tsize(const gabp_ctx *c) { return c->p.prec ? sizeof(double) : sizeof(float); }
 
 // Host set-up work in parallel chunks: chunk ch of nchunk covers [ch * count / nchunk, ...); the
 // results of every caller below do not depend on the number of chunks.
@@ -835,6 +870,31 @@ int gabp_reset(gabp_ctx *c) {
     int rc = init_messages(c);
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream), "reset sync");
+    return GABP_OK;
+}
+
+int gabp_set_prior_mean(gabp_ctx *c, const double *f_b) {
+    if (!c) return GABP_ERR_ARG;
+    if (c->p.order == 2) return fail(c, GABP_ERR_STATE, "a prior mean is not available for the alpha = 4 prior");
+    DeviceGuard g(c->dev);
+    if (!g.ok) return fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
+    const int64_t n = c->p.n;
+    int rc;
+    if (f_b) {
+        if ((rc = alloc_targets(c))) return rc;
+        if (!c->fb) {
+            void *q;
+            if ((rc = dalloc(c, &q, (size_t)n * sizeof(double), "alloc prior mean"))) return rc;
+            c->fb = (double *)q;
+        }
+        CK(cudaMemcpyAsync(c->fb, f_b, (size_t)n * sizeof(double), cudaMemcpyDefault, c->stream), "copy prior mean");
+    } else {
+        c->fb = nullptr;   // the buffer stays allocated with the context (freed at destroy)
+    }
+    if ((rc = set_targets(c))) return rc;
+    CK(gabp::launch_rhs_norm(c->p, c->stream), "rhs norm");
+    CK(cudaStreamSynchronize(c->stream), "prior mean sync");
+    c->last_res = NAN;
     return GABP_OK;
 }
 
@@ -1640,6 +1700,7 @@ int gabp_mg_create(gabp_mg **out, gabp_ctx *ctx, int levels) {
     *out = nullptr;
     if (levels < 2 || levels > GABP_MG_MAX_LEVELS) return fail(ctx, GABP_ERR_ARG, "levels must be in [2, 16]");
     if (ctx->p.order == 2) return fail(ctx, GABP_ERR_STATE, "multigrid is not available for the alpha = 4 prior");
+    if (ctx->fb) return fail(ctx, GABP_ERR_STATE, "multigrid levels are built for a zero prior mean");
     const int nx = ctx->p.nx, ny = ctx->p.ny;
     const int64_t m = ctx->p.m;
     for (int k = 1; k < levels; ++k) {
@@ -1817,6 +1878,7 @@ int gabp_pw_create(gabp_pw **out, gabp_ctx *ctx) {
     if (!out || !ctx) return GABP_ERR_ARG;
     *out = nullptr;
     if (ctx->p.order == 2) return fail(ctx, GABP_ERR_STATE, "the pairwise form is built for the alpha = 2 prior only");
+    if (ctx->fb) return fail(ctx, GABP_ERR_STATE, "the pairwise form is built for a zero prior mean");
     gabp_pw *w = new (std::nothrow) gabp_pw();
     if (!w) return GABP_ERR_OOM;
     w->ctx = ctx;

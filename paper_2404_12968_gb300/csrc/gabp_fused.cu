@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(FT) k_fused(DevProblem p, int src, T beta) {
             }
         }
         T L[5], E[5];
-        factor_messages<T, 5>(a, var_prior, T(0), lam, eta, L, E);
+        const T r = p.ptgt ? ((const T *)p.ptgt)[c] : T(0);
+        factor_messages<T, 5>(a, var_prior, r, lam, eta, L, E);
 #pragma unroll
         for (int u = 0; u < 5; ++u) {
             T2<T> out;

@@ -243,12 +243,12 @@ __device__ __forceinline__ float2 damp2(float2 old, float2 fresh, float2 beta2) 
 // streaming store of the five outgoing messages (planes n apart).  Slots with a = 0 (missing
 // neighbours at the grid border) send (0, 0).
 __device__ __forceinline__ void cell_factor(const float (&a)[5], const Belief2 *const (&bs)[5], const float2 (&own)[5],
-                                            float var, float2 beta2, float2 *q, int64_t n) {
+                                            float var, float r, float2 beta2, float2 *q, int64_t n) {
     float2 cav[5];
 #pragma unroll
     for (int u = 0; u < 5; ++u) cav[u] = a[u] != 0.f ? cavity2(*bs[u], own[u]) : f2(0.f, 1.f);
     float2 msg[5];
-    factor_messages2<5>(a, var, 0.f, cav, msg);
+    factor_messages2<5>(a, var, r, cav, msg);
 #pragma unroll
     for (int u = 0; u < 5; ++u) __stcs(q + u * n, a[u] != 0.f ? damp2(own[u], msg[u], beta2) : f2(0.f, 0.f));
 }
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                 // (corners 3, 2); the first message of each range is loaded before the prior
                 // sums, so that its latency overlaps them (the order of the sum is unchanged)
                 int lo1 = 0, mid1 = 0, hi1 = 0, lo2 = 0, mid2 = 0, hi2 = 0;
-                float2 first1 = f2(0.f, 0.f), first2 = f2(0.f, 0.f);
+                float2 first1 = f2(0.f, 0.f), first2 = f2(0.f, 0.f), second1 = f2(0.f, 0.f), second2 = f2(0.f, 0.f);
                 if (m > 0) {
                     const bool last = gx == nx - 1;
                     mid1 = wptr(gx, gy);
@@ -474,9 +474,17 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                         const int c = lo1 < mid1 ? 1 : 0;
                         first1 = *reinterpret_cast<const float2 *>(O + 8 * (int64_t)lo1 + 2 * c);
                     }
+                    if (lo1 + 1 < hi1) {
+                        const int c = lo1 + 1 < mid1 ? 1 : 0;
+                        second1 = *reinterpret_cast<const float2 *>(O + 8 * (int64_t)(lo1 + 1) + 2 * c);
+                    }
                     if (lo2 < hi2) {
                         const int c = lo2 < mid2 ? 3 : 2;
                         first2 = *reinterpret_cast<const float2 *>(O + 8 * (int64_t)lo2 + 2 * c);
+                    }
+                    if (lo2 + 1 < hi2) {
+                        const int c = lo2 + 1 < mid2 ? 3 : 2;
+                        second2 = *reinterpret_cast<const float2 *>(O + 8 * (int64_t)(lo2 + 1) + 2 * c);
                     }
                 }
                 CompSum2 s(sm[(DIR_C * RY + ry) * RX + rx]);
@@ -487,11 +495,17 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                 s.add(sm[(DIR_S * RY + ry + 1) * RX + rx]);
                 if (lo1 < hi1) {
                     s.add(first1);
-                    add_obs_pair2(s, O, lo1 + 1, mid1, hi1, 1, 0);
+                    if (lo1 + 1 < hi1) {
+                        s.add(second1);
+                        add_obs_pair2(s, O, lo1 + 2, mid1, hi1, 1, 0);
+                    }
                 }
                 if (lo2 < hi2) {
                     s.add(first2);
-                    add_obs_pair2(s, O, lo2 + 1, mid2, hi2, 3, 2);
+                    if (lo2 + 1 < hi2) {
+                        s.add(second2);
+                        add_obs_pair2(s, O, lo2 + 2, mid2, hi2, 3, 2);
+                    }
                 }
                 s.finish();
                 b.hi = s.hi;
@@ -534,14 +548,15 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
             float2 own[5];
 #pragma unroll
             for (int u = 0; u < 5; ++u) own[u] = sm[(u * RY + ty + 2) * RX + tx + 2];
+            const float tg = cur.ptgt ? ((const float *)cur.ptgt)[c] : 0.f;   // the cell factor's target
             if (gx > 0 && gx < nx - 1 && gy > 0 && gy < ny - 1) {
                 // interior cell: literal coefficients, so the compiler folds the -1 factors
                 const float a[5] = {aC_in, -1.f, -1.f, -1.f, -1.f};
-                cell_factor(a, bs, own, var_prior, beta2, Q + c, n);
+                cell_factor(a, bs, own, var_prior, tg, beta2, Q + c, n);
             } else {
                 const float a[5] = {cur.aC_f[grid_degree(gy, gx, nx, ny)], gx > 0 ? -1.f : 0.f,
                                     gx < nx - 1 ? -1.f : 0.f, gy > 0 ? -1.f : 0.f, gy < ny - 1 ? -1.f : 0.f};
-                cell_factor(a, bs, own, var_prior, beta2, Q + c, n);
+                cell_factor(a, bs, own, var_prior, tg, beta2, Q + c, n);
             }
         }
         if (m > 0) {

@@ -44,6 +44,13 @@ struct DevProblem {
     int debug_stall;     // test hook: the TMA kernel first waits on a barrier nothing completes
     int order;           // prior operator: 1 = L (alpha = 2, 5-slot cell factors), 2 = L^2 (alpha = 4)
     int planes;          // prior message planes: 5 (order 1) or 13 (order 2)
+    // targets r_c of the cell factors exp(-(gamma / 2) (l_c . f - r_c)^2), r = L f_b for a prior
+    // mean f_b (NULL: every target is zero, the zero prior mean): in the message precision for
+    // the iteration kernels, in FP64 for the residual and ||b||, and as double-float pairs for
+    // the residual of FP32 contexts
+    const void *ptgt;
+    const double *ptgt64;
+    const float2 *ptgtdf;
 };
 
 // Prior constants in the kernel's precision.  FP32 kernels read the values rounded once on the
@@ -119,6 +126,12 @@ cudaError_t launch_msg_change(const DevProblem &p, int cur, double *out, cudaStr
 cudaError_t launch_df_precompute(const DevProblem &p, cudaStream_t st);
 cudaError_t launch_ws_decode(const DevProblem &p, double scale, int Wp, const float *out, double *mu0, double *lam0,
                              cudaStream_t st);
+// ---- prior mean (gabp_split.cu) ----
+// cell-factor targets t = L d (d: n doubles; NULL = zero) into t64 (FP64), tT (message
+// precision) and, for FP32 contexts, tdf (double-float pairs)
+cudaError_t launch_cell_targets(const DevProblem &p, const double *d, double *t64, void *tT, float2 *tdf,
+                                cudaStream_t st);
+
 
 // ---- fused path (gabp_fused.cu) ----
 struct FusedShape {

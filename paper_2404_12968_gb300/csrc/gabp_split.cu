@@ -103,7 +103,8 @@ template <typename T> __global__ void k_prior(DevProblem p, int src, T beta) {
         }
     }
     T L[5], E[5];
-    factor_messages<T, 5>(a, prior_var<T>(p), T(0), lam, eta, L, E);
+    const T r = p.ptgt ? ((const T *)p.ptgt)[c] : T(0);
+    factor_messages<T, 5>(a, prior_var<T>(p), r, lam, eta, L, E);
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
         T2<T> out;
@@ -469,7 +470,19 @@ __device__ __forceinline__ double obs_gather64(const DevProblem &p, int64_t v, i
     return acc;
 }
 
-// ||b||^2 with b_v = sum over incoming observation edges of w * s * y
+// (L x)_v = (kappa^2 + deg) x_v - sum of existing neighbours
+__device__ __forceinline__ double apply_L(const DevProblem &p, const double *x, int64_t v, int i, int j) {
+    const int nx = p.nx, ny = p.ny;
+    double s = p.aC[grid_degree(i, j, nx, ny)] * x[v];
+    if (j > 0) s -= x[v - 1];
+    if (j < nx - 1) s -= x[v + 1];
+    if (i > 0) s -= x[v - nx];
+    if (i < ny - 1) s -= x[v + nx];
+    return s;
+}
+
+// ||b||^2 with b_v = sum over incoming observation edges of w * s * y, plus gamma (L r)_v for
+// cell-factor targets r
 __global__ void k_rhs_norm(DevProblem p) {
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
@@ -489,6 +502,7 @@ __global__ void k_rhs_norm(DevProblem p) {
             if (i > 0 && j > 0)
                 for (int k = o[v - nx - 1]; k < o[v - nx]; ++k) bv += p.ow64[4 * (int64_t)k + 3] * p.oys64[2 * (int64_t)k] * p.oys64[2 * (int64_t)k + 1];
         }
+        if (p.ptgt64) bv += p.gamma * apply_L(p, p.ptgt64, v, i, j);   // gamma L^T r (L symmetric)
         acc += bv * bv;
     }
     double s = block_sum(acc);
@@ -586,7 +600,9 @@ __global__ void k_Lmu_df(DevProblem p) {
     if (v >= p.n) return;
     int i, j;
     node_rc(v, p.nx, i, j);
-    df_st((float2 *)p.z64, v, apply_L_df(p, (const float2 *)p.mu64, v, i, j));
+    dfl z = apply_L_df(p, (const float2 *)p.mu64, v, i, j);
+    if (p.ptgtdf) z = df_add(z, df_neg(df_ld(p.ptgtdf, v)));   // l_v . mu - r_v
+    df_st((float2 *)p.z64, v, z);
 }
 
 // partial sums of r_v^2, r = b - A mu = -gamma L (L mu) - H^T (s (H mu - y)); per-thread sums in
@@ -636,17 +652,6 @@ __global__ void k_obs_err(DevProblem p) {
     p.e64[k] = p.oys64[2 * k + 1] * (hm - p.oys64[2 * k]);
 }
 
-// (L x)_v = (kappa^2 + deg) x_v - sum of existing neighbours
-__device__ __forceinline__ double apply_L(const DevProblem &p, const double *x, int64_t v, int i, int j) {
-    const int nx = p.nx, ny = p.ny;
-    double s = p.aC[grid_degree(i, j, nx, ny)] * x[v];
-    if (j > 0) s -= x[v - 1];
-    if (j < nx - 1) s -= x[v + 1];
-    if (i > 0) s -= x[v - nx];
-    if (i < ny - 1) s -= x[v + nx];
-    return s;
-}
-
 // y = L x (FP64); the alpha = 4 residual applies L four times
 __global__ void k_Lx(DevProblem p, const double *x, double *y) {
     const int64_t v = gtid();
@@ -661,7 +666,9 @@ __global__ void k_Lmu(DevProblem p) {
     if (v >= p.n) return;
     int i, j;
     node_rc(v, p.nx, i, j);
-    p.z64[v] = apply_L(p, p.mu64, v, i, j);
+    double z = apply_L(p, p.mu64, v, i, j);
+    if (p.ptgt64) z -= p.ptgt64[v];   // l_v . mu - r_v
+    p.z64[v] = z;
 }
 
 // r = b - A mu = -gamma L (L mu) - H^T S (H mu - y); accumulate ||r||^2
@@ -1061,6 +1068,27 @@ cudaError_t launch_marginals(const DevProblem &p, int src, double *mean, double 
     if (e != cudaSuccess) return e;
     if (p.prec) k_marg<double><<<nblocks(p.n), TPB, 0, st>>>(p, mean, var);
     else k_marg<float><<<nblocks(p.n), TPB, 0, st>>>(p, mean, var);
+    return cudaGetLastError();
+}
+
+
+// ---- prior mean ----
+// t = L d (FP64), rounded to the message precision and (FP32 contexts) split into double-float
+template <typename T> __global__ void k_cell_targets(DevProblem p, const double *d, double *t64, T *tT, float2 *tdf) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    int i, j;
+    node_rc(v, p.nx, i, j);
+    const double t = d ? apply_L(p, d, v, i, j) : 0.0;
+    t64[v] = t;
+    tT[v] = (T)t;
+    if (tdf) df_st(tdf, v, df_split(t));
+}
+
+cudaError_t launch_cell_targets(const DevProblem &p, const double *d, double *t64, void *tT, float2 *tdf,
+                                cudaStream_t st) {
+    if (p.prec == 0) k_cell_targets<float><<<nblocks(p.n), TPB, 0, st>>>(p, d, t64, (float *)tT, tdf);
+    else k_cell_targets<double><<<nblocks(p.n), TPB, 0, st>>>(p, d, t64, (double *)tT, nullptr);
     return cudaGetLastError();
 }
 

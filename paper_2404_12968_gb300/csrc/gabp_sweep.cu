@@ -165,7 +165,7 @@ struct WarpRing {
 // Damped messages of the cell factor (x, r).  `a` holds the row of L for this cell (literal
 // -1 entries let the compiler fold the generic update for interior cells; the arithmetic is
 // the same either way).
-__device__ __forceinline__ void cell_factor(const float (&a)[5], float var_prior, float beta,
+__device__ __forceinline__ void cell_factor(const float (&a)[5], float var_prior, float r, float beta,
                                             const Row5 &own, const Belief<float> *const (&bs)[5],
                                             float2 *Q, int64_t n, int64_t c) {
     float lam[5], eta[5];
@@ -179,7 +179,7 @@ __device__ __forceinline__ void cell_factor(const float (&a)[5], float var_prior
         }
     }
     float L[5], E[5];
-    factor_messages<float, 5>(a, var_prior, 0.f, lam, eta, L, E);
+    factor_messages<float, 5>(a, var_prior, r, lam, eta, L, E);
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
         float2 out;
@@ -307,14 +307,15 @@ __device__ __forceinline__ void sweep_strip(const DevProblem &p, WarpRing &ring,
         if (owned) {
             const Belief<float> *const bs[5] = {&b_cur, &b_w, &b_e, &b_prev, &b_next};
             const int64_t c = (int64_t)r * nx + x;
+            const float tg = p.ptgt ? ((const float *)p.ptgt)[c] : 0.f;
             if (x_inner && r > 0 && r < ny - 1) {
                 const float a[5] = {aC_in, -1.f, -1.f, -1.f, -1.f};
-                cell_factor(a, var_prior, beta, s_0.msg, bs, Q, n, c);
+                cell_factor(a, var_prior, tg, beta, s_0.msg, bs, Q, n, c);
             } else {
                 const int deg = grid_degree(r, x, nx, ny);
                 const float a[5] = {p.aC_f[deg], x > 0 ? -1.f : 0.f, x < nx - 1 ? -1.f : 0.f,
                                     r > 0 ? -1.f : 0.f, r < ny - 1 ? -1.f : 0.f};
-                cell_factor(a, var_prior, beta, s_0.msg, bs, Q, n, c);
+                cell_factor(a, var_prior, tg, beta, s_0.msg, bs, Q, n, c);
             }
         }
         if (p.m > 0 && ((r - y0) % OBS_BATCH == OBS_BATCH - 1 || r == y1 - 1)) {

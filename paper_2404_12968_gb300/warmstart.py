@@ -89,9 +89,10 @@ PW_C, PW_ETA = 20.0, 0.6   # the paper's pairwise form (its c = 10 diverges on t
 PW_CHECK, PW_MAX = 500, 12000
 
 
-def pairwise_to_tol(solver: Solver, tol: float = TOL):
+def pairwise_to_tol(solver: Solver, tol: float = TOL, means: dict | None = None):
     """The paper's pairwise re-weighted form from zero messages: residual checked every
-    PW_CHECK iterations, at most PW_MAX; (seconds, iterations, residual)."""
+    PW_CHECK iterations, at most PW_MAX; (seconds, iterations, residual).  With ``means`` given,
+    the final marginal means are stored under "pairwise"."""
     with Pairwise(solver) as pw:
         pw.iterate(2, PW_C, PW_ETA)    # warm-up launch
         pw.reset()
@@ -103,7 +104,10 @@ def pairwise_to_tol(solver: Solver, tol: float = TOL):
             r = pw.residual()
             if not r > tol:
                 break
-        return time.perf_counter() - t0, its, r
+        dt = time.perf_counter() - t0
+        if means is not None:
+            means["pairwise"] = pw.marginals(want_var=False)[0]
+        return dt, its, r
 
 
 def time_to_tol(solver: Solver, net: WarmStartNet | None, tol: float = TOL, check_every: int = 10, mg=None):
@@ -123,7 +127,10 @@ def time_to_tol(solver: Solver, net: WarmStartNet | None, tol: float = TOL, chec
     return dt, int(st["iterations"]), float(st["last_residual"]), coarse
 
 
-def evaluate(net: WarmStartNet, problem=None, device: int = 0, repeats: int = 3):
+def evaluate(net: WarmStartNet, problem=None, device: int = 0, repeats: int = 3, means: dict | None = None):
+    """Time to TOL from the cold start, the learned warm start, the multigrid warm start and the
+    pairwise form.  With ``means`` given, the final marginal means of each ("cold", "warm",
+    "multigrid", "pairwise") are stored there (read after the timed runs)."""
     p = problem if problem is not None else gabp_synth.config_warm_eval(0)
     with Solver(p, precision="fp32", tol=TOL, check_every=10, max_iters=400000, device=device) as s:
         with Multigrid(s, MG_LEVELS) as mg:      # the coarse problem is set up once, like the solver
@@ -131,9 +138,15 @@ def evaluate(net: WarmStartNet, problem=None, device: int = 0, repeats: int = 3)
             time_to_tol(s, net)
             time_to_tol(s, None, mg=mg)
             cold = [time_to_tol(s, None) for _ in range(repeats)]
+            if means is not None:
+                means["cold"] = s.marginals(want_var=False)[0]
             warm = [time_to_tol(s, net) for _ in range(repeats)]
+            if means is not None:
+                means["warm"] = s.marginals(want_var=False)[0]
             mgr = [time_to_tol(s, None, mg=mg) for _ in range(repeats)]
-        pw_s, pw_its, pw_res = pairwise_to_tol(s)
+            if means is not None:
+                means["multigrid"] = s.marginals(want_var=False)[0]
+        pw_s, pw_its, pw_res = pairwise_to_tol(s, means=means)
     best = lambda r: min(r, key=lambda z: z[0])  # noqa: E731
     c, w, g = best(cold), best(warm), best(mgr)
     return {"grid": [p.nx, p.ny], "kappa": p.kappa, "m": p.m, "tol": TOL, "damping": DAMPING,

@@ -52,3 +52,45 @@ def sorted_obs_order(orc, p: gabp_synth.Problem):
     i0, j0, w = orc.bilinear_base_weights(p.nx, p.ny, p.obs_x, p.obs_y)
     base = i0 * p.nx + j0
     return np.argsort(base, kind="stable"), base, w
+
+
+def golden_writer():
+    """``tests/golden/make_exact_means.py``, the script that wrote the stored exact means (the
+    oracle alone), loaded as a module for its reader and its list of stored batch instances."""
+    import importlib.util
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "make_exact_means.py")
+    spec = importlib.util.spec_from_file_location("make_exact_means", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def load_exact_sample(name: str) -> dict:
+    """A stored exact posterior mean at sampled nodes (``tests/golden/exact_mean_<name>.txt``)."""
+    return golden_writer().load(name)
+
+
+def same_inputs_as_sample(p: gabp_synth.Problem, g: dict) -> bool:
+    """The problem the generator made here is the one the stored sample was solved for."""
+    sums = {"sum_obs_x": p.obs_x, "sum_obs_y": p.obs_y, "sum_y": p.y, "sum_noise_var": p.noise_var}
+    ok = p.nx == g["nx"] and p.ny == g["ny"] and p.m == g["m"] and abs(p.kappa - g["kappa"]) == 0.0
+    for k, v in sums.items():
+        ok = ok and abs(float(np.sum(v)) - g[k]) <= 1e-12 * max(1.0, abs(g[k]))
+    return bool(ok)
+
+
+def iterate_to_floor(step, residual, chunk: int, max_iters: int):
+    """Iterate in chunks until the FP64 relative residual stops halving from one chunk to the
+    next (the rounding floor of the message precision) or ``max_iters`` pass; returns the last
+    residual and the iteration count."""
+    best = np.inf
+    its = 0
+    res = np.inf
+    while its < max_iters:
+        step(chunk)
+        its += chunk
+        res = residual()
+        if not res < 0.5 * best:
+            break
+        best = res
+    return res, its

@@ -61,3 +61,4 @@ def test_targets_are_rows_of_L_times_the_mean(orc):
             for a, b in nb:
                 L[v, a * nx + b] = -1.0
     np.testing.assert_allclose(pf.r, L @ fb, rtol=1e-12, atol=1e-11)
+
