@@ -399,6 +399,11 @@ int64_t gabp_pw_iterations(const gabp_pw *pw);
  *   the call the change is the reference; stop after the first t >= 3 whose change is below
  *   tau times it (*stopped_at = t).  GABP_ERR_TIMEOUT after max_iters (>= 3), GABP_ERR_DIVERGED
  *   if a change is not finite.
+ * gabp_pw_iterate_early_stop_ref: the same rule with the reference given: reference > 0 is
+ *   compared against instead of this call's own change between its iterations 1 and 2 (App. B
+ *   names m_1 and m_2 without a level; a multigrid driver can pass every level the coarsest
+ *   level's change); reference <= 0 is gabp_pw_iterate_early_stop.  *reference_used (may be
+ *   NULL) receives the reference the rule compared against.
  * gabp_pw_upscale: "Upscale Messages": fine's messages = coarse's current messages on the same
  *   directions, node (i, j) of fine taking those of (floor(i/2), floor(j/2)) of coarse (clamped
  *   to its grid), (0, 0) where either level lacks the pair; same precision and device;
@@ -406,6 +411,8 @@ int64_t gabp_pw_iterations(const gabp_pw *pw);
 int gabp_pw_message_change(gabp_pw *pw, double *mean_abs_change);
 int gabp_pw_iterate_early_stop(gabp_pw *pw, int max_iters, double c, double learning_rate, double tau,
                                int64_t *stopped_at);
+int gabp_pw_iterate_early_stop_ref(gabp_pw *pw, int max_iters, double c, double learning_rate, double tau,
+                                   double reference, int64_t *stopped_at, double *reference_used);
 int gabp_pw_upscale(gabp_pw *fine, const gabp_pw *coarse);
 const char *gabp_pw_last_error(const gabp_pw *pw);
 void gabp_pw_destroy(gabp_pw *pw);

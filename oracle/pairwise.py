@@ -109,17 +109,22 @@ def message_change(new, old) -> float:
     return float((da.sum() + db.sum()) / (da.size + db.size))
 
 
-def run_early_stop(P, h, c: float, eta: float, tau: float, max_iters: int, messages=None):
+def run_early_stop(P, h, c: float, eta: float, tau: float, max_iters: int, messages=None, ref=None,
+                   out_ref=None):
     """Iterate one level under the early-stopping rule (App. B).  Returns (t, mean, precision,
     messages, finite): t = the stopping iteration (None if max_iters came first or the run
-    stopped being finite)."""
+    stopped being finite).  The reference change is mean |m_2 - m_1| of this run's first two
+    iterations, or ``ref`` when given; ``out_ref`` (a list) receives the reference used."""
     E = edges(P)
     msg = messages if messages is not None else (np.zeros(E[0].size), np.zeros(E[0].size))
     _, _, m1, ok1 = run(P, h, c, eta, 1, messages=msg, E=E)
     mean, prec, m2, ok2 = run(P, h, c, eta, 1, messages=m1, E=E)
     if not (ok1 and ok2):
         return None, mean, prec, m2, False
-    ref = message_change(m2, m1)
+    if ref is None:
+        ref = message_change(m2, m1)
+    if out_ref is not None:
+        out_ref.append(ref)
     t, cur = 2, m2
     while t < max_iters:
         prev = cur
@@ -169,13 +174,20 @@ def level_observations(ox, oy, y, noise_var, k: int):
 
 
 def multigrid(nx, ny, kappa, gamma, ox, oy, y, noise_var, levels: int, c: float, eta: float, tau: float,
-              max_iters: int):
+              max_iters: int, reference: str = "level"):
     """Alg. 2: levels - 1 coarse levels and the target, each iterated under the early-stopping
     rule from the upscaled edge values of the level below it (zero on the coarsest).  Returns
-    (mean, precision, stop) on the target grid, stop[k] = the stopping iteration of level k."""
+    (mean, precision, stop) on the target grid, stop[k] = the stopping iteration of level k.
+
+    ``reference`` reads which m_1, m_2 the rule compares against (App. B writes them without a
+    level): "level" = the first two iterations of each level (the reading the library follows),
+    "first" = those of the first, coarsest level, for every level."""
+    if reference not in ("level", "first"):
+        raise ValueError(reference)
     prev = None
     stop = {}
     mean = prec = None
+    first_ref = []
     for k in range(levels - 1, -1, -1):
         s = 1 << k
         nxk, nyk = -(-nx // s), -(-ny // s)
@@ -184,7 +196,9 @@ def multigrid(nx, ny, kappa, gamma, ox, oy, y, noise_var, levels: int, c: float,
         fl = build_factors(nxk, nyk, kappa * s, lox, loy, ly, lv, gamma=gamma / (s * s))
         P, h = assemble(fl)
         msg = None if prev is None else upscale(prev[0], prev[1], prev[2], prev[3], P, nxk, nyk)
-        t, mean, prec, msg, ok = run_early_stop(P, h, c, eta, tau, max_iters, msg)
+        ref = first_ref[0] if (reference == "first" and first_ref) else None
+        t, mean, prec, msg, ok = run_early_stop(P, h, c, eta, tau, max_iters, msg, ref=ref,
+                                                out_ref=first_ref if not first_ref else None)
         stop[k] = t
         prev = (msg, P, nxk, nyk)
     return mean, prec, stop

@@ -364,11 +364,18 @@ class Pairwise:
         return d.value
 
     def iterate_early_stop(self, max_iters: int, c: float = 10.0, learning_rate: float = 0.6,
-                           tau: float = 1e-3) -> int:
-        """Iterate under the early-stopping rule (App. B); returns the stopping iteration."""
+                           tau: float = 1e-3, reference: float | None = None) -> int:
+        """Iterate under the early-stopping rule (App. B); returns the stopping iteration.
+        ``reference`` (> 0) replaces this call's own change between its iterations 1 and 2;
+        the reference the rule used is left in ``self.reference_used``."""
         t = ctypes.c_int64()
-        _pcheck(_lib.load().gabp_pw_iterate_early_stop(self.handle, int(max_iters), float(c), float(learning_rate),
-                                                        float(tau), ctypes.byref(t)), self.handle)
+        used = ctypes.c_double()
+        used.value = float("nan")
+        rc = _lib.load().gabp_pw_iterate_early_stop_ref(self.handle, int(max_iters), float(c), float(learning_rate),
+                                                        float(tau), float(reference or 0.0), ctypes.byref(t),
+                                                        ctypes.byref(used))
+        self.reference_used = used.value     # set once iterations 1 and 2 ran, also on a timeout
+        _pcheck(rc, self.handle)
         return t.value
 
     def upscale_from(self, coarse: "Pairwise") -> None:

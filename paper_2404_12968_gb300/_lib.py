@@ -117,6 +117,10 @@ def load():
     L.gabp_pw_iterate_early_stop.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              ctypes.POINTER(ctypes.c_int64)]
     L.gabp_pw_iterate_early_stop.restype = ctypes.c_int
+    L.gabp_pw_iterate_early_stop_ref.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.POINTER(ctypes.c_int64),
+                                                 ctypes.POINTER(ctypes.c_double)]
+    L.gabp_pw_iterate_early_stop_ref.restype = ctypes.c_int
     L.gabp_pw_upscale.argtypes = [_vp, _vp]
     L.gabp_pw_upscale.restype = ctypes.c_int
     L.gabp_pw_last_error.argtypes = [_vp]

@@ -1979,16 +1979,19 @@ int gabp_pw_message_change(gabp_pw *w, double *out) {
     return GABP_OK;
 }
 
-int gabp_pw_iterate_early_stop(gabp_pw *w, int max_iters, double c, double learning_rate, double tau,
-                               int64_t *stopped_at) {
+int gabp_pw_iterate_early_stop_ref(gabp_pw *w, int max_iters, double c, double learning_rate, double tau,
+                                   double reference, int64_t *stopped_at, double *reference_used) {
     if (!w) return GABP_ERR_ARG;
     if (!(tau > 0.0) || max_iters < 3) return pfail(w, GABP_ERR_ARG, "tau > 0 and max_iters >= 3 required");
+    if (!std::isfinite(reference)) return pfail(w, GABP_ERR_ARG, "reference must be finite");
     if (stopped_at) *stopped_at = 0;
     int rc = gabp_pw_iterate(w, 2, c, learning_rate);
     if (rc) return rc;
     double ref = 0.0, d = 0.0;
     if ((rc = gabp_pw_message_change(w, &ref))) return rc;
     if (!std::isfinite(ref)) return pfail(w, GABP_ERR_DIVERGED, "message change is not finite");
+    if (reference > 0.0) ref = reference;
+    if (reference_used) *reference_used = ref;
     for (int64_t t = 2;;) {
         if (t >= max_iters) return pfail(w, GABP_ERR_TIMEOUT, "max_iters reached before the early-stopping rule held");
         if ((rc = gabp_pw_iterate(w, 1, c, learning_rate))) return rc;
@@ -2000,6 +2003,11 @@ int gabp_pw_iterate_early_stop(gabp_pw *w, int max_iters, double c, double learn
             return GABP_OK;
         }
     }
+}
+
+int gabp_pw_iterate_early_stop(gabp_pw *w, int max_iters, double c, double learning_rate, double tau,
+                               int64_t *stopped_at) {
+    return gabp_pw_iterate_early_stop_ref(w, max_iters, c, learning_rate, tau, 0.0, stopped_at, nullptr);
 }
 
 int gabp_pw_upscale(gabp_pw *fine, const gabp_pw *coarse) {

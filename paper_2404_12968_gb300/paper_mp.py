@@ -42,13 +42,20 @@ def level_observations(obs_x, obs_y, y, noise_var, k: int):
 
 def solve(problem, *, c: float = 10.0, learning_rate: float = 0.6, tau: float = 1e-3, levels: int | None = None,
           base: int = 32, max_iters: int = 10000, precision: str = "fp32", gamma: float | None = None,
-          device: int = 0):
+          device: int = 0, reference: str = "level"):
     """Run Alg. 2 on a problem with grid-point observations.  Returns (mean, variance, stops)
-    with stops[k] the stopping iteration of level k (max_iters where the rule did not hold)."""
+    with stops[k] the stopping iteration of level k (max_iters where the rule did not hold).
+
+    ``reference`` reads which m_1, m_2 the early-stopping rule (App. B) compares against:
+    "level" = the first two iterations of each level, "first" = those of the coarsest level,
+    passed on to every finer level."""
+    if reference not in ("level", "first"):
+        raise ValueError(reference)
     nx, ny = int(problem.nx), int(problem.ny)
     g = float(gamma if gamma is not None else getattr(problem, "gamma", 1.0))
     L = levels if levels is not None else level_count(nx, ny, base)
     stops = {}
+    first_ref = None
     prev = None   # (solver, pairwise) of the coarser level
     try:
         for k in range(L - 1, -1, -1):
@@ -63,11 +70,13 @@ def solve(problem, *, c: float = 10.0, learning_rate: float = 0.6, tau: float = 
                 prev[1].close()
                 prev[0].close()
             try:
-                stops[k] = pw.iterate_early_stop(max_iters, c, learning_rate, tau)
+                stops[k] = pw.iterate_early_stop(max_iters, c, learning_rate, tau, first_ref)
             except GabpError as e:
                 if e.code != GABP_ERR_TIMEOUT:
                     raise
                 stops[k] = max_iters
+            if reference == "first" and first_ref is None:
+                first_ref = pw.reference_used
             prev = (sol, pw)
         mean, var = prev[1].marginals()
         return mean, var, stops

@@ -188,3 +188,18 @@ def test_papers_algorithm_matches_oracle(orc, prec, tol):
     if prec == "fp64":
         assert stop == stop_o
     assert rel_l2(mean, mean_o) < tol
+
+
+def test_papers_algorithm_first_level_reference_matches_oracle(orc):
+    """Alg. 2 under the other reading of App. B's reference change (every level compares with
+    the coarsest level's change between its first two iterations): stopping iterations and
+    the final mean equal the oracle's under the same reading (FP64)."""
+    from paper_2404_12968_gb300 import paper_mp
+    p = gabp_synth.paper_synthetic(64, 0.1, 3)
+    mean_o, _, stop_o = opw.multigrid(p.nx, p.ny, p.kappa, p.gamma, p.obs_x, p.obs_y, p.y, p.noise_var,
+                                      3, 10.0, 0.6, 1e-3, 10000, reference="first")
+    mean, _, stop = paper_mp.solve(p, levels=3, precision="fp64", reference="first")
+    assert stop == stop_o
+    assert rel_l2(mean, mean_o) < 1e-10
+    _, _, stop_l = paper_mp.solve(p, levels=3, precision="fp64")
+    assert stop_l[2] == stop[2]          # the coarsest level is the same under both readings

@@ -174,3 +174,40 @@ def test_multigrid_levels_and_fixed_point():
     exact = oracle.exact_mean(fl, p.nx)
     assert all(t is not None for t in stop.values())
     assert np.linalg.norm(mean - exact) / np.linalg.norm(exact) < 1e-6
+
+
+def test_multigrid_reference_change_readings():
+    """App. B writes the rule's m_1, m_2 without a level.  Reading "level" (the library's): each
+    level compares with the change between its own first two iterations.  Reading "first": every
+    level compares with that change of the coarsest level.  Checked by hand: the coarsest level
+    stops at the same iteration under both, and each finer level under "first" stops at the
+    first iteration whose change, from the upscaled start, is below tau times the coarsest
+    level's reference (a step-by-step run of the same level)."""
+    p = gabp_synth.paper_synthetic(32, 0.1, 2)
+    args = (p.nx, p.ny, p.kappa, p.gamma, p.obs_x, p.obs_y, p.y, p.noise_var, 2, 10.0, 0.6, 1e-3, 20000)
+    _, _, stop_l = pw.multigrid(*args, reference="level")
+    mean_f, _, stop_f = pw.multigrid(*args, reference="first")
+    assert stop_l[1] == stop_f[1] and stop_f[0] is not None
+    # by hand: the coarse level (k = 1) and its reference, then the fine level from the upscaled
+    # edges, one iteration at a time
+    lox, loy, ly, lv = pw.level_observations(p.obs_x, p.obs_y, p.y, p.noise_var, 1)
+    nxc, nyc = -(-p.nx // 2), -(-p.ny // 2)
+    flc = oracle.build_factors(nxc, nyc, p.kappa * 2, lox, loy, ly, lv, gamma=p.gamma / 4)
+    Pc, hc = pw.assemble(flc)
+    msgs = [(np.zeros(pw.edges(Pc)[0].size),) * 2]
+    for _ in range(stop_l[1]):
+        msgs.append(pw.run(Pc, hc, 10.0, 0.6, 1, messages=msgs[-1])[2])
+    ref = pw.message_change(msgs[2], msgs[1])
+    flf = oracle.build_factors(p.nx, p.ny, p.kappa, p.obs_x, p.obs_y, p.y, p.noise_var, gamma=p.gamma)
+    Pf, hf = pw.assemble(flf)
+    cur = pw.upscale(msgs[-1], Pc, nxc, nyc, Pf, p.nx, p.ny)
+    t = 0
+    while True:
+        nxt = pw.run(Pf, hf, 10.0, 0.6, 1, messages=cur)[2]
+        t += 1
+        if t >= 3 and pw.message_change(nxt, cur) < 1e-3 * ref:
+            break
+        cur = nxt
+        assert t < 20000
+    assert t == stop_f[0]
+    assert np.all(np.isfinite(mean_f))
