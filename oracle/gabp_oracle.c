@@ -51,31 +51,36 @@ int orc_version(void) { return 1; }
  *     V_v = 1/s + sum_{u != v} a_u^2 / lam_c[u]          (variance of a_v x_v - r given the rest)
  *     m_v = r - sum_{u != v} a_u * eta_c[u] / lam_c[u]  (its mean)
  *     Lambda_out[v] = a_v^2 / V_v,   eta_out[v] = a_v * m_v / V_v.
- * Slots with a_u = 0 are skipped.  A slot u != v with a_u != 0 whose cavity precision is
- * below the smallest normal double (non-positive, or so small that 1/lam_c overflows) carries
- * no information about x_u, so V_v is infinite and the message is (0, 0).  (Such cavities do
- * occur: away from the observations the precision recursion can drive the neighbour-slot
- * messages of the cell factors geometrically towards zero.)
+ * Slots with a_u = 0 are skipped.
+ *
+ * A cavity of (near) zero precision.  Away from the observations the precision recursion
+ * drives some cavity precisions geometrically towards zero while their information stays
+ * finite: the cavity tends to the linear potential exp(eta_u x_u).  Integrating the factor
+ * against it over x_u (substitute z = a_u x_u + sum_{w != u} a_w x_w - r) leaves
+ * exp(-(eta_u / a_u) sum_{w != u} a_w x_w) up to a constant, so the message to every other
+ * slot v tends to (eta, Lambda) = (-a_v eta_u / a_u, 0), and the formulas above converge to
+ * it as lam_c[u] -> 0 (the difference is of relative order lam_c[u] V / a_u^2).  A cavity
+ * precision below 1e-20 a_u^2 (zero and negative included) is raised to 1e-20 a_u^2: the
+ * messages are then that limit to a relative 1e-20 V, and no term overflows.  With several
+ * such slots in one factor the messages to the others are the limit along the path where
+ * their precisions shrink in proportion to a_u^2.
  */
+#define ORC_LAM_FLOOR 1e-20
+
 void orc_factor_update(int k, const double *a, double s, double r, const double *lam_c,
                        const double *eta_c, double *lam_out, double *eta_out) {
     for (int v = 0; v < k; ++v) {
         double V = 1.0 / s;
         double mv = r;
-        int infinite = 0;
         for (int u = 0; u < k; ++u) {
             if (u == v || a[u] == 0.0) continue;
-            if (!(lam_c[u] >= DBL_MIN)) { infinite = 1; break; }
-            V += a[u] * a[u] / lam_c[u];
-            mv -= a[u] * (eta_c[u] / lam_c[u]);
+            const double floor_u = ORC_LAM_FLOOR * (a[u] * a[u]);
+            const double lam = lam_c[u] >= floor_u ? lam_c[u] : floor_u;
+            V += a[u] * a[u] / lam;
+            mv -= a[u] * (eta_c[u] / lam);
         }
-        if (infinite) {
-            lam_out[v] = 0.0;
-            eta_out[v] = 0.0;
-        } else {
-            lam_out[v] = a[v] * a[v] / V;
-            eta_out[v] = a[v] * mv / V;
-        }
+        lam_out[v] = a[v] * a[v] / V;
+        eta_out[v] = a[v] * mv / V;
     }
 }
 

@@ -19,11 +19,15 @@ template <> struct vec2<float> { using type = float2; };
 template <> struct vec2<double> { using type = double2; };
 template <typename T> using T2 = typename vec2<T>::type;
 
-// Smallest normal number: a cavity precision below it has an overflowing reciprocal and is
-// treated as carrying no information.
+// Smallest normal number.
 template <typename T> __device__ __forceinline__ T tiny_normal();
 template <> __device__ __forceinline__ float tiny_normal<float>() { return 1.17549435e-38f; }
 template <> __device__ __forceinline__ double tiny_normal<double>() { return 2.2250738585072014e-308; }
+
+// Floor of a cavity precision relative to its slot's a^2 (see factor_messages).
+template <typename T> __device__ __forceinline__ T lam_floor_rel();
+template <> __device__ __forceinline__ float lam_floor_rel<float>() { return 1e-20f; }
+template <> __device__ __forceinline__ double lam_floor_rel<double>() { return 1e-20; }
 
 template <typename T> __device__ __forceinline__ T pos_inf();
 template <> __device__ __forceinline__ float pos_inf<float>() { return __int_as_float(0x7f800000); }
@@ -32,9 +36,9 @@ template <> __device__ __forceinline__ double pos_inf<double>() {
 }
 
 // Reciprocal.  FP32: the hardware approximation rcp.approx.ftz.f32, within 1 ulp over the
-// range the callers use (they never pass 0, a denormal or an infinity: cavities are guarded at
-// the smallest normal number and an infinite V is tested before the call; a result below the
-// smallest normal number flushes to 0).  FP64: IEEE division.
+// range the callers use (they never pass 0, a denormal or an infinity: cavity precisions are
+// floored at a normal number, and V is at least var > 0 and at most about 5e20).  FP64: IEEE
+// division.
 template <typename T> __device__ __forceinline__ T recip(T x);
 template <> __device__ __forceinline__ float recip<float>(float x) {
     float r;
@@ -110,9 +114,13 @@ __device__ __forceinline__ void cavity(const Belief<T> &b, T own_eta, T own_lam,
 //   V_v = var + sum_{u != v} a_u^2 / lam_u,   m_v = r - sum_{u != v} a_u eta_u / lam_u,
 //   Lambda_v = a_v^2 / V_v,                   eta_v = a_v m_v / V_v.
 // Leave-one-out sums come from prefix and suffix sums (no "total minus own" cancellation).
-// Slots with a_u = 0 are skipped; a slot with a_u != 0 whose cavity precision is below the
-// smallest normal number (non-positive, or so small that its reciprocal overflows) carries no
-// information: it makes V infinite for every other slot, whose message is then exactly (0, 0).
+// Slots with a_u = 0 are skipped.  A cavity precision below 1e-20 a_u^2 (zero and negative
+// included; in FP32 also below the smallest normal number) is raised to that floor.  Such a
+// cavity is in the limit lam -> 0 with finite information, the linear potential exp(eta x):
+// the messages to the other slots then equal that limit, (-a_v eta_u / a_u, 0), to a relative
+// 1e-20 V, and nothing overflows.  (Far from the observations the precision recursion drives
+// some cavity precisions far below the FP32 range while their information stays finite;
+// treating them as carrying no information would drop that information.)
 template <typename T, int K>
 __device__ __forceinline__ void factor_messages(const T (&a)[K], T var, T r, const T (&lam)[K],
                                                 const T (&eta)[K], T (&L)[K], T (&E)[K]) {
@@ -122,12 +130,12 @@ __device__ __forceinline__ void factor_messages(const T (&a)[K], T var, T r, con
         if (a[u] == T(0)) {
             t[u] = T(0);
             p[u] = T(0);
-        } else if (!(lam[u] >= tiny_normal<T>())) {
-            t[u] = pos_inf<T>();
-            p[u] = T(0);
         } else {
-            T rl = recip(lam[u]);
-            t[u] = mul_rn(mul_rn(a[u], a[u]), rl);
+            const T a2 = mul_rn(a[u], a[u]);
+            // fmax returns the other operand for a NaN one: a NaN cavity precision is floored
+            const T fl = fmax(mul_rn(lam_floor_rel<T>(), a2), tiny_normal<T>());
+            const T rl = recip(fmax(lam[u], fl));
+            t[u] = mul_rn(a2, rl);
             p[u] = mul_rn(a[u], mul_rn(eta[u], rl));
         }
     }
@@ -142,13 +150,11 @@ __device__ __forceinline__ void factor_messages(const T (&a)[K], T var, T r, con
     T sufV = T(0), sufM = T(0);
 #pragma unroll
     for (int v = K - 1; v >= 0; --v) {
-        T V = add_rn(preV[v], sufV);
-        T M = add_rn(preM[v], sufM);
-        // V >= var > 0; an infinite V (a slot without information) gives the message (0, 0)
-        const bool inf_v = V == pos_inf<T>();
-        const T rV = inf_v ? T(0) : recip(V);
+        const T V = add_rn(preV[v], sufV);
+        const T M = add_rn(preM[v], sufM);
+        const T rV = recip(V);
         L[v] = mul_rn(mul_rn(a[v], a[v]), rV);
-        E[v] = inf_v ? T(0) : mul_rn(mul_rn(a[v], add_rn(r, -M)), rV);
+        E[v] = mul_rn(mul_rn(a[v], add_rn(r, -M)), rV);
         sufV = add_rn(sufV, t[v]);
         sufM = add_rn(sufM, p[v]);
     }

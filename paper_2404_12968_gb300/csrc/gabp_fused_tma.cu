@@ -201,19 +201,23 @@ __device__ __forceinline__ void add_obs_pair2(CompSum2 &s, const float *O, int l
 // Factor-to-variable messages of a rank-1 factor with K slots on (eta, Lambda) pairs: the
 // arithmetic of factor_messages (App. A) with the (M, V) sums and the (eta, Lambda) outputs
 // carried as pairs.  cav[u] = cavity (eta, Lambda) of slot u; out[u] = message (eta, Lambda).
-template <int K>
+// UNIT_A: every nonzero a_u^2 is at least 1.2e-18 (cell factors: -1 and kappa^2 + deg with
+// deg >= 1, as on every grid of four or more columns), so 1e-20 a_u^2 is a normal number and the
+// second floor of factor_messages is a no-op that can be left out.
+template <int K, bool UNIT_A>
 __device__ __forceinline__ void factor_messages2(const float (&a)[K], float var, float r, const float2 (&cav)[K],
                                                  float2 (&out)[K]) {
-    float2 tp[K];   // (a eta / lam, a^2 / lam)
+    float2 tp[K];   // (a eta / lam, a^2 / lam), lam floored as in factor_messages
 #pragma unroll
     for (int u = 0; u < K; ++u) {
         if (a[u] == 0.f) {
             tp[u] = f2(0.f, 0.f);
-        } else if (!(cav[u].y >= tiny_normal<float>())) {
-            tp[u] = f2(0.f, pos_inf<float>());
         } else {
-            const float rl = recip(cav[u].y);
-            tp[u] = mul2(f2(a[u], mul_rn(a[u], a[u])), f2(mul_rn(cav[u].x, rl), rl));
+            const float a2 = mul_rn(a[u], a[u]);
+            float fl = mul_rn(lam_floor_rel<float>(), a2);
+            if (!UNIT_A) fl = fmaxf(fl, tiny_normal<float>());
+            const float rl = recip(fmaxf(cav[u].y, fl));
+            tp[u] = mul2(f2(a[u], a2), f2(mul_rn(cav[u].x, rl), rl));
         }
     }
     float2 pre[K];   // prefix sums (M, V), V starting from var
@@ -224,11 +228,8 @@ __device__ __forceinline__ void factor_messages2(const float (&a)[K], float var,
 #pragma unroll
     for (int v = K - 1; v >= 0; --v) {
         const float2 MV = add2(pre[v], suf);
-        const bool inf_v = MV.y == pos_inf<float>();
-        const float rV = inf_v ? 0.f : recip(MV.y);
-        float2 o = mul2(f2(mul_rn(a[v], add_rn(r, -MV.x)), mul_rn(a[v], a[v])), f2(rV, rV));
-        if (inf_v) o.x = 0.f;
-        out[v] = o;
+        const float rV = recip(MV.y);
+        out[v] = mul2(f2(mul_rn(a[v], add_rn(r, -MV.x)), mul_rn(a[v], a[v])), f2(rV, rV));
         suf = add2(suf, tp[v]);
     }
 }
@@ -248,7 +249,7 @@ __device__ __forceinline__ void cell_factor(const float (&a)[5], const Belief2 *
 #pragma unroll
     for (int u = 0; u < 5; ++u) cav[u] = a[u] != 0.f ? cavity2(*bs[u], own[u]) : f2(0.f, 1.f);
     float2 msg[5];
-    factor_messages2<5>(a, var, r, cav, msg);
+    factor_messages2<5, true>(a, var, r, cav, msg);
 #pragma unroll
     for (int u = 0; u < 5; ++u) __stcs(q + u * n, a[u] != 0.f ? damp2(own[u], msg[u], beta2) : f2(0.f, 0.f));
 }
@@ -587,7 +588,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                 for (int u = 0; u < 4; ++u) cav[u] = cavity2(*ob[u], own4[u]);
                 const float2 yv = *reinterpret_cast<const float2 *>(YV + 2 * k);
                 float2 msg[4];
-                factor_messages2<4>(aw, yv.y, yv.x, cav, msg);
+                factor_messages2<4, false>(aw, yv.y, yv.x, cav, msg);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) msg[u] = damp2(own4[u], msg[u], beta2);
                 *reinterpret_cast<float4 *>(OQ + 8 * k) = make_float4(msg[0].x, msg[0].y, msg[1].x, msg[1].y);

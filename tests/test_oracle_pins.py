@@ -104,18 +104,43 @@ def test_pairwise_factor_reduces_to_paper_update(orc):
         assert b_num == pytest.approx(-beta * P_ij / alpha, rel=1e-6, abs=1e-8)
 
 
-def test_nonpositive_cavity_gives_zero_messages(orc):
+def test_zero_precision_cavity_gives_the_limit_message(orc):
+    """A cavity of zero precision and finite information is the linear potential exp(eta x):
+    the factor's messages are the dense Schur complement with that zero on the diagonal (the
+    integral of App. A stays proper along the factor's direction), which the formulas reach
+    as the precision tends to zero.  Catches: dropping such a slot's information (a (0, 0)
+    message), a wrong sign or a_u / a_v swap in the limit, a jump at the precision floor."""
     a = np.array([2.0, -1.0, -1.0])
-    lo, eo = orc.factor_update(a, 1.0, 0.3, np.array([1.0, 0.0, 2.0]), np.array([0.1, 0.2, 0.3]))
-    # slot 1 has no information: every other slot's message is (0, 0); slot 1 itself is fine
-    assert lo[0] == 0 and eo[0] == 0 and lo[2] == 0 and eo[2] == 0
-    L1, E1 = _schur_message(a, 1.0, 0.3, np.array([1.0, 0.0, 2.0]), np.array([0.1, 0.2, 0.3]), 1)
-    assert lo[1] == pytest.approx(L1) and eo[1] == pytest.approx(E1)
-    # a positive cavity below the smallest normal double (reciprocal overflows) counts as no
-    # information too: the other slots get exactly (0, 0), never NaN
-    lo, eo = orc.factor_update(a, 1.0, 0.3, np.array([1.0, 1e-310, 2.0]), np.array([0.1, 0.5, 0.3]))
-    assert lo[0] == 0 and eo[0] == 0 and lo[2] == 0 and eo[2] == 0
-    assert np.all(np.isfinite(lo)) and np.all(np.isfinite(eo))
+    lam = np.array([1.0, 0.0, 2.0])
+    eta = np.array([0.1, 0.2, 0.3])
+    lo, eo = orc.factor_update(a, 1.0, 0.3, lam, eta)
+    for v in range(3):
+        L_ref, E_ref = _schur_message(a, 1.0, 0.3, lam, eta, v)
+        assert lo[v] == pytest.approx(L_ref, rel=1e-12, abs=1e-18)
+        assert eo[v] == pytest.approx(E_ref, rel=1e-12)
+    # the other slots' messages: precision 0, information -a_v eta_1 / a_1
+    assert abs(lo[0]) < 1e-18 and eo[0] == pytest.approx(0.4) and abs(lo[2]) < 1e-18 and eo[2] == pytest.approx(-0.2)
+    # a small positive precision: the dense Schur complement, which tends to the same limit
+    for lam1 in (1e-8, 1e-12):
+        lam_s = np.array([1.0, lam1, 2.0])
+        lo, eo = orc.factor_update(a, 1.0, 0.3, lam_s, eta)
+        for v in range(3):
+            L_ref, E_ref = _schur_message(a, 1.0, 0.3, lam_s, eta, v)
+            assert lo[v] == pytest.approx(L_ref, rel=1e-9) and eo[v] == pytest.approx(E_ref, rel=1e-9)
+    # no jump at the floor (1e-20 a_u^2), and a negative cavity is read as a zero one
+    lo1, eo1 = orc.factor_update(a, 1.0, 0.3, np.array([1.0, 1.01e-20, 2.0]), eta)
+    lo2, eo2 = orc.factor_update(a, 1.0, 0.3, np.array([1.0, 0.99e-20, 2.0]), eta)
+    lon, eon = orc.factor_update(a, 1.0, 0.3, np.array([1.0, -1.0, 2.0]), eta)
+    assert np.allclose(eo1, eo2, rtol=1e-12, atol=0) and np.allclose(eon, eo2, rtol=1e-12, atol=0)
+    assert np.all(np.isfinite(lon)) and np.all(np.isfinite(eon))
+    # two such slots: the limit along precisions shrinking as c a_u^2 (dense Schur at c = 1e-9)
+    a4 = np.array([2.0, -1.0, -0.5, 0.25])
+    eta4 = np.array([0.1, 0.2, -0.6, 0.3])
+    lo, eo = orc.factor_update(a4, 1.0, 0.3, np.array([1.0, 0.0, 0.0, 3.0]), eta4)
+    lam_c = np.array([1.0, 1e-9 * a4[1] ** 2, 1e-9 * a4[2] ** 2, 3.0])
+    for v in range(4):
+        L_ref, E_ref = _schur_message(a4, 1.0, 0.3, lam_c, eta4, v)
+        assert eo[v] == pytest.approx(E_ref, rel=1e-6, abs=1e-12) and lo[v] == pytest.approx(L_ref, rel=1e-6, abs=1e-8)
     # zero coefficients are skipped even when the cavity is non-positive
     lo, eo = orc.factor_update(np.array([1.0, 0.0]), 2.0, 0.5, np.array([1.0, -1.0]),
                                np.array([0.0, 0.0]))
