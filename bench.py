@@ -151,18 +151,28 @@ def sampled_error(mu, g) -> float:
     return float(np.linalg.norm(d) / np.linalg.norm(g["mean"]))
 
 
-def solve_to_floor(step, residual, chunk: int = 1000, max_iters: int = 20000):
-    """Iterate in chunks until the FP64 relative residual stops halving from one chunk to the
-    next (the rounding floor of FP32 messages) or max_iters pass; (residual, iterations)."""
-    best, its, res = float("inf"), 0, float("inf")
+def solve_until_settled(step, means, chunk: int = 1000, max_iters: int = 60000, tol: float = 1e-7):
+    """Iterate in chunks until the means (an array, or a list of arrays: each must settle) change
+    by less than tol (relative L2) from one chunk to the next, or max_iters pass; returns the
+    iterations.  (The FP64 residual is no guide here: with FP32 messages it levels off near 5e-8
+    while the poorly observed smooth modes are still converging.)"""
+    import numpy as np
+
+    def snap():
+        m = means()
+        return [np.array(x, copy=True) for x in (m if isinstance(m, list) else [m])]
+
+    prev = snap()
+    its = 0
     while its < max_iters:
         step(chunk)
         its += chunk
-        res = residual()
-        if not res < 0.5 * best:
+        cur = snap()
+        change = max(float(np.linalg.norm(c - q) / max(np.linalg.norm(c), 1e-300)) for c, q in zip(cur, prev))
+        prev = cur
+        if change < tol:
             break
-        best = res
-    return res, its
+    return its
 
 
 class ClockSampler:
@@ -371,11 +381,18 @@ def main_accuracy(s, p, res_last: float, iters_done: int):
     mu = np.empty(p.n)
     s.marginals(out_mean=mu, want_var=False)
     e0 = sampled_error(mu, g)
-    res, its = solve_to_floor(lambda k: s.iterate(k, DAMPING), s.residual)
+
+    def means():
+        s.marginals(out_mean=mu, want_var=False)
+        return mu
+
+    its = solve_until_settled(lambda k: s.iterate(k, DAMPING), means)
+    res = s.residual()
     s.marginals(out_mean=mu, want_var=False)
     return {"reference": "exact posterior mean A^-1 b (oracle, FP64 PCG to its rounding floor, about 3e-15), 4096 sampled nodes",
             "after_timed_steps": {"iterations": iters_done, "rel_residual": res_last, "mean_rel_l2": e0},
-            "at_fp32_floor": {"iterations": iters_done + its, "rel_residual": res, "mean_rel_l2": sampled_error(mu, g)},
+            "converged": {"iterations": iters_done + its, "rel_residual": res, "mean_rel_l2": sampled_error(mu, g),
+                          "stop": "means changed by less than 1e-7 (relative L2) over 1000 iterations"},
             "gate": 1e-4}
 
 
@@ -396,17 +413,12 @@ def batch_rate(device: int):
         b.iterate(100, DAMPING)
         dt = (time.perf_counter() - t) / 100
         kernel = b.kernel_name
-        # accuracy (untimed): every instance to its FP32 floor, then the stored instances' means
-        # against their exact means
-        best = np.full(len(probs), np.inf)
-        its = 120
-        while its < 20000:
-            b.iterate(1000, DAMPING)
-            its += 1000
-            res = b.residuals()
-            if np.all(~(res < 0.5 * best)):
-                break
-            best = np.minimum(best, res)
+        # accuracy (untimed): the whole batch iterated until every instance's means settle, then
+        # the stored instances' means against their exact means
+        its = 120 + solve_until_settled(lambda k: b.iterate(k, DAMPING),
+                                        lambda: [b.marginals(i)[0] for i in range(len(probs))],
+                                        chunk=2000, max_iters=80000)
+        res = b.residuals()
         errs = {}
         for i in range(len(probs)):
             g = exact_sample(f"batch_{i:02d}", probs[i])
@@ -420,8 +432,8 @@ def batch_rate(device: int):
                          "iterations": its, "max_rel_residual": float(np.max(res)),
                          "mean_rel_l2_per_instance": {str(k): v for k, v in errs.items()},
                          "max_mean_rel_l2": max(errs.values()) if errs else None,
-                         "note": "FP32 messages at their rounding floor (every instance iterated until "
-                                 "its residual stopped halving per 1000 iterations)"}}
+                         "stop": "all instances' means changed by less than 1e-7 (relative L2) over "
+                                 "2000 iterations"}}
 
 
 def pairwise_rate(p, device: int):
