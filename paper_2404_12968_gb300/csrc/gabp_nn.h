@@ -57,6 +57,24 @@ cudaError_t tc_pack_weights(const __nv_bfloat16 *w, int Cout, int T, int Cin, __
 cudaError_t tc_conv(const __nv_bfloat16 *in, TcConvArgs a, cudaStream_t st);
 int64_t wgrad_chunks(const WgradArgs &a);
 cudaError_t conv_wgrad(WgradArgs a, float *dw, cudaStream_t st);
+// Weight gradient on the tcgen05 tensor cores (gabp_nn_tc.cu): dw[co][t][ci] = sum over the
+// pixels p of g[p][co] in[p + d_t][ci] (zero outside the image), as partial sums over pixel
+// chunks in part (at most part_cap floats) reduced into dw in chunk order.  Cin a multiple
+// of 16 (at most 256 per block of N), any Cout (blocks of 128; rows past Cout are zero).
+struct TcWgradArgs {
+    const __nv_bfloat16 *g;     // [B][H][W][Cout]
+    const __nv_bfloat16 *in;    // [B][H][W][Cin]
+    float *part;
+    int64_t part_cap;
+    int *err;                   // device flag, set if a bounded wait ran out
+    int B, H, W, Cin, Cout, T;
+    // set by tc_wgrad
+    int N, nbn, nbm, chunks, stages;
+    int64_t ktiles, tiles_x, tiles_y, per_chunk;
+};
+cudaError_t tc_wgrad(TcWgradArgs a, float *dw, cudaStream_t st);
+// out[i] = sum over c < chunks of part[c * count + i], in chunk order
+cudaError_t reduce_chunks(const float *part, int chunks, int64_t count, float *out, cudaStream_t st);
 cudaError_t bias_grad(const __nv_bfloat16 *g, int64_t P, int C, float *db, cudaStream_t st);
 cudaError_t flip_transpose(const __nv_bfloat16 *w, int Cout, int T, int Cin, __nv_bfloat16 *wt, cudaStream_t st);
 cudaError_t relu_bwd(const __nv_bfloat16 *y, const __nv_bfloat16 *dy, __nv_bfloat16 *dx, int64_t n, cudaStream_t st);

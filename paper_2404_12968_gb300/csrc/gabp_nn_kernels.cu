@@ -494,6 +494,11 @@ cudaError_t conv_wgrad(WgradArgs a, float *dw, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+cudaError_t reduce_chunks(const float *part, int chunks, int64_t count, float *out, cudaStream_t st) {
+    k_reduce_chunks<<<nb(count), 256, 0, st>>>(part, chunks, count, out);
+    return cudaGetLastError();
+}
+
 cudaError_t bias_grad(const __nv_bfloat16 *g, int64_t P, int C, float *db, cudaStream_t st) {
     k_bias_grad<<<C, 256, 0, st>>>(g, P, C, db);
     return cudaGetLastError();

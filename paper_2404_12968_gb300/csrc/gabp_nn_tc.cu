@@ -22,6 +22,15 @@
 // NHWC.  Optional fused epilogues: 2x2 average pooling, nearest upsampling plus a skip tensor
 // (the decoder's 1x1 reductions), and the 1x1 FP32 head.  Every mbarrier wait is bounded; a
 // wait that runs out raises the error flag and the block finishes without further copies.
+//
+// The weight gradient of training, dw[co][t][ci] = sum_p g[p][co] in[p + d_t][ci], is a GEMM
+// with M = output channels, N = input channels and K = pixels, per tap (k_tc_wgrad).  Both
+// operands come straight from the NHWC tensors: 8 channels of one pixel are 16 contiguous
+// bytes, so a tile of 64 pixels (16 x 4) x 8 channels is one MN-major core-matrix column
+// (8 pixels = 128 bytes per core matrix along K), loaded by one 5-D TMA copy per operand
+// (channel-in-group, x, y, image, channel group) with zero fill outside the image for the tap
+// shift.  One accumulator of N FP32 columns per block covers a chunk of pixel tiles; the
+// epilogue writes it to a partial-sum buffer that a second kernel reduces in chunk order.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -90,6 +99,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both MN-major (transpose bits 15
+// and 16), M = 128, N.
+__device__ __forceinline__ uint32_t instr_desc_mn(int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
+}
+
 // Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M = 128, N.
 template <int N> __device__ __forceinline__ uint32_t instr_desc() {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
@@ -347,6 +372,148 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_conv(const __grid_constant__ 
     }
 }
 
+// ---- weight gradient ----
+constexpr int WG_THREADS = 192;
+constexpr int WG_KX = 16, WG_KY = 4;                     // pixels per K tile (K = 64)
+constexpr uint32_t WG_GROUP = WG_KX * WG_KY * 16;       // one 8-channel group of a tile (1 KB)
+constexpr uint32_t WG_A = 16 * WG_GROUP;                // 128 output channels
+
+// Block: tap t, output-channel block mb (128), input-channel block nb (N), pixel-tile chunk c.
+// Shared memory per stage: A [16 groups][64 pixels][8] then B [N / 8 groups][64 pixels][8];
+// canonical MN-major, no swizzle: core matrix = 8 pixels x 8 channels (128 B), K-direction
+// core matrices 128 B apart (LBO), channel-direction 1 KB apart (SBO).
+__global__ void __launch_bounds__(WG_THREADS) k_tc_wgrad(const __grid_constant__ CUtensorMap gmap,
+                                                         const __grid_constant__ CUtensorMap xmap, TcWgradArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int S = a.stages, N = a.N;
+    const uint32_t STAGE = WG_A + (uint32_t)(N / 8) * WG_GROUP;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)S * STAGE);   // full[S], empty[S], acc
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * S + 1);
+    volatile int *fail = reinterpret_cast<volatile int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = saddr(smem);
+    auto full = [&](int s) { return saddr(&bars[s]); };
+    auto empty = [&](int s) { return saddr(&bars[S + s]); };
+    const uint32_t accb = saddr(&bars[2 * S]);
+    const uint32_t tcols = N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
+
+    // block -> (chunk, tap, mb, nb)
+    int64_t r = blockIdx.x;
+    const int nb = (int)(r % a.nbn);
+    r /= a.nbn;
+    const int mb = (int)(r % a.nbm);
+    r /= a.nbm;
+    const int t = (int)(r % a.T);
+    const int chunk = (int)(r / a.T);
+    const int dy = a.T == 9 ? t / 3 - 1 : 0, dx = a.T == 9 ? t % 3 - 1 : 0;
+    const int64_t kt0 = (int64_t)chunk * a.per_chunk;
+    const int64_t kt1 = kt0 + a.per_chunk < a.ktiles ? kt0 + a.per_chunk : a.ktiles;
+    const int nk = (int)(kt1 > kt0 ? kt1 - kt0 : 0);
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        mbar_init(accb, 1);
+        *fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
+                     "r"(tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (warp == 4) {
+        // ---- TMA producer: tile k = (image, tile row, tile column) ----
+        if (lane == 0) {
+            for (int i = 0; i < nk && !*fail; ++i) {
+                const int s = i % S;
+                if (!mbar_wait(empty(s), ((uint32_t)(i / S) & 1) ^ 1)) {
+                    *fail = 1;
+                    break;
+                }
+                const int64_t k = kt0 + i;
+                const int tx = (int)(k % a.tiles_x);
+                const int64_t q = k / a.tiles_x;
+                const int ty = (int)(q % a.tiles_y);
+                const int b = (int)(q / a.tiles_y);
+                const int x0 = tx * WG_KX, y0 = ty * WG_KY;
+                const uint32_t st = sbase + (uint32_t)s * STAGE;
+                mbar_expect_tx(full(s), STAGE);
+                tma_load_5d(st, &gmap, 0, x0, y0, b, 16 * mb, full(s));
+                tma_load_5d(st + WG_A, &xmap, 0, x0 + dx, y0 + dy, b, nb * (N / 8), full(s));
+            }
+        }
+    } else if (warp == 5) {
+        // ---- MMA issuer: 4 MMAs (K = 16) per tile ----
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc_mn(N);
+            bool ok = true;
+            for (int i = 0; i < nk && !*fail; ++i) {
+                const int s = i % S;
+                if (!mbar_wait(full(s), (uint32_t)(i / S) & 1)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = sbase + (uint32_t)s * STAGE;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t ad = smem_desc(st + (uint32_t)kk * 256u, 128u, WG_GROUP);
+                    const uint64_t bd = smem_desc(st + WG_A + (uint32_t)kk * 256u, 128u, WG_GROUP);
+                    umma(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                }
+                umma_commit(empty(s));   // the stage is free once these MMAs have read it
+            }
+            if (!ok) *fail = 1;
+            umma_commit(accb);   // also after a failure, so that the epilogue does not wait out
+        }
+    } else {
+        // ---- epilogue: warps 0-3, TMEM lane 32 w + lane = output channel 128 mb + 32 w + lane ----
+        const bool ok = mbar_wait(accb, 0);
+        if (!ok) *fail = 1;
+        // warp-uniform decision: tcgen05.ld is a whole-warp instruction
+        const bool go = __all_sync(0xffffffffu, ok && !*fail);
+        if (go && nk > 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int co = 128 * mb + 32 * warp + lane;
+            float *dst = a.part + (((int64_t)chunk * a.Cout + co) * a.T + t) * a.Cin + nb * N;
+#pragma unroll 1
+            for (int c = 0; c < N; c += 16) {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+                if (co < a.Cout) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4 *>(dst + c + j) =
+                            make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
+                                        __uint_as_float(v[j + 3]));
+                }
+            }
+        } else if (go) {   // an empty chunk: zero partial sums
+            const int co = 128 * mb + 32 * warp + lane;
+            if (co < a.Cout) {
+                float *dst = a.part + (((int64_t)chunk * a.Cout + co) * a.T + t) * a.Cin + nb * N;
+                for (int c = 0; c < N; ++c) dst[c] = 0.f;
+            }
+        }
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (*fail && tid == 0) atomicExch(a.err, 1);
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+    }
+}
+
 // packed[nb][kb][t][h][n][e] = w[nb * N + n][t][16 kb + 8 h + e]
 __global__ void k_tc_pack(const __nv_bfloat16 *w, int Cout, int T, int Cin, int N, __nv_bfloat16 *out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -433,9 +600,69 @@ cudaError_t tc_launch(const CUtensorMap &map, TcConvArgs a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+bool encode_nhwc_groups(CUtensorMap &map, const __nv_bfloat16 *p, int B, int H, int W, int C, int groups_box) {
+    auto enc = tc_encoder();
+    if (!enc) return false;
+    // [B][H][W][C] viewed as (channel in group, x, y, image, 8-channel group)
+    cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B, (cuuint64_t)(C / 8)};
+    cuuint64_t strides[4] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2, 16};
+    cuuint32_t box[5] = {8, WG_KX, WG_KY, 1, (cuuint32_t)groups_box};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void *)p, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 int tc_block_n(int Cout) { return Cout < 128 ? Cout : 128; }
+
+cudaError_t tc_wgrad(TcWgradArgs a, float *dw, cudaStream_t st) {
+    if (a.Cin % 16 || a.Cout % 8 || a.Cin < 16 || (a.T != 1 && a.T != 9) || a.B < 1 || a.H < 1 || a.W < 1)
+        return cudaErrorInvalidValue;
+    a.N = a.Cin <= 256 ? a.Cin : 256;
+    if (a.Cin % a.N) return cudaErrorInvalidValue;
+    a.nbn = a.Cin / a.N;
+    a.nbm = (a.Cout + 127) / 128;
+    a.tiles_x = (a.W + WG_KX - 1) / WG_KX;
+    a.tiles_y = (a.H + WG_KY - 1) / WG_KY;
+    a.ktiles = (int64_t)a.B * a.tiles_y * a.tiles_x;
+    static int configured_dev = -1, nsm = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured_dev != dev) {
+        e = cudaFuncSetAttribute(k_tc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        configured_dev = dev;
+    }
+    // about two blocks per SM over (chunk, tap, output block, input block); every chunk's partial
+    // sums must fit the buffer
+    const int64_t per_chunk_blocks = (int64_t)a.T * a.nbm * a.nbn;
+    const int64_t count = (int64_t)a.Cout * a.T * a.Cin;
+    int64_t chunks = (2 * nsm + per_chunk_blocks - 1) / per_chunk_blocks;
+    if (chunks > a.ktiles) chunks = a.ktiles;
+    if (chunks * count > a.part_cap) chunks = a.part_cap / count;
+    if (chunks < 1) return cudaErrorInvalidValue;
+    a.per_chunk = (a.ktiles + chunks - 1) / chunks;
+    a.chunks = (int)((a.ktiles + a.per_chunk - 1) / a.per_chunk);
+    const uint32_t stage = WG_A + (uint32_t)(a.N / 8) * WG_GROUP;
+    int S = (int)((196u * 1024u) / stage);
+    a.stages = S > 6 ? 6 : S;
+    if (a.stages < 2) return cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)a.stages * stage + 8 * (2 * a.stages + 1) + 16;
+    CUtensorMap gmap, xmap;
+    if (!encode_nhwc_groups(gmap, a.g, a.B, a.H, a.W, a.Cout, 16) ||
+        !encode_nhwc_groups(xmap, a.in, a.B, a.H, a.W, a.Cin, a.N / 8))
+        return cudaErrorInvalidValue;
+    const int64_t grid = (int64_t)a.chunks * per_chunk_blocks;
+    k_tc_wgrad<<<(unsigned)grid, WG_THREADS, smem, st>>>(gmap, xmap, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return reduce_chunks(a.part, a.chunks, count, dw, st);
+}
 
 cudaError_t tc_pack_weights(const __nv_bfloat16 *w, int Cout, int T, int Cin, __nv_bfloat16 *out, cudaStream_t st) {
     const int64_t total = (int64_t)Cout * T * Cin;

@@ -302,7 +302,23 @@ int conv_bwd(gabp_wsnet *net, int l, const Buf &g, const Buf &in, Buf *din, int 
     wa.Cin = s.cin;
     wa.Cout = s.cout;
     wa.T = s.taps;
-    WK(gabp::nn::conv_wgrad(wa, net->g + net->woff[l], st), "conv wgrad");
+    if (net->kernels == GABP_WSNET_TCGEN05) {
+        gabp::nn::TcWgradArgs ta{};
+        ta.g = g.p;
+        ta.in = in.p;
+        ta.part = net->part;
+        ta.part_cap = net->part_n;
+        ta.err = net->derr;
+        ta.B = B;
+        ta.H = h;
+        ta.W = w;
+        ta.Cin = s.cin;
+        ta.Cout = s.cout;
+        ta.T = s.taps;
+        WK(gabp::nn::tc_wgrad(ta, net->g + net->woff[l], st), "tensor-core weight gradient");
+    } else {
+        WK(gabp::nn::conv_wgrad(wa, net->g + net->woff[l], st), "conv wgrad");
+    }
     WK(gabp::nn::bias_grad(g.p, (int64_t)B * h * w, s.cout, net->g + net->boff[l], st), "bias grad");
     if (din && net->kernels == GABP_WSNET_TCGEN05) {
         // gradient w.r.t. the input: the forward convolution of g with the flipped, transposed

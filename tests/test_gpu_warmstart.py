@@ -92,9 +92,10 @@ def test_network_forward_and_gradients_match_reference():
 
 @pytest.mark.parametrize("B,H,W", [(2, 40, 72), (1, 64, 64)])
 def test_tensor_core_gradients_match_mma_sync_gradients(B, H, W):
-    """Training gradients with the tcgen05 kernels (forward and backward-data convolutions)
-    against the mma.sync kernels of the same network: the same BF16 arithmetic up to the
-    accumulation order, per layer within the BF16 bar of the reference comparison."""
+    """Training gradients with the tcgen05 kernels (forward, backward-data and weight-gradient
+    convolutions) against the mma.sync kernels of the same network: the same BF16 arithmetic
+    up to the accumulation order, per layer within the BF16 bar of the reference comparison;
+    the bias gradients are the same kernel on both."""
     torch = pytest.importorskip("torch")
     from oracle import unet
     from paper_2404_12968_gb300 import (GABP_WSNET_MMA_SYNC, GABP_WSNET_TCGEN05, WarmStartNet,
