@@ -69,13 +69,16 @@ struct TcWgradArgs {
     int *err;                   // device flag, set if a bounded wait ran out
     int B, H, W, Cin, Cout, T;
     // set by tc_wgrad
-    int N, nbn, nbm, chunks, stages;
+    int N, nbn, nbm, chunks, stages, ky, ga, tpc, ngroups;
     int64_t ktiles, tiles_x, tiles_y, per_chunk;
 };
 cudaError_t tc_wgrad(TcWgradArgs a, float *dw, cudaStream_t st);
 // out[i] = sum over c < chunks of part[c * count + i], in chunk order
 cudaError_t reduce_chunks(const float *part, int chunks, int64_t count, float *out, cudaStream_t st);
-cudaError_t bias_grad(const __nv_bfloat16 *g, int64_t P, int C, float *db, cudaStream_t st);
+// db[c] = sum over the P pixels of g[p][c]: chunk partials in part (at most part_cap floats),
+// reduced in chunk order; C at most 256
+cudaError_t bias_grad(const __nv_bfloat16 *g, int64_t P, int C, float *db, float *part, int64_t part_cap,
+                      cudaStream_t st);
 cudaError_t flip_transpose(const __nv_bfloat16 *w, int Cout, int T, int Cin, __nv_bfloat16 *wt, cudaStream_t st);
 cudaError_t relu_bwd(const __nv_bfloat16 *y, const __nv_bfloat16 *dy, __nv_bfloat16 *dx, int64_t n, cudaStream_t st);
 cudaError_t pool(const __nv_bfloat16 *x, int B, int H, int W, int C, __nv_bfloat16 *y, cudaStream_t st);

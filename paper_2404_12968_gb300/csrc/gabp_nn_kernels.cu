@@ -267,6 +267,22 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(WgradArgs a) {
         }
 }
 
+// many chunks of few values: one block per value, the chunks strided over its threads, then a
+// fixed-shape tree (a fixed order)
+__global__ void k_reduce_chunks_wide(const float *part, int chunks, int64_t count, float *out) {
+    __shared__ float sh[256];
+    const int64_t i = blockIdx.x;
+    float s = 0.f;
+    for (int c = threadIdx.x; c < chunks; c += 256) s += part[(int64_t)c * count + i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = sh[0];
+}
+
 // sum the chunk partials in chunk order
 __global__ void k_reduce_chunks(const float *part, int chunks, int64_t count, float *out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -276,19 +292,25 @@ __global__ void k_reduce_chunks(const float *part, int chunks, int64_t count, fl
     out[i] = s;
 }
 
-// bias gradient: sum over pixels of g[p][c] (fixed partition then fixed-order sum)
-__global__ void k_bias_grad(const __nv_bfloat16 *g, int64_t P, int C, float *db) {
-    const int c = blockIdx.x;
+// bias gradient, first stage: part[b][c] = sum of g[p][c] over the pixels of chunk b.  A block
+// reads R = 256 / C pixels per step, C consecutive threads per pixel (coalesced), then adds its
+// R row sums per channel in a fixed order.
+__global__ void k_bias_part(const __nv_bfloat16 *g, int64_t P, int C, int64_t per_chunk, float *part) {
     __shared__ float sh[256];
+    const int R = 256 / C;
+    const int c = threadIdx.x % C, r = threadIdx.x / C;
+    const int64_t p0 = (int64_t)blockIdx.x * per_chunk;
+    const int64_t p1 = p0 + per_chunk < P ? p0 + per_chunk : P;
     float s = 0.f;
-    for (int64_t p = threadIdx.x; p < P; p += 256) s += __bfloat162float(g[p * C + c]);
+    if (r < R)
+        for (int64_t p = p0 + r; p < p1; p += R) s += __bfloat162float(g[p * C + c]);
     sh[threadIdx.x] = s;
     __syncthreads();
-    for (int k = 128; k > 0; k >>= 1) {
-        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
-        __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.f;
+        for (int q = 0; q < R; ++q) t += sh[q * C + threadIdx.x];
+        part[(int64_t)blockIdx.x * C + threadIdx.x] = t;
     }
-    if (threadIdx.x == 0) db[c] = sh[0];
 }
 
 // w_t[ci][t][co] = w[co][8 - t][ci] (3x3) or w[co][0][ci] (1x1): weights of the input gradient
@@ -499,8 +521,17 @@ cudaError_t reduce_chunks(const float *part, int chunks, int64_t count, float *o
     return cudaGetLastError();
 }
 
-cudaError_t bias_grad(const __nv_bfloat16 *g, int64_t P, int C, float *db, cudaStream_t st) {
-    k_bias_grad<<<C, 256, 0, st>>>(g, P, C, db);
+cudaError_t bias_grad(const __nv_bfloat16 *g, int64_t P, int C, float *db, float *part, int64_t part_cap,
+                      cudaStream_t st) {
+    if (C < 1 || C > 256) return cudaErrorInvalidValue;
+    int64_t chunks = 1216;                      // about 8 blocks per SM
+    if (chunks * C > part_cap) chunks = part_cap / C;
+    if (chunks > P) chunks = P;
+    if (chunks < 1) return cudaErrorInvalidValue;
+    const int64_t per_chunk = (P + chunks - 1) / chunks;
+    chunks = (P + per_chunk - 1) / per_chunk;
+    k_bias_part<<<(unsigned)chunks, 256, 0, st>>>(g, P, C, per_chunk, part);
+    k_reduce_chunks_wide<<<(unsigned)C, 256, 0, st>>>(part, (int)chunks, C, db);
     return cudaGetLastError();
 }
 

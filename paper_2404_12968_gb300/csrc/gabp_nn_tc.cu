@@ -374,19 +374,26 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_conv(const __grid_constant__ 
 
 // ---- weight gradient ----
 constexpr int WG_THREADS = 192;
-constexpr int WG_KX = 16, WG_KY = 4;                     // pixels per K tile (K = 64)
-constexpr uint32_t WG_GROUP = WG_KX * WG_KY * 16;       // one 8-channel group of a tile (1 KB)
-constexpr uint32_t WG_A = 16 * WG_GROUP;                // 128 output channels
+constexpr int WG_KX = 16;                               // pixels per tile row (one MMA, K = 16)
 
-// Block: tap t, output-channel block mb (128), input-channel block nb (N), pixel-tile chunk c.
-// Shared memory per stage: A [16 groups][64 pixels][8] then B [N / 8 groups][64 pixels][8];
-// canonical MN-major, no swizzle: core matrix = 8 pixels x 8 channels (128 B), K-direction
-// core matrices 128 B apart (LBO), channel-direction 1 KB apart (SBO).
+// Block: a group of taps [t0, t0 + tpc), output-channel block mb (128), input-channel block nb
+// (N), pixel-tile chunk.  A tile is 16 x KY pixels.  Shared memory per stage:
+//   A [16 groups][KY][16][8]: g at the tile's pixels, 8 output channels per group;
+//   B [N / 8 groups][KY + 2 h][16 + 2 h][8]: the input at the tile's pixels plus a one-pixel
+//     halo (h = 1 for 3x3 taps), so that every tap (dy, dx) of a tile row is the same matrix at
+//     another start address, ((row + h + dy) (16 + 2 h) + h + dx) 16 bytes.
+// Canonical MN-major, no swizzle: core matrix = 8 pixels x 8 channels (128 B), K-direction core
+// matrices 128 B apart (LBO), channel-direction one group apart (SBO).  One MMA per tile row and
+// tap accumulates into that tap's N TMEM columns.  Only the A groups of existing output channels
+// are copied (a.ga of them); the rest of A is zeroed once and stays zero.
 __global__ void __launch_bounds__(WG_THREADS) k_tc_wgrad(const __grid_constant__ CUtensorMap gmap,
                                                          const __grid_constant__ CUtensorMap xmap, TcWgradArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int S = a.stages, N = a.N;
-    const uint32_t STAGE = WG_A + (uint32_t)(N / 8) * WG_GROUP;
+    const int S = a.stages, N = a.N, KY = a.ky, h = a.T == 9 ? 1 : 0;
+    const int HX = WG_KX + 2 * h, HY = KY + 2 * h;
+    const uint32_t AG = (uint32_t)(WG_KX * KY * 16), BG = (uint32_t)(HX * HY * 16);
+    const uint32_t ABYTES = 16 * AG;
+    const uint32_t STAGE = (ABYTES + (uint32_t)(N / 8) * BG + 127u) & ~127u;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)S * STAGE);   // full[S], empty[S], acc
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * S + 1);
     volatile int *fail = reinterpret_cast<volatile int *>(tslot + 1);
@@ -395,21 +402,33 @@ __global__ void __launch_bounds__(WG_THREADS) k_tc_wgrad(const __grid_constant__
     auto full = [&](int s) { return saddr(&bars[s]); };
     auto empty = [&](int s) { return saddr(&bars[S + s]); };
     const uint32_t accb = saddr(&bars[2 * S]);
-    const uint32_t tcols = N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
+    const uint32_t need = (uint32_t)(a.tpc * N);
+    const uint32_t tcols = need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
 
-    // block -> (chunk, tap, mb, nb)
+    // block -> (chunk, tap group, mb, nb)
     int64_t r = blockIdx.x;
     const int nb = (int)(r % a.nbn);
     r /= a.nbn;
     const int mb = (int)(r % a.nbm);
     r /= a.nbm;
-    const int t = (int)(r % a.T);
-    const int chunk = (int)(r / a.T);
-    const int dy = a.T == 9 ? t / 3 - 1 : 0, dx = a.T == 9 ? t % 3 - 1 : 0;
+    const int tg = (int)(r % a.ngroups);
+    const int chunk = (int)(r / a.ngroups);
+    const int t0 = tg * a.tpc;
+    const int ntap = a.T - t0 < a.tpc ? a.T - t0 : a.tpc;
     const int64_t kt0 = (int64_t)chunk * a.per_chunk;
     const int64_t kt1 = kt0 + a.per_chunk < a.ktiles ? kt0 + a.per_chunk : a.ktiles;
     const int nk = (int)(kt1 > kt0 ? kt1 - kt0 : 0);
 
+    // A rows past the copied groups: zero, written once through the generic proxy and made
+    // visible to the tensor core's (async proxy) reads
+    if (a.ga < 16) {
+        const uint32_t zbytes = (16u - (uint32_t)a.ga) * AG;
+        for (int s = 0; s < S; ++s) {
+            uint4 *z = reinterpret_cast<uint4 *>(smem + (size_t)s * STAGE + (size_t)a.ga * AG);
+            for (uint32_t i = tid; i < zbytes / 16; i += WG_THREADS) z[i] = make_uint4(0, 0, 0, 0);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full(s), 1);
@@ -443,15 +462,15 @@ __global__ void __launch_bounds__(WG_THREADS) k_tc_wgrad(const __grid_constant__
                 const int64_t q = k / a.tiles_x;
                 const int ty = (int)(q % a.tiles_y);
                 const int b = (int)(q / a.tiles_y);
-                const int x0 = tx * WG_KX, y0 = ty * WG_KY;
+                const int x0 = tx * WG_KX, y0 = ty * KY;
                 const uint32_t st = sbase + (uint32_t)s * STAGE;
-                mbar_expect_tx(full(s), STAGE);
+                mbar_expect_tx(full(s), (uint32_t)a.ga * AG + (uint32_t)(N / 8) * BG);
                 tma_load_5d(st, &gmap, 0, x0, y0, b, 16 * mb, full(s));
-                tma_load_5d(st + WG_A, &xmap, 0, x0 + dx, y0 + dy, b, nb * (N / 8), full(s));
+                tma_load_5d(st + ABYTES, &xmap, 0, x0 - h, y0 - h, b, nb * (N / 8), full(s));
             }
         }
     } else if (warp == 5) {
-        // ---- MMA issuer: 4 MMAs (K = 16) per tile ----
+        // ---- MMA issuer: one MMA (K = 16) per tile row and tap ----
         if (lane == 0) {
             const uint32_t idesc = instr_desc_mn(N);
             bool ok = true;
@@ -463,11 +482,15 @@ __global__ void __launch_bounds__(WG_THREADS) k_tc_wgrad(const __grid_constant__
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = sbase + (uint32_t)s * STAGE;
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t ad = smem_desc(st + (uint32_t)kk * 256u, 128u, WG_GROUP);
-                    const uint64_t bd = smem_desc(st + WG_A + (uint32_t)kk * 256u, 128u, WG_GROUP);
-                    umma(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                for (int j = 0; j < ntap; ++j) {
+                    const int t = t0 + j;
+                    const int dy = a.T == 9 ? t / 3 - 1 : 0, dx = a.T == 9 ? t % 3 - 1 : 0;
+                    for (int kk = 0; kk < KY; ++kk) {
+                        const uint64_t ad = smem_desc(st + (uint32_t)kk * 256u, 128u, AG);
+                        const uint64_t bd =
+                            smem_desc(st + ABYTES + (uint32_t)(((kk + h + dy) * HX + h + dx) * 16), 128u, BG);
+                        umma(tmem + (uint32_t)(j * N), ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                    }
                 }
                 umma_commit(empty(s));   // the stage is free once these MMAs have read it
             }
@@ -480,26 +503,28 @@ __global__ void __launch_bounds__(WG_THREADS) k_tc_wgrad(const __grid_constant__
         if (!ok) *fail = 1;
         // warp-uniform decision: tcgen05.ld is a whole-warp instruction
         const bool go = __all_sync(0xffffffffu, ok && !*fail);
+        const int co = 128 * mb + 32 * warp + lane;
         if (go && nk > 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int co = 128 * mb + 32 * warp + lane;
-            float *dst = a.part + (((int64_t)chunk * a.Cout + co) * a.T + t) * a.Cin + nb * N;
 #pragma unroll 1
-            for (int c = 0; c < N; c += 16) {
-                uint32_t v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
-                if (co < a.Cout) {
+            for (int j = 0; j < ntap; ++j) {
+                float *dst = a.part + (((int64_t)chunk * a.Cout + co) * a.T + t0 + j) * a.Cin + nb * N;
+#pragma unroll 1
+                for (int c = 0; c < N; c += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(j * N + c), v);
+                    if (co < a.Cout) {
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4 *>(dst + c + j) =
-                            make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
-                                        __uint_as_float(v[j + 3]));
+                        for (int e = 0; e < 16; e += 4)
+                            *reinterpret_cast<float4 *>(dst + c + e) =
+                                make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
+                                            __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
+                    }
                 }
             }
-        } else if (go) {   // an empty chunk: zero partial sums
-            const int co = 128 * mb + 32 * warp + lane;
-            if (co < a.Cout) {
-                float *dst = a.part + (((int64_t)chunk * a.Cout + co) * a.T + t) * a.Cin + nb * N;
+        } else if (go && co < a.Cout) {   // an empty chunk: zero partial sums
+            for (int j = 0; j < ntap; ++j) {
+                float *dst = a.part + (((int64_t)chunk * a.Cout + co) * a.T + t0 + j) * a.Cin + nb * N;
                 for (int c = 0; c < N; ++c) dst[c] = 0.f;
             }
         }
@@ -600,13 +625,14 @@ cudaError_t tc_launch(const CUtensorMap &map, TcConvArgs a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-bool encode_nhwc_groups(CUtensorMap &map, const __nv_bfloat16 *p, int B, int H, int W, int C, int groups_box) {
+bool encode_nhwc_groups(CUtensorMap &map, const __nv_bfloat16 *p, int B, int H, int W, int C, int bx, int by,
+                        int groups_box) {
     auto enc = tc_encoder();
     if (!enc) return false;
     // [B][H][W][C] viewed as (channel in group, x, y, image, 8-channel group)
     cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B, (cuuint64_t)(C / 8)};
     cuuint64_t strides[4] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2, 16};
-    cuuint32_t box[5] = {8, WG_KX, WG_KY, 1, (cuuint32_t)groups_box};
+    cuuint32_t box[5] = {8, (cuuint32_t)bx, (cuuint32_t)by, 1, (cuuint32_t)groups_box};
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
     return enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void *)p, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -624,8 +650,25 @@ cudaError_t tc_wgrad(TcWgradArgs a, float *dw, cudaStream_t st) {
     if (a.Cin % a.N) return cudaErrorInvalidValue;
     a.nbn = a.Cin / a.N;
     a.nbm = (a.Cout + 127) / 128;
+    a.ga = a.Cout / 8 < 16 ? a.Cout / 8 : 16;
+    // taps per block: as many N-column accumulators as the 512 TMEM columns hold, in groups of
+    // balanced size
+    const int maxt = 512 / a.N;
+    a.ngroups = (a.T + maxt - 1) / maxt;
+    a.tpc = (a.T + a.ngroups - 1) / a.ngroups;
+    const int h = a.T == 9 ? 1 : 0;
+    // tile height: 8 pixel rows when three stages of it fit in shared memory, else 4
+    auto stage_bytes = [&](int ky) {
+        const uint32_t ab = 16u * WG_KX * ky * 16, bb = (uint32_t)(a.N / 8) * (WG_KX + 2 * h) * (ky + 2 * h) * 16;
+        return (ab + bb + 127u) & ~127u;
+    };
+    a.ky = stage_bytes(8) * 3 <= 196u * 1024u ? 8 : 4;
+    const uint32_t stage = stage_bytes(a.ky);
+    int S = (int)((196u * 1024u) / stage);
+    a.stages = S > 6 ? 6 : S;
+    if (a.stages < 2) return cudaErrorInvalidConfiguration;
     a.tiles_x = (a.W + WG_KX - 1) / WG_KX;
-    a.tiles_y = (a.H + WG_KY - 1) / WG_KY;
+    a.tiles_y = (a.H + a.ky - 1) / a.ky;
     a.ktiles = (int64_t)a.B * a.tiles_y * a.tiles_x;
     static int configured_dev = -1, nsm = 0;
     int dev = 0;
@@ -638,24 +681,21 @@ cudaError_t tc_wgrad(TcWgradArgs a, float *dw, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         configured_dev = dev;
     }
-    // about two blocks per SM over (chunk, tap, output block, input block); every chunk's partial
-    // sums must fit the buffer
-    const int64_t per_chunk_blocks = (int64_t)a.T * a.nbm * a.nbn;
+    // blocks: about one per SM per resident slot over (chunk, tap group, output block, input
+    // block); every chunk's partial sums must fit the buffer
+    const int64_t per_chunk_blocks = (int64_t)a.ngroups * a.nbm * a.nbn;
     const int64_t count = (int64_t)a.Cout * a.T * a.Cin;
-    int64_t chunks = (2 * nsm + per_chunk_blocks - 1) / per_chunk_blocks;
+    const int resident = a.tpc * a.N <= 256 && stage * a.stages <= 100u * 1024u ? 2 : 1;
+    int64_t chunks = ((int64_t)resident * nsm + per_chunk_blocks - 1) / per_chunk_blocks;
     if (chunks > a.ktiles) chunks = a.ktiles;
     if (chunks * count > a.part_cap) chunks = a.part_cap / count;
     if (chunks < 1) return cudaErrorInvalidValue;
     a.per_chunk = (a.ktiles + chunks - 1) / chunks;
     a.chunks = (int)((a.ktiles + a.per_chunk - 1) / a.per_chunk);
-    const uint32_t stage = WG_A + (uint32_t)(a.N / 8) * WG_GROUP;
-    int S = (int)((196u * 1024u) / stage);
-    a.stages = S > 6 ? 6 : S;
-    if (a.stages < 2) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)a.stages * stage + 8 * (2 * a.stages + 1) + 16;
     CUtensorMap gmap, xmap;
-    if (!encode_nhwc_groups(gmap, a.g, a.B, a.H, a.W, a.Cout, 16) ||
-        !encode_nhwc_groups(xmap, a.in, a.B, a.H, a.W, a.Cin, a.N / 8))
+    if (!encode_nhwc_groups(gmap, a.g, a.B, a.H, a.W, a.Cout, WG_KX, a.ky, a.ga) ||
+        !encode_nhwc_groups(xmap, a.in, a.B, a.H, a.W, a.Cin, WG_KX + 2 * h, a.ky + 2 * h, a.N / 8))
         return cudaErrorInvalidValue;
     const int64_t grid = (int64_t)a.chunks * per_chunk_blocks;
     k_tc_wgrad<<<(unsigned)grid, WG_THREADS, smem, st>>>(gmap, xmap, a);
@@ -698,6 +738,7 @@ cudaError_t tc_conv(const __nv_bfloat16 *in, TcConvArgs a, cudaStream_t st) {
     if (N == 64) return a.T == 9 ? tc_launch<64, 9>(map, a, st) : tc_launch<64, 1>(map, a, st);
     return a.T == 9 ? tc_launch<128, 9>(map, a, st) : tc_launch<128, 1>(map, a, st);
 }
+
 
 }  // namespace nn
 }  // namespace gabp

@@ -153,8 +153,13 @@ int ensure_shape(gabp_wsnet *net, int B, int H, int W, bool grads) {
             wa.Cin = SPECS[l].cin;
             wa.Cout = SPECS[l].cout;
             wa.T = SPECS[l].taps;
-            const int64_t c = gabp::nn::wgrad_chunks(wa) * SPECS[l].cout * SPECS[l].taps * SPECS[l].cin;
+            const int64_t count = (int64_t)SPECS[l].cout * SPECS[l].taps * SPECS[l].cin;
+            const int64_t c = gabp::nn::wgrad_chunks(wa) * count;
             need = c > need ? c : need;
+            // the tensor-core weight gradient: up to 32 pixel chunks of partial sums per layer
+            // (enough blocks for the wide, shallow layers: 256 x 256 x 9 over 64^2 pixels)
+            const int64_t c32 = 32 * count;
+            need = c32 > need ? c32 : need;
         }
         const int64_t hp = ((P0 + 1023) / 1024) * (2 * HEAD_C + 2);
         need = need > hp ? need : hp;
@@ -319,7 +324,8 @@ int conv_bwd(gabp_wsnet *net, int l, const Buf &g, const Buf &in, Buf *din, int 
     } else {
         WK(gabp::nn::conv_wgrad(wa, net->g + net->woff[l], st), "conv wgrad");
     }
-    WK(gabp::nn::bias_grad(g.p, (int64_t)B * h * w, s.cout, net->g + net->boff[l], st), "bias grad");
+    WK(gabp::nn::bias_grad(g.p, (int64_t)B * h * w, s.cout, net->g + net->boff[l], net->part, net->part_n, st),
+       "bias grad");
     if (din && net->kernels == GABP_WSNET_TCGEN05) {
         // gradient w.r.t. the input: the forward convolution of g with the flipped, transposed
         // weights (Cin and Cout exchanged), on the tcgen05 tensor cores like the forward pass
