@@ -2,6 +2,7 @@
 
     python -m paper_2404_12968_gb300.warmstart train --count 2000 --epochs 8 --out wsnet.npy
     python -m paper_2404_12968_gb300.warmstart eval --weights wsnet.npy
+    python -m paper_2404_12968_gb300.warmstart step-time [--batch 8 --side 512 --steps 10 --warmup 3]
 
 Training data: plain-GaBP posteriors that the library itself computes.  Problems of 512^2
 nodes (kappa ~ U[0.02, 0.2], 8-32 satellite-like tracks, sigma 0.05) are solved in batches of
@@ -13,7 +14,8 @@ residual 1e-5 from the cold start, from the learned warm start (scatter + networ
 + message initialisation included) and from the multigrid warm start (the paper's own
 accelerator: a coarse level solved to 1e-4, upscaled; its iterations included); and the
 paper's own pairwise re-weighted form (c = 20, learning rate 0.6) from zero messages, capped
-at 12000 iterations.
+at 12000 iterations.  ``step-time``: the time of one forward and backward pass (all weight
+gradients) on random inputs, with the tcgen05 kernels and with the mma.sync kernels.
 
 PyTorch only holds the samples in device memory; every computation runs in libgabp.
 """
@@ -159,9 +161,41 @@ def evaluate(net: WarmStartNet, problem=None, device: int = 0, repeats: int = 3,
             "pairwise_residual": pw_res, "pairwise_reached_tol": bool(pw_res <= TOL)}
 
 
+def step_time(batch: int, side: int, steps: int = 10, warmup: int = 3) -> dict:
+    """Milliseconds per forward and backward pass (every layer's gradients) on random inputs
+    of ``batch`` x side^2, for each set of convolution kernels (CUDA events on the default
+    stream around ``steps`` passes after ``warmup``)."""
+    import torch
+    from paper_2404_12968_gb300 import (GABP_WSNET_MMA_SYNC, GABP_WSNET_TCGEN05, gabp_wsnet_gradients,
+                                        gabp_wsnet_param_count, gabp_wsnet_set_kernels)
+    dev = torch.device("cuda", 0)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    xs = [torch.randn(side, side, 16, device=dev, generator=gen).to(torch.bfloat16).view(torch.int16)
+          for _ in range(batch)]
+    ts = [torch.randn(side, side, 2, device=dev, generator=gen) for _ in range(batch)]
+    net = WarmStartNet(seed=1, device=0)
+    g = np.empty(gabp_wsnet_param_count(net.handle), np.float32)
+    out = {"batch": batch, "side": side}
+    try:
+        for name, k in (("tcgen05", GABP_WSNET_TCGEN05), ("mma_sync", GABP_WSNET_MMA_SYNC)):
+            gabp_wsnet_set_kernels(net.handle, k)
+            for _ in range(warmup):
+                gabp_wsnet_gradients(net.handle, xs, ts, side, side, g)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                gabp_wsnet_gradients(net.handle, xs, ts, side, side, g)
+            torch.cuda.synchronize()
+            out[f"{name}_ms"] = (time.perf_counter() - t0) / steps * 1e3
+            out[f"{name}_grad_norm"] = float(np.linalg.norm(g))
+    finally:
+        net.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=["train", "eval"])
+    ap.add_argument("mode", choices=["train", "eval", "step-time"])
     ap.add_argument("--count", type=int, default=2000)
     ap.add_argument("--side", type=int, default=512)
     ap.add_argument("--epochs", type=int, default=8)
@@ -171,7 +205,12 @@ def main():
     ap.add_argument("--out", default="wsnet.npy")
     ap.add_argument("--weights", default=None)
     ap.add_argument("--eval-side", type=int, default=2048)
+    ap.add_argument("--steps", type=int, default=10, help="step-time: timed passes per kernel set")
+    ap.add_argument("--warmup", type=int, default=3, help="step-time: untimed passes first")
     args = ap.parse_args()
+    if args.mode == "step-time":
+        print(json.dumps(step_time(args.batch, args.side, args.steps, args.warmup)), flush=True)
+        return
     net = WarmStartNet(seed=args.seed, device=0)
     report = {}
     if args.mode == "train":
