@@ -80,7 +80,10 @@ typedef struct gabp_ctx gabp_ctx;   /* opaque; owns every device buffer it alloc
 typedef struct {
     int nx;        /* columns, >= 1 (>= 2 when there are observations) */
     int ny;        /* rows,    >= 1 (>= 2 when there are observations) */
-    double h;      /* grid spacing; must be 1.0 (unit spacing) */
+    double h;      /* grid spacing of the prior's Laplacian, > 0 (1.0 = unit spacing): L = kappa^2 I -
+                      Delta_h with the 5-point Delta_h at spacing h (App. C), which is h^-2 times
+                      the unit-spacing operator at kappa h; observation locations stay in grid
+                      units */
 } gabp_grid;
 
 typedef struct {

@@ -134,17 +134,21 @@ _L2_OFFSETS = [(0, 0), (-1, 0), (1, 0), (0, -1), (0, 1), (-1, -1), (1, -1), (-1,
                (-2, 0), (2, 0), (0, -2), (0, 2)]
 
 
-def prior_factors(nx: int, ny: int, kappa: float, gamma: float = 1.0, alpha: int = 2) -> FactorList:
-    """One factor per cell: a = row of L = kappa^2 I + graph Laplacian (zero-Neumann), or for
-    alpha = 4 a row of L^2.
+def prior_factors(nx: int, ny: int, kappa: float, gamma: float = 1.0, alpha: int = 2, h: float = 1.0) -> FactorList:
+    """One factor per cell: a = row of L = kappa^2 I - Delta_h (zero-Neumann), or for alpha = 4
+    a row of L^2.  Delta_h is the 5-point Laplacian at grid spacing h (App. C's finite
+    differences, (f_W + f_E + f_S + f_N - 4 f) / h^2 in the interior), so a row of L has
+    kappa^2 + deg / h^2 on the diagonal and -1 / h^2 per existing neighbour.
 
     Slot order within a cell factor: the cell itself, then its west (x-1), east (x+1),
     south (y-1) and north (y+1) neighbours, those that exist; for alpha = 4 then the
     diagonal neighbours (x-1, y-1), (x+1, y-1), (x-1, y+1), (x+1, y+1) and the nodes
     (x-2, y), (x+2, y), (x, y-2), (x, y+2), those that exist.
     """
+    if not (h > 0.0 and np.isfinite(h)):
+        raise ValueError("grid spacing h must be finite and > 0")
     if alpha == 4:
-        return _prior_factors_l2(nx, ny, kappa, gamma)
+        return _prior_factors_l2(nx, ny, kappa, gamma, h)
     if alpha != 2:
         raise ValueError("alpha must be 2 or 4")
     n = nx * ny
@@ -155,8 +159,8 @@ def prior_factors(nx: int, ny: int, kappa: float, gamma: float = 1.0, alpha: int
     exists = np.stack([np.ones(n, bool), jj > 0, jj < nx - 1, ii > 0, ii < ny - 1], axis=1)
     deg = exists[:, 1:].sum(axis=1)
     coefs = np.empty((n, 5))
-    coefs[:, 0] = kappa * kappa + deg
-    coefs[:, 1:] = -1.0
+    coefs[:, 0] = kappa * kappa + deg / (h * h)
+    coefs[:, 1:] = -1.0 / (h * h)
     counts = exists.sum(axis=1)
     ptr = np.zeros(n + 1, np.int64)
     np.cumsum(counts, out=ptr[1:])
@@ -164,11 +168,11 @@ def prior_factors(nx: int, ny: int, kappa: float, gamma: float = 1.0, alpha: int
                       np.full(n, float(gamma)), np.zeros(n))
 
 
-def _prior_factors_l2(nx: int, ny: int, kappa: float, gamma: float) -> FactorList:
+def _prior_factors_l2(nx: int, ny: int, kappa: float, gamma: float, h: float = 1.0) -> FactorList:
     """Rows of L^2: L assembled from the alpha = 2 factor rows, squared by a sparse matrix
     product (a library step), each row read out in the slot order of ``_L2_OFFSETS``."""
     import scipy.sparse as sp
-    fl1 = _prior_factors_l1(nx, ny, kappa)
+    fl1 = prior_factors(nx, ny, kappa, 1.0, 2, h)
     rows = np.repeat(np.arange(fl1.nf), np.diff(fl1.ptr))
     L = sp.csr_matrix((fl1.coef, (rows, fl1.var)), shape=(fl1.n, fl1.n))
     L2 = (L @ L).tocsr()
@@ -189,10 +193,6 @@ def _prior_factors_l2(nx: int, ny: int, kappa: float, gamma: float) -> FactorLis
     # the slots are exactly the nonzeros of each row of L^2
     assert L2.nnz == var.size and np.all(coef != 0.0)
     return FactorList(n, ptr, var, coef, np.full(n, float(gamma)), np.zeros(n))
-
-
-def _prior_factors_l1(nx: int, ny: int, kappa: float) -> FactorList:
-    return prior_factors(nx, ny, kappa, 1.0, 2)
 
 
 def bilinear_base_weights(nx: int, ny: int, ox: np.ndarray, oy: np.ndarray):
@@ -248,10 +248,11 @@ def with_prior_mean(fl: FactorList, prior_mean) -> FactorList:
 
 
 def build_factors(nx, ny, kappa, ox, oy, y, noise_var, gamma: float = 1.0, alpha: int = 2,
-                  prior_mean=None) -> FactorList:
+                  prior_mean=None, h: float = 1.0) -> FactorList:
     """The posterior's factor list: prior cell factors first, then observations in input order.
-    ``prior_mean`` (one value per node) gives the cell factors their targets (``with_prior_mean``)."""
-    pf = prior_factors(nx, ny, kappa, gamma, alpha)
+    ``prior_mean`` (one value per node) gives the cell factors their targets (``with_prior_mean``);
+    ``h`` is the grid spacing of the prior's Laplacian (observation locations stay in grid units)."""
+    pf = prior_factors(nx, ny, kappa, gamma, alpha, h)
     if prior_mean is not None:
         pf = with_prior_mean(pf, prior_mean)
     return concat(pf, obs_factors(nx, ny, ox, oy, y, noise_var)).check()

@@ -70,9 +70,10 @@ def gabp_default_options(**over) -> _lib.gabp_options:
 
 
 def gabp_create(nx: int, ny: int, kappa: float, obs_xy, y, noise_var, *, gamma: float = 1.0, alpha: int = 2,
-                options: _lib.gabp_options | None = None, **opts) -> int:
-    """Create a context; returns its handle.  ``obs_xy`` is (m, 2) float64 host data; ``alpha``
-    the SPDE exponent (2: cell factors = rows of L, 4: rows of L^2)."""
+                h: float = 1.0, options: _lib.gabp_options | None = None, **opts) -> int:
+    """Create a context; returns its handle.  ``obs_xy`` is (m, 2) float64 host data in grid
+    units; ``alpha`` the SPDE exponent (2: cell factors = rows of L, 4: rows of L^2); ``h`` the
+    grid spacing of the prior's Laplacian."""
     L = _lib.load()
     obs_xy = np.ascontiguousarray(obs_xy, np.float64).reshape(-1)
     y = np.ascontiguousarray(y, np.float64).reshape(-1)
@@ -82,12 +83,12 @@ def gabp_create(nx: int, ny: int, kappa: float, obs_xy, y, noise_var, *, gamma: 
         raise ValueError("obs_xy must be (m, 2) and noise_var (m,)")
     o = options if options is not None else gabp_default_options(**opts)
     prior = _lib.gabp_prior(gamma, 0, int(alpha))
-    h = ctypes.c_void_p()
-    rc = L.gabp_create(ctypes.byref(h), _lib.gabp_grid(nx, ny, 1.0), float(kappa), ctypes.byref(prior),
+    handle = ctypes.c_void_p()
+    rc = L.gabp_create(ctypes.byref(handle), _lib.gabp_grid(nx, ny, float(h)), float(kappa), ctypes.byref(prior),
                        m, obs_xy.ctypes.data if m else None, y.ctypes.data if m else None,
                        noise_var.ctypes.data if m else None, ctypes.byref(o))
     _check(rc, create=True)
-    return h.value
+    return handle.value
 
 
 def gabp_iterate(ctx: int, n_iters: int, damping: float) -> None:
@@ -586,14 +587,15 @@ class Solver:
     object (fields nx, ny, kappa, obs_x, obs_y, y, noise_var)."""
 
     def __init__(self, problem=None, *, nx=None, ny=None, kappa=None, obs_xy=None, y=None,
-                 noise_var=None, precision: str = "fp32", gamma: float = 1.0, alpha: int = 2, **opts):
+                 noise_var=None, precision: str = "fp32", gamma: float = 1.0, alpha: int = 2, h: float = 1.0,
+                 **opts):
         if problem is not None:
             nx, ny, kappa = problem.nx, problem.ny, problem.kappa
             obs_xy = np.stack([problem.obs_x, problem.obs_y], axis=1)
             y, noise_var = problem.y, problem.noise_var
         opts.setdefault("precision", GABP_FP64 if precision == "fp64" else GABP_FP32)
         self.nx, self.ny = int(nx), int(ny)
-        self.ctx = gabp_create(self.nx, self.ny, kappa, obs_xy, y, noise_var, gamma=gamma, alpha=alpha, **opts)
+        self.ctx = gabp_create(self.nx, self.ny, kappa, obs_xy, y, noise_var, gamma=gamma, alpha=alpha, h=h, **opts)
 
     @property
     def n(self) -> int:

@@ -379,18 +379,29 @@ template <typename F> void parallel_chunks(int64_t count, int nchunk, F f) {
     p->job = nullptr;
 }
 
-int create_impl(gabp_ctx *c, gabp_grid grid, double kappa, const gabp_prior *prior, int64_t m,
+int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *prior, int64_t m,
                 const double *obs_xy, const double *y, const double *noise_var) {
     const int nx = grid.nx, ny = grid.ny;
     if (nx < 1 || ny < 1) return fail(c, GABP_ERR_ARG, "grid sizes must be >= 1");
     if ((int64_t)nx * ny > (int64_t)1 << 30) return fail(c, GABP_ERR_ARG, "grid larger than 2^30 nodes");
-    if (!(grid.h == 1.0)) return fail(c, GABP_ERR_ARG, "grid spacing h must be 1");
-    if (!(kappa > 0.0) || !std::isfinite(kappa)) return fail(c, GABP_ERR_ARG, "kappa must be finite and > 0");
-    const double gamma = prior ? prior->gamma : 1.0;
-    if (!(gamma > 0.0) || !std::isfinite(gamma)) return fail(c, GABP_ERR_ARG, "gamma must be finite and > 0");
+    const double h = grid.h;
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(c, GABP_ERR_ARG, "grid spacing h must be finite and > 0");
+    if (!(kappa_h > 0.0) || !std::isfinite(kappa_h)) return fail(c, GABP_ERR_ARG, "kappa must be finite and > 0");
+    const double gamma_h = prior ? prior->gamma : 1.0;
+    if (!(gamma_h > 0.0) || !std::isfinite(gamma_h)) return fail(c, GABP_ERR_ARG, "gamma must be finite and > 0");
     if (prior && prior->boundary != 0) return fail(c, GABP_ERR_ARG, "only the zero-Neumann boundary (0) is implemented");
     const int alpha = prior && prior->alpha ? prior->alpha : 2;
     if (alpha != 2 && alpha != 4) return fail(c, GABP_ERR_ARG, "alpha must be 2 or 4");
+    // spacing h: L_h = kappa^2 I - Delta_h = h^-2 L_1(kappa h), so the prior gamma (L_h^(alpha/2))^T
+    // L_h^(alpha/2) is the unit-spacing one with kappa h and gamma / h^(2 alpha); everything
+    // below (kernels, multigrid, warm starts) works at unit spacing
+    const double kappa = kappa_h * h;
+    double hp = h * h;
+    hp = hp * hp;
+    if (alpha == 4) hp = hp * hp;
+    const double gamma = gamma_h / hp;
+    if (!(kappa > 0.0) || !std::isfinite(kappa) || !(gamma > 0.0) || !std::isfinite(gamma))
+        return fail(c, GABP_ERR_ARG, "kappa h and gamma / h^(2 alpha) must be finite and > 0");
     if (m < 0 || m > ((int64_t)1 << 28)) return fail(c, GABP_ERR_ARG, "observation count out of range");
     if (m > 0 && (!obs_xy || !y || !noise_var)) return fail(c, GABP_ERR_ARG, "observation arrays must not be NULL");
     if (m > 0 && (nx < 2 || ny < 2)) return fail(c, GABP_ERR_ARG, "observations need a grid of at least 2 x 2");

@@ -258,6 +258,32 @@ def test_prior_precision_eigenvectors_are_dct(orc):
         + 4 * math.sin(math.pi * (ny - 1) / (2 * ny)) ** 2)
 
 
+@pytest.mark.parametrize("alpha", [2, 4])
+def test_grid_spacing_scales_the_laplacian(orc, alpha):
+    # catches: h applied to kappa instead of the Laplacian, h instead of h^2, the diagonal's
+    # degree term left unscaled.  On the DCT basis the operator at spacing h has eigenvalue
+    # kappa^2 + (4 / h^2) (sin^2(pi k / 2 nx) + sin^2(pi l / 2 ny)) (its precision that to the
+    # power alpha, times gamma), and on the unit interval the first mode tends to the
+    # continuum Neumann eigenvalue kappa^2 + pi^2 as h -> 0.
+    nx, ny, kappa, gamma, h = 10, 7, 1.3, 0.8, 0.25
+    fl = orc.prior_factors(nx, ny, kappa, gamma, alpha, h)
+    for (k, l) in [(0, 0), (1, 0), (0, 1), (4, 3), (9, 6)]:
+        phi = _dct_basis(nx, ny, k, l)
+        ev = kappa ** 2 + (4.0 / h ** 2) * (math.sin(math.pi * k / (2 * nx)) ** 2 + math.sin(math.pi * l / (2 * ny)) ** 2)
+        np.testing.assert_allclose(orc.apply_A(fl, phi), gamma * ev ** alpha * phi, rtol=1e-12,
+                                   atol=1e-9 * ev ** alpha)
+    # h = 1 is the unit-spacing operator
+    f1, f0 = orc.prior_factors(6, 5, kappa, gamma, alpha, 1.0), orc.prior_factors(6, 5, kappa, gamma, alpha)
+    assert np.array_equal(f1.coef, f0.coef) and np.array_equal(f1.var, f0.var)
+    # continuum: first Neumann mode of the unit square's x direction, nx = 1 / h nodes
+    for n1 in (64, 256):
+        hh = 1.0 / n1
+        fl = orc.prior_factors(n1, 2, kappa, 1.0, 2, hh)
+        phi = _dct_basis(n1, 2, 1, 0)
+        ev = float(phi @ orc.apply_A(fl, phi)) ** 0.5   # P = L^2: sqrt of the Rayleigh quotient
+        assert ev == pytest.approx(kappa ** 2 + math.pi ** 2, rel=2.0 / n1 ** 2)
+
+
 def test_band_solver_matches_dct_solve(orc):
     from scipy import fft as sfft
     nx, ny, kappa = 24, 17, 0.15
