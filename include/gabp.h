@@ -147,7 +147,7 @@ void gabp_default_options(gabp_options *opt);
  * "Including Observations", here with bilinear observation rows) and initialise messages.
  *
  *   out        receives the new context (set to NULL on failure).
- *   grid       grid size; grid.h must be 1.0.
+ *   grid       grid size and the spacing h of the prior's Laplacian (> 0).
  *   kappa      SPDE parameter kappa of (kappa^2 - Delta) (Eq. for the Matern SPDE); > 0.
  *   prior      prior options; NULL = { gamma = 1, zero-Neumann }.
  *   m          number of observations, >= 0.

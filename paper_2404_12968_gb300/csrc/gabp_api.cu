@@ -18,6 +18,18 @@
 
 #include "gabp.h"
 #include "gabp_internal.h"
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// NVTX range around a public call (header-only NVTX 3: a no-op unless a profiler is attached),
+// so that a timeline shows create / iterate / residual / marginals / warm-start phases
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 using gabp::DevProblem;
 
@@ -689,6 +701,7 @@ const char *gabp_create_error(void) { return t_create_err.c_str(); }
 
 int gabp_create(gabp_ctx **out, gabp_grid grid, double kappa, const gabp_prior *prior, int64_t m,
                 const double *obs_xy, const double *y, const double *noise_var, const gabp_options *opt) {
+    NvtxRange nvtx_range("gabp_create");
     t_create_err.clear();
     if (!out) {
         t_create_err = "out must not be NULL";
@@ -741,6 +754,7 @@ int gabp_create(gabp_ctx **out, gabp_grid grid, double kappa, const gabp_prior *
 }
 
 int gabp_iterate(gabp_ctx *c, int n_iters, double damping) {
+    NvtxRange nvtx_range("gabp_iterate");
     if (!c) return GABP_ERR_ARG;
     if (!(damping >= 0.0 && damping < 1.0)) return fail(c, GABP_ERR_ARG, "damping must be in [0, 1)");
     DeviceGuard g(c->dev);
@@ -821,6 +835,7 @@ int gabp_iterate_early_stop(gabp_ctx *c, int max_iters, double damping, double t
 }
 
 int gabp_residual(gabp_ctx *c, double *rel) {
+    NvtxRange nvtx_range("gabp_residual");
     if (!c || !rel) return c ? fail(c, GABP_ERR_ARG, "rel_residual must not be NULL") : GABP_ERR_ARG;
     DeviceGuard g(c->dev);
     if (!g.ok) return fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
@@ -828,6 +843,7 @@ int gabp_residual(gabp_ctx *c, double *rel) {
 }
 
 int gabp_marginals(gabp_ctx *c, double *mean, double *var) {
+    NvtxRange nvtx_range("gabp_marginals");
     if (!c) return GABP_ERR_ARG;
     if (!mean) return fail(c, GABP_ERR_ARG, "mean must not be NULL");
     DeviceGuard g(c->dev);
@@ -845,6 +861,7 @@ int gabp_marginals(gabp_ctx *c, double *mean, double *var) {
 }
 
 int gabp_warm_start(gabp_ctx *c, const double *mu0, const double *lam0) {
+    NvtxRange nvtx_range("gabp_warm_start");
     if (!c) return GABP_ERR_ARG;
     if (c->p.order == 2) return fail(c, GABP_ERR_STATE, "warm starts are not available for the alpha = 4 prior");
     if (!mu0 || !lam0) return fail(c, GABP_ERR_ARG, "mu0 and lam0 must not be NULL");
@@ -1507,6 +1524,7 @@ int gabp_batch_create(gabp_batch **out, int count, const gabp_problem *problems,
 }
 
 int gabp_batch_iterate(gabp_batch *b, int n_iters, double damping) {
+    NvtxRange nvtx_range("gabp_batch_iterate");
     if (!b) return GABP_ERR_ARG;
     if (!(damping >= 0.0 && damping < 1.0)) return bfail(b, GABP_ERR_ARG, "damping must be in [0, 1)");
     DeviceGuard g(b->dev);
@@ -1765,6 +1783,7 @@ int gabp_mg_create(gabp_mg **out, gabp_ctx *ctx, int levels) {
 }
 
 int gabp_mg_warm_start(gabp_mg *g, double damping, double tol, int max_iters, gabp_mg_stats *stats) {
+    NvtxRange nvtx_range("gabp_mg_warm_start");
     if (!g) return GABP_ERR_ARG;
     if (!(damping >= 0.0 && damping < 1.0)) return mfail(g, GABP_ERR_ARG, "damping must be in [0, 1)");
     if (max_iters < 1) return mfail(g, GABP_ERR_ARG, "max_iters must be >= 1");
@@ -1916,6 +1935,7 @@ int gabp_pw_create(gabp_pw **out, gabp_ctx *ctx) {
 }
 
 int gabp_pw_iterate(gabp_pw *w, int n_iters, double c, double learning_rate) {
+    NvtxRange nvtx_range("gabp_pw_iterate");
     if (!w) return GABP_ERR_ARG;
     if (n_iters < 0 || c == 0.0 || !std::isfinite(c) || !(learning_rate > 0.0 && learning_rate <= 1.0))
         return pfail(w, GABP_ERR_ARG, "n_iters >= 0, c finite and nonzero, learning_rate in (0, 1] required");
@@ -2048,6 +2068,7 @@ void gabp_pw_destroy(gabp_pw *w) {
 }
 
 int gabp_wsnet_warm_start(gabp_ctx *c, gabp_wsnet *net) {
+    NvtxRange nvtx_range("gabp_wsnet_warm_start");
     if (!c || !net) return c ? fail(c, GABP_ERR_ARG, "net must not be NULL") : GABP_ERR_ARG;
     if (gabp::wsnet_device(net) != c->dev) return fail(c, GABP_ERR_ARG, "network and context on different devices");
     if (c->p.order == 2) return fail(c, GABP_ERR_STATE, "warm starts are not available for the alpha = 4 prior");
