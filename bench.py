@@ -396,7 +396,7 @@ def main_accuracy(s, p, res_last: float, iters_done: int):
             "gate": 1e-4}
 
 
-def batch_rate(device: int):
+def batch_rate(device: int, accuracy: bool = True):
     """Iteration rate of the batched solver on the 64-instance configuration (sides log-uniform
     in [128, 1024], 4-32 tracks): every instance iterated in one launch per iteration."""
     import gabp_synth
@@ -413,6 +413,8 @@ def batch_rate(device: int):
         b.iterate(100, DAMPING)
         dt = (time.perf_counter() - t) / 100
         kernel = b.kernel_name
+        if not accuracy:
+            return {"instances": len(probs), "nodes": n, "ms_per_iter": dt * 1e3, "kernel": kernel}
         # accuracy (untimed): the whole batch iterated until every instance's means settle, then
         # the stored instances' means against their exact means
         its = 120 + solve_until_settled(lambda k: b.iterate(k, DAMPING),
@@ -616,8 +618,14 @@ def main():
     ap.add_argument("--kernel", type=int, default=0, help="iteration kernel (gabp.h GABP_KERNEL_*); 0 = auto")
     ap.add_argument("--tile-run", type=int, default=0,
                     help="tiles per run of the TMA kernel's schedule (1..8); 0 = the library's choice")
+    ap.add_argument("--leg", choices=["batch"], default=None,
+                    help="run one side leg alone and print its JSON object (profiling)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.leg == "batch":
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"batch": batch_rate(0, accuracy=not args.no_accuracy)}), flush=True)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         own_arm(args)
