@@ -71,6 +71,9 @@ struct gabp_ctx {
 namespace {
 
 thread_local std::string t_create_err;
+// set while a batch creates its members: rows of the message planes of odd-width problems are
+// padded by one cell (DevProblem::px), so that the batched TMA kernel copies them as tensors
+thread_local bool t_pad_odd_planes = false;
 
 struct DeviceGuard {
     int prev = -1;
@@ -550,6 +553,8 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
     }
     DevProblem &p = c->p;
     p.nx = nx;
+    p.px = (t_pad_odd_planes && nx % 2 && alpha == 2) ? nx + 1 : nx;
+    p.pn = (int64_t)p.px * ny;
     p.ny = ny;
     p.n = n;
     p.m = m;
@@ -578,8 +583,11 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
     int rc;
     void *q;
     for (int b = 0; b < 2; ++b) {
-        if ((rc = dalloc(c, &p.P[b], (size_t)p.planes * (size_t)n * 2 * T, "alloc prior messages"))) return rc;
+        if ((rc = dalloc(c, &p.P[b], (size_t)p.planes * (size_t)p.pn * 2 * T, "alloc prior messages"))) return rc;
         if ((rc = dalloc(c, &p.O[b], 8 * (size_t)m * T, "alloc obs messages"))) return rc;
+        // padding cells: (0, 0) in both buffers, never written by a kernel
+        if (p.px != nx)
+            CK(cudaMemsetAsync(p.P[b], 0, (size_t)p.planes * (size_t)p.pn * 2 * T, c->stream), "memset planes");
     }
     if ((rc = dalloc(c, &q, (size_t)m * sizeof(int), "alloc obs base"))) return rc;
     p.obase = (const int *)q;
@@ -934,6 +942,7 @@ int64_t gabp_message_bytes(const gabp_ctx *c) {
 
 int gabp_get_messages(gabp_ctx *c, void *buf) {
     if (!c || !buf) return c ? fail(c, GABP_ERR_ARG, "buffer must not be NULL") : GABP_ERR_ARG;
+    if (c->p.px != c->p.nx) return fail(c, GABP_ERR_STATE, "padded message layout");   // batch members only
     DeviceGuard g(c->dev);
     const size_t T = tsize(c);
     const size_t pb = 2 * (size_t)c->p.planes * (size_t)c->p.n * T, ob = 8 * (size_t)c->p.m * T;
@@ -945,6 +954,7 @@ int gabp_get_messages(gabp_ctx *c, void *buf) {
 
 int gabp_set_messages(gabp_ctx *c, const void *buf) {
     if (!c || !buf) return c ? fail(c, GABP_ERR_ARG, "buffer must not be NULL") : GABP_ERR_ARG;
+    if (c->p.px != c->p.nx) return fail(c, GABP_ERR_STATE, "padded message layout");   // batch members only
     DeviceGuard g(c->dev);
     const size_t T = tsize(c);
     const size_t pb = 2 * (size_t)c->p.planes * (size_t)c->p.n * T, ob = 8 * (size_t)c->p.m * T;
@@ -1157,7 +1167,7 @@ int batch_encode_maps(gabp_batch *b, int ty) {
                                  sizeof(int) * (size_t)nxi, pi.ny, cudaMemcpyDeviceToDevice, b->stream),
                "padded index copy");
         }
-        const int parts = (nxi % 2 == 0 ? gabp::TMA_MAP_PLANES : 0) | gabp::TMA_MAP_OPTR;
+        const int parts = (pi.px % 2 == 0 ? gabp::TMA_MAP_PLANES : 0) | gabp::TMA_MAP_OPTR;
         gabp::TmaMaps m{};
         BK(gabp::make_tma_maps(pi, 30, ty, m, parts, b->optr_pad[i], pitch), "tensor map encode");
         maps[i].planes[0] = m.planes[0];
@@ -1445,7 +1455,9 @@ int batch_create_impl(gabp_batch *b, int count, const gabp_problem *problems) {
         const gabp_problem &pr = problems[i];
         gabp_prior prior{pr.gamma > 0.0 ? pr.gamma : 1.0, 0, 2};
         gabp_ctx *c = nullptr;
+        t_pad_odd_planes = true;
         const int rc = gabp_create(&c, pr.grid, pr.kappa, &prior, pr.m, pr.obs_xy, pr.y, pr.noise_var, &io);
+        t_pad_odd_planes = false;
         if (rc) return bfail(b, rc, "problem " + std::to_string(i) + ": " + gabp_create_error());
         b->inst.push_back(c);
     }

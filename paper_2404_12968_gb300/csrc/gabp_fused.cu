@@ -39,7 +39,6 @@ __global__ void __launch_bounds__(FT) k_fused(DevProblem p, int src, T beta) {
     int *rpre = rstart + (TY + 1);                                                     // [TY+1]
 
     const int nx = p.nx, ny = p.ny;
-    const int64_t n = p.n;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const T2<T> *P = (const T2<T> *)p.P[src];
     T2<T> *Q = (T2<T> *)p.P[src ^ 1];
@@ -56,7 +55,7 @@ __global__ void __launch_bounds__(FT) k_fused(DevProblem p, int src, T beta) {
         T2<T> val;
         val.x = T(0);
         val.y = T(0);
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) val = P[d * n + (int64_t)gy * nx + gx];
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) val = P[d * p.pn + (int64_t)gy * p.px + gx];
         sm[q] = val;
     }
     // observation ranges of the tile's base rows (cells [x0, x0+TX) of rows y0 .. y0+TY-1)
@@ -147,7 +146,7 @@ __global__ void __launch_bounds__(FT) k_fused(DevProblem p, int src, T beta) {
                 out.x = T(0);
                 out.y = T(0);
             }
-            Q[u * n + c] = out;
+            Q[u * p.pn + (int64_t)gy * p.px + gx] = out;
         }
     }
 

@@ -241,17 +241,17 @@ __device__ __forceinline__ float2 damp2(float2 old, float2 fresh, float2 beta2) 
 
 // Update of the rank-1 factor of one cell (row of L, Eq. 5 / App. A): cavities of its five
 // slots from the compensated beliefs, the factor-to-variable messages, damping, and a
-// streaming store of the five outgoing messages (planes n apart).  Slots with a = 0 (missing
+// streaming store of the five outgoing messages (planes pn apart).  Slots with a = 0 (missing
 // neighbours at the grid border) send (0, 0).
 __device__ __forceinline__ void cell_factor(const float (&a)[5], const Belief2 *const (&bs)[5], const float2 (&own)[5],
-                                            float var, float r, float2 beta2, float2 *q, int64_t n) {
+                                            float var, float r, float2 beta2, float2 *q, int64_t pn) {
     float2 cav[5];
 #pragma unroll
     for (int u = 0; u < 5; ++u) cav[u] = a[u] != 0.f ? cavity2(*bs[u], own[u]) : f2(0.f, 1.f);
     float2 msg[5];
     factor_messages2<5, true>(a, var, r, cav, msg);
 #pragma unroll
-    for (int u = 0; u < 5; ++u) __stcs(q + u * n, a[u] != 0.f ? damp2(own[u], msg[u], beta2) : f2(0.f, 0.f));
+    for (int u = 0; u < 5; ++u) __stcs(q + u * pn, a[u] != 0.f ? damp2(own[u], msg[u], beta2) : f2(0.f, 0.f));
 }
 
 // RW belief-window rows (and up to RW cell rows) per warp: (TY + 2) / RW warps per block.
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         const DevProblem &q = ba.table[prob];
         const int qnx = q.nx, qny = q.ny;
         const int x0 = w.y * TTX, y0 = w.z * TY;
-        const bool tma_planes = qnx % 2 == 0;
+        const bool tma_planes = q.px % 2 == 0;
         if (tid == 0) {
             mbar_expect_tx_only(bar, (tma_planes ? LY::plane_bytes : 0u) + LY::optr_bytes);
             if (tma_planes) tma_load_3d(smem_addr(base), &ba.maps[prob].planes[src], 2 * (x0 - 2), y0 - 2, 0, bar);
@@ -334,12 +334,12 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         }
         if (!tma_planes) {
             const float2 *P = (const float2 *)q.P[src];
-            const int64_t qn = q.n;
+            const int64_t qn = q.pn;
             const uint32_t dp = smem_addr(base);
             for (int row = warp; row < 5 * RY; row += TW) {   // [5][RY][RX] cells from (x0 - 2, y0 - 2)
                 const int d = row / RY, gy = y0 - 2 + (row - d * RY);
                 const bool rin = gy >= 0 && gy < qny;
-                const float2 *src_row = P + d * qn + (int64_t)(rin ? gy : 0) * qnx;
+                const float2 *src_row = P + d * qn + (int64_t)(rin ? gy : 0) * q.px;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int cx = lane + 32 * h, gx = x0 - 2 + cx;
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         const bool carry = BATCH ? w.w != 0 : wk.r > 0;
         const DevProblem &cur = BATCH ? ba.table[w.x] : p;
         const int nx = cur.nx, ny = cur.ny;
-        const int64_t n = cur.n, m = cur.m;
+        const int64_t pn = cur.pn, m = cur.m;
         float2 *const Q = (float2 *)cur.P[src ^ 1];
         const float *const O = (const float *)cur.O[src];
         float *const OQ = (float *)cur.O[src ^ 1];
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         for (int ty = warp; ty < TY; ty += TW) {
             const int tx = lane, gx = x0 + tx, gy = y0 + ty;
             if (tx >= TTX || gx >= nx || gy >= ny) continue;
-            const int64_t c = (int64_t)gy * nx + gx;
+            const int64_t c = (int64_t)gy * nx + gx, pc = (int64_t)gy * cur.px + gx;
             const Belief2 *bs[5] = {&sb[(ty + 1) * BX + tx + 1], &sb[(ty + 1) * BX + tx],
                                           &sb[(ty + 1) * BX + tx + 2], &sb[ty * BX + tx + 1],
                                           &sb[(ty + 2) * BX + tx + 1]};
@@ -553,11 +553,11 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
             if (gx > 0 && gx < nx - 1 && gy > 0 && gy < ny - 1) {
                 // interior cell: literal coefficients, so the compiler folds the -1 factors
                 const float a[5] = {aC_in, -1.f, -1.f, -1.f, -1.f};
-                cell_factor(a, bs, own, var_prior, tg, beta2, Q + c, n);
+                cell_factor(a, bs, own, var_prior, tg, beta2, Q + pc, pn);
             } else {
                 const float a[5] = {cur.aC_f[grid_degree(gy, gx, nx, ny)], gx > 0 ? -1.f : 0.f,
                                     gx < nx - 1 ? -1.f : 0.f, gy > 0 ? -1.f : 0.f, gy < ny - 1 ? -1.f : 0.f};
-                cell_factor(a, bs, own, var_prior, tg, beta2, Q + c, n);
+                cell_factor(a, bs, own, var_prior, tg, beta2, Q + pc, pn);
             }
         }
         if (m > 0) {
@@ -685,8 +685,9 @@ bool tma_shape_supported(int tx, int ty) { return tx == TTX && (ty == 14 || ty =
 
 bool tma_problem_supported(const DevProblem &p) { return p.prec == 0 && p.nx % 4 == 0 && p.nx >= 4; }
 
-// Tensor maps of both message buffers (3-D: 2 nx floats x ny rows x 5 planes) and of the
-// observation index (2-D: nx x ny int32 of optr[0..n)), with boxes for the tile shape.
+// Tensor maps of both message buffers (3-D: 2 nx floats x ny rows x 5 planes, rows px cells
+// apart) and of the observation index (2-D: nx x ny int32 of optr[0..n)), with boxes for the
+// tile shape.
 cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps, int parts, const int *optr,
                           int optr_pitch) {
     maps.valid = false;
@@ -695,7 +696,7 @@ cudaError_t make_tma_maps(const DevProblem &p, int tx, int ty, TmaMaps &maps, in
     if (!enc) return cudaErrorNotSupported;
     for (int b = 0; b < 2 && (parts & TMA_MAP_PLANES); ++b) {
         cuuint64_t dims[3] = {(cuuint64_t)2 * p.nx, (cuuint64_t)p.ny, 5};
-        cuuint64_t strides[2] = {(cuuint64_t)p.nx * 8, (cuuint64_t)p.n * 8};
+        cuuint64_t strides[2] = {(cuuint64_t)p.px * 8, (cuuint64_t)p.pn * 8};
         cuuint32_t box[3] = {(cuuint32_t)(2 * (tx + 4)), (cuuint32_t)(ty + 4), 5};
         cuuint32_t es[3] = {1, 1, 1};
         CUresult r = enc(&maps.planes[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p.P[b], dims, strides, box, es,

@@ -26,7 +26,13 @@ struct DevProblem {
     float init_n_f;      // cold-start precision gamma (-1)^2 of a neighbour slot, as float
     const float2 *owdf;  // FP32 contexts: 4 * m observation weights as double-float (hi, lo) pairs
     const float2 *oysdf; // FP32 contexts: 2 * m (y, 1/sigma^2) as double-float pairs
-    void *P[2];          // prior messages, ping-pong: 5 * n (eta, Lambda) pairs
+    void *P[2];          // prior messages, ping-pong: planes * pn (eta, Lambda) pairs
+    // layout of the prior message planes: node (i, j) of plane d at d * pn + i * px + j.  px = nx
+    // except for the members of a batch with an odd width, whose rows are padded to px = nx + 1
+    // so that every row starts on a 16-byte boundary (tensor copies); the padding cells hold
+    // (0, 0) in both buffers.  pn = px * ny.
+    int px;
+    int64_t pn;
     void *O[2];          // observation messages, ping-pong: per observation (eta, Lambda) of corners 0..3, interleaved
     const int *obase;    // m base-cell indices (sorted ascending)
     const void *ow;      // 4 * m bilinear weights (T)
@@ -52,6 +58,11 @@ struct DevProblem {
     const double *ptgt64;
     const float2 *ptgtdf;
 };
+
+// plane index of node (i, j)
+__host__ __device__ __forceinline__ int64_t plane_at(const DevProblem &p, int i, int j) {
+    return (int64_t)i * p.px + j;
+}
 
 // Prior constants in the kernel's precision.  FP32 kernels read the values rounded once on the
 // host (the same roundings as converting the FP64 values on the device, without FP64

@@ -49,13 +49,13 @@ template <typename T> __global__ void k_beliefs(DevProblem p, int src) {
     node_rc(v, nx, i, j);
     const T2<T> *P = (const T2<T> *)p.P[src];
     const T *O = (const T *)p.O[src];
-    const int64_t n = p.n;
-    T2<T> q = P[DIR_C * n + v];
+    const int64_t pn = p.pn, pv = plane_at(p, i, j);
+    T2<T> q = P[DIR_C * pn + pv];
     CompSum<T> se(q.x), sl(q.y);
-    if (j > 0) { q = P[DIR_E * n + v - 1]; se.add(q.x); sl.add(q.y); }
-    if (j < nx - 1) { q = P[DIR_W * n + v + 1]; se.add(q.x); sl.add(q.y); }
-    if (i > 0) { q = P[DIR_N * n + v - nx]; se.add(q.x); sl.add(q.y); }
-    if (i < ny - 1) { q = P[DIR_S * n + v + nx]; se.add(q.x); sl.add(q.y); }
+    if (j > 0) { q = P[DIR_E * pn + pv - 1]; se.add(q.x); sl.add(q.y); }
+    if (j < nx - 1) { q = P[DIR_W * pn + pv + 1]; se.add(q.x); sl.add(q.y); }
+    if (i > 0) { q = P[DIR_N * pn + pv - p.px]; se.add(q.x); sl.add(q.y); }
+    if (i < ny - 1) { q = P[DIR_S * pn + pv + p.px]; se.add(q.x); sl.add(q.y); }
     if (p.m > 0) {
         const int *optr = p.optr;
         // bases (j-1, i), (j, i) then (j-1, i-1), (j, i-1): corners 1, 0, 3, 2
@@ -83,7 +83,7 @@ template <typename T> __global__ void k_prior(DevProblem p, int src, T beta) {
     const int nx = p.nx, ny = p.ny;
     int i, j;
     node_rc(c, nx, i, j);
-    const int64_t n = p.n;
+    const int64_t pn = p.pn, pc = plane_at(p, i, j);
     const T2<T> *P = (const T2<T> *)p.P[src];
     T2<T> *Q = (T2<T> *)p.P[src ^ 1];
     const int deg = grid_degree(i, j, nx, ny);
@@ -94,7 +94,7 @@ template <typename T> __global__ void k_prior(DevProblem p, int src, T beta) {
     T lam[5], eta[5];
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
-        own[u] = P[u * n + c];
+        own[u] = P[u * pn + pc];
         if (a[u] != T(0)) {
             cavity(load_belief<T>(p, node[u]), own[u].x, own[u].y, eta[u], lam[u]);
         } else {
@@ -115,7 +115,7 @@ template <typename T> __global__ void k_prior(DevProblem p, int src, T beta) {
             out.x = T(0);
             out.y = T(0);
         }
-        Q[u * n + c] = out;
+        Q[u * pn + pc] = out;
     }
 }
 
@@ -325,7 +325,7 @@ template <typename T> __global__ void k_init_prior(DevProblem p, int dst, int pa
         if constexpr (sizeof(T) == 4) cold = u == 0 ? p.init_c_f[deg] : p.init_n_f;
         else cold = u == 0 ? p.gamma * p.aC[deg] * p.aC[deg] : p.gamma * -1.0 * -1.0;
         o.y = !has[u] ? T(0) : (paper ? T(1e-8) : cold);
-        Q[u * p.n + c] = o;
+        Q[u * p.pn + plane_at(p, i, j)] = o;
     }
 }
 
@@ -377,7 +377,7 @@ __global__ void k_init_warm_prior(DevProblem p, int dst, const double *mu0, cons
             o.x = T(mu0[node[u]] * L);
             o.y = T(L);
         }
-        Q[u * p.n + c] = o;
+        Q[u * p.pn + plane_at(p, i, j)] = o;
     }
 }
 
@@ -818,7 +818,7 @@ __global__ void k_init_nodes_prior(DevProblem p, int dst, const float2 *nm) {
     const int64_t node[5] = {c, c - 1, c + 1, c - nx, c + nx};
     float2 *Q = (float2 *)p.P[dst];
 #pragma unroll
-    for (int u = 0; u < 5; ++u) Q[u * p.n + c] = exists[u] ? nm[node[u]] : make_float2(0.f, 0.f);
+    for (int u = 0; u < 5; ++u) Q[u * p.pn + plane_at(p, i, j)] = exists[u] ? nm[node[u]] : make_float2(0.f, 0.f);
 }
 __global__ void k_init_nodes_obs(DevProblem p, int dst, const float2 *nm) {
     const int64_t k = gtid();
@@ -857,7 +857,7 @@ cudaError_t launch_split_iteration(const DevProblem &p, int src, double beta, cu
 }
 
 cudaError_t launch_l2_iteration(const DevProblem &p, int src, double beta, cudaStream_t st) {
-    if (p.order != 2) return cudaErrorInvalidValue;
+    if (p.order != 2 || p.px != p.nx) return cudaErrorInvalidValue;   // alpha = 4 planes are unpadded
     if (p.prec) {
         k_beliefs_l2<double><<<row_grid(p.nx, p.ny), TPB, 0, st>>>(p, src);
         k_prior_l2<double><<<row_grid(p.nx, p.ny), TPB, 0, st>>>(p, src, beta);
@@ -940,7 +940,7 @@ cudaError_t launch_rhs_norm(const DevProblem &p, cudaStream_t st) {
 template <typename T> __global__ void k_msg_change(DevProblem p, int cur) {
     const T *a = (const T *)p.P[cur], *b = (const T *)p.P[cur ^ 1];
     const T *oa = (const T *)p.O[cur], *ob = (const T *)p.O[cur ^ 1];
-    const int64_t np_ = 2 * (int64_t)p.planes * p.n, no = 8 * p.m;
+    const int64_t np_ = 2 * (int64_t)p.planes * p.pn, no = 8 * p.m;   // padding cells: (0, 0) in both
     const int64_t stride = (int64_t)gridDim.x * TPB;
     T acc = T(0);
     for (int64_t i = gtid(); i < np_; i += stride) acc += fabs(a[i] - b[i]);

@@ -26,12 +26,13 @@ struct Row5 {
     float2 m[5];   // C, W, E, S, N
 };
 
-__device__ __forceinline__ Row5 load_row(const float2 *P, int64_t n, int nx, int ny, int x, int y) {
+// planes: node (x, y) of plane d at d * pn + y * px + x (px >= nx: the padded row pitch)
+__device__ __forceinline__ Row5 load_row(const float2 *P, int64_t pn, int px, int nx, int ny, int x, int y) {
     Row5 r;
     if (x >= 0 && x < nx && y >= 0 && y < ny) {
-        const int64_t c = (int64_t)y * nx + x;
+        const int64_t c = (int64_t)y * px + x;
 #pragma unroll
-        for (int d = 0; d < 5; ++d) r.m[d] = __ldg(P + d * n + c);
+        for (int d = 0; d < 5; ++d) r.m[d] = __ldg(P + d * pn + c);
     } else {
 #pragma unroll
         for (int d = 0; d < 5; ++d) r.m[d] = make_float2(0.f, 0.f);
@@ -39,8 +40,8 @@ __device__ __forceinline__ Row5 load_row(const float2 *P, int64_t n, int nx, int
     return r;
 }
 
-__device__ __forceinline__ float2 load_one(const float2 *P, int64_t n, int nx, int ny, int d, int x, int y) {
-    if (x >= 0 && x < nx && y >= 0 && y < ny) return __ldg(P + d * n + (int64_t)y * nx + x);
+__device__ __forceinline__ float2 load_one(const float2 *P, int64_t pn, int px, int nx, int ny, int d, int x, int y) {
+    if (x >= 0 && x < nx && y >= 0 && y < ny) return __ldg(P + d * pn + (int64_t)y * px + x);
     return make_float2(0.f, 0.f);
 }
 
@@ -92,10 +93,10 @@ struct RowState {
 
 __device__ __forceinline__ RowRaw load_raw(const DevProblem &p, const float2 *P, int lane, int x, int y) {
     RowRaw r;
-    r.msg = load_row(P, p.n, p.nx, p.ny, x, y);
+    r.msg = load_row(P, p.pn, p.px, p.nx, p.ny, x, y);
     r.fx = make_float2(0.f, 0.f);
-    if (lane == 0) r.fx = load_one(P, p.n, p.nx, p.ny, DIR_E, x - 1, y);
-    if (lane == 31) r.fx = load_one(P, p.n, p.nx, p.ny, DIR_W, x + 1, y);
+    if (lane == 0) r.fx = load_one(P, p.pn, p.px, p.nx, p.ny, DIR_E, x - 1, y);
+    if (lane == 31) r.fx = load_one(P, p.pn, p.px, p.nx, p.ny, DIR_W, x + 1, y);
     r.o0 = r.ox = 0;
     if (p.m > 0) {
         r.o0 = load_optr(p.optr, p.nx, p.ny, x, y);
@@ -167,7 +168,7 @@ struct WarpRing {
 // the same either way).
 __device__ __forceinline__ void cell_factor(const float (&a)[5], float var_prior, float r, float beta,
                                             const Row5 &own, const Belief<float> *const (&bs)[5],
-                                            float2 *Q, int64_t n, int64_t c) {
+                                            float2 *Q, int64_t pn, int64_t pc) {
     float lam[5], eta[5];
 #pragma unroll
     for (int u = 0; u < 5; ++u) {
@@ -190,7 +191,7 @@ __device__ __forceinline__ void cell_factor(const float (&a)[5], float var_prior
             out.x = 0.f;
             out.y = 0.f;
         }
-        __stcs(Q + u * n + c, out);
+        __stcs(Q + u * pn + pc, out);
     }
 }
 
@@ -262,7 +263,7 @@ template <int H>
 __device__ __forceinline__ void sweep_strip(const DevProblem &p, WarpRing &ring, int lane, int strip, int src,
                                             float beta) {
     const int nx = p.nx, ny = p.ny;
-    const int64_t n = p.n;
+    const int64_t pn = p.pn;
     const int ncs = (nx + SW - 1) / SW;
     const float2 *P = (const float2 *)p.P[src];
     float2 *Q = (float2 *)p.P[src ^ 1];
@@ -306,16 +307,16 @@ __device__ __forceinline__ void sweep_strip(const DevProblem &p, WarpRing &ring,
         const Belief<float> b_e = shfl_down_b(b_cur);
         if (owned) {
             const Belief<float> *const bs[5] = {&b_cur, &b_w, &b_e, &b_prev, &b_next};
-            const int64_t c = (int64_t)r * nx + x;
+            const int64_t c = (int64_t)r * nx + x, pc = (int64_t)r * p.px + x;
             const float tg = p.ptgt ? ((const float *)p.ptgt)[c] : 0.f;
             if (x_inner && r > 0 && r < ny - 1) {
                 const float a[5] = {aC_in, -1.f, -1.f, -1.f, -1.f};
-                cell_factor(a, var_prior, tg, beta, s_0.msg, bs, Q, n, c);
+                cell_factor(a, var_prior, tg, beta, s_0.msg, bs, Q, pn, pc);
             } else {
                 const int deg = grid_degree(r, x, nx, ny);
                 const float a[5] = {p.aC_f[deg], x > 0 ? -1.f : 0.f, x < nx - 1 ? -1.f : 0.f,
                                     r > 0 ? -1.f : 0.f, r < ny - 1 ? -1.f : 0.f};
-                cell_factor(a, var_prior, tg, beta, s_0.msg, bs, Q, n, c);
+                cell_factor(a, var_prior, tg, beta, s_0.msg, bs, Q, pn, pc);
             }
         }
         if (p.m > 0 && ((r - y0) % OBS_BATCH == OBS_BATCH - 1 || r == y1 - 1)) {
