@@ -272,9 +272,10 @@ void gabp_destroy(gabp_ctx *ctx);
  * uneven sizes iterated together.  Every iteration of the whole batch is ONE persistent
  * kernel launch over the work items of all active problems (FP32 messages), replayed from a
  * CUDA graph; the per-problem residual checks are a second graph.  Two kernels serve batches:
- * the TMA kernel over 30 x 22 or 30 x 30 tiles (tensor copies for problems with nx a multiple of 4,
- * cp.async copies of the same tiles for the others) and the column-sweep kernel over strips of
- * 16, 32, 64 or 128 rows.  The autotuner times every candidate on this batch at create time
+ * the TMA kernel over 30 x 14, 30 x 22 or 30 x 30 tiles (tensor copies of every problem's tiles:
+ * the message planes of a problem of odd width are stored with rows padded to an even pitch,
+ * its observation index in a copy with rows padded to a multiple of 4) and the column-sweep
+ * kernel over strips of 16, 32, 64 or 128 rows.  The autotuner times every candidate on this batch at create time
  * and keeps the fastest (cached per device and batch shape in the file named by
  * GABP_AUTOTUNE_CACHE, if set).  Messages are bit-identical to single-problem contexts
  * whichever kernel runs.
@@ -296,7 +297,7 @@ typedef struct {
  * opt: NULL = defaults; precision must be GABP_FP32; opt->kernel GABP_KERNEL_AUTO (the
  * autotuner's choice among both kernels), GABP_KERNEL_TMA or GABP_KERNEL_SWEEP (the
  * autotuner's choice among that kernel's shapes; others: GABP_ERR_ARG); opt->tile_y, if
- * non-zero, fixes the configuration instead of the autotuner: 22 or 30 = the TMA kernel's tile
+ * non-zero, fixes the configuration instead of the autotuner: 14, 22 or 30 = the TMA kernel's tile
  * height, 16, 32, 64 or 128 = the sweep kernel's strip height; tol, check_every (rounded up
  * to even), max_iters, device and stream apply
  * to the whole batch.  Host arrays are read during the call only.  Errors as for gabp_create;
@@ -326,7 +327,7 @@ int gabp_batch_marginals(gabp_batch *b, int index, double *mean, double *var);
  * is GABP_KERNEL_TMA or GABP_KERNEL_SWEEP, tile_x x tile_y its tile or strip shape). */
 int gabp_batch_get_stats(const gabp_batch *b, int index, gabp_stats *stats);
 
-/* Tile or strip height in use (chosen by the autotuner or opt.tile_y): 22 or 30 for the TMA
+/* Tile or strip height in use (chosen by the autotuner or opt.tile_y): 14, 22 or 30 for the TMA
  * kernel, 16, 32, 64 or 128 for the sweep kernel. */
 int gabp_batch_strip_height(const gabp_batch *b);
 

@@ -262,7 +262,7 @@ class Batch:
 
     @property
     def strip_height(self) -> int:
-        """Tile height of the TMA kernel (22, 30) or strip height of the sweep kernel."""
+        """Tile height of the TMA kernel (14, 22, 30) or strip height of the sweep kernel."""
         return gabp_batch_strip_height(self.handle)
 
     @property

@@ -1066,7 +1066,7 @@ void batch_drop_graphs(gabp_batch *b) {
 
 int tma_tiles(const gabp::DevProblem &p, int ty) { return ((p.nx + 29) / 30) * ((p.ny + ty - 1) / ty); }
 
-constexpr int TMA_MIN_TY = 22;   // the smallest batched TMA tile height (sizes the work-item list)
+constexpr int TMA_MIN_TY = 14;   // the smallest batched TMA tile height (sizes the work-item list)
 
 cudaError_t batch_launch(gabp_batch *b, int src, double beta, cudaStream_t st) {
     const int count = (int)b->inst.size();
@@ -1371,7 +1371,7 @@ int batch_autotune(gabp_batch *b, int kernels) {
     if (!best) {
         std::vector<int> cands;
         if (kernels != GABP_KERNEL_TMA) cands.insert(cands.end(), {16, 32, 64, 128});
-        if (kernels != GABP_KERNEL_SWEEP) cands.insert(cands.end(), {22, 30});
+        if (kernels != GABP_KERNEL_SWEEP) cands.insert(cands.end(), {14, 22, 30});
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
         BK(cudaEventCreate(&e0), "event");
@@ -1441,11 +1441,11 @@ int batch_create_impl(gabp_batch *b, int count, const gabp_problem *problems) {
     if (kreq != GABP_KERNEL_AUTO && kreq != GABP_KERNEL_TMA && kreq != GABP_KERNEL_SWEEP)
         return bfail(b, GABP_ERR_ARG, "batches run the TMA or the sweep kernel");
     if (kreq == GABP_KERNEL_TMA && ty && !gabp::tma_batch_shape_supported(ty))
-        return bfail(b, GABP_ERR_ARG, "the batched TMA kernel uses 30 x 22 or 30 x 30 tiles");
+        return bfail(b, GABP_ERR_ARG, "the batched TMA kernel uses 30 x 14, 30 x 22 or 30 x 30 tiles");
     if (kreq == GABP_KERNEL_SWEEP && ty && !gabp::sweep_shape_supported(ty))
         return bfail(b, GABP_ERR_ARG, "strip height must be 16, 32, 64 or 128");
     if (kreq == GABP_KERNEL_AUTO && ty && !gabp::tma_batch_shape_supported(ty) && !gabp::sweep_shape_supported(ty))
-        return bfail(b, GABP_ERR_ARG, "strip height must be 16, 32, 64 or 128 (sweep) or 22, 30 (TMA)");
+        return bfail(b, GABP_ERR_ARG, "strip height must be 16, 32, 64 or 128 (sweep) or 14, 22, 30 (TMA)");
     gabp_options io = b->opt;
     io.stream = b->stream;
     io.kernel = GABP_KERNEL_SWEEP;

@@ -86,28 +86,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Expected transaction bytes of the current phase, without an arrival.
-__device__ __forceinline__ void mbar_expect_tx_only(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Asynchronous copy of `size` (4 or 8) bytes, of which the first `src_bytes` are read from
-// global memory and the rest zero-filled (src_bytes = 0: a zero, the address is not read).
-template <int SIZE> __device__ __forceinline__ void cp_async_zfill(uint32_t dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"(SIZE), "r"(src_bytes)
-                 : "memory");
-}
-
-// The mbarrier's current phase also waits for this thread's earlier cp.async copies (its
-// pending count is raised now and lowered when they have landed: no net arrival).
-__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
-    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
-
 // Bounded wait on phase `parity` of an mbarrier: gives up after `limit` clock cycles
 // (default 2^32, about two seconds).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = 1LL << 32) {
@@ -311,52 +289,23 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
         tma_load_2d(smem_addr(base + a128(LY::plane_bytes)), &moptr, (x0 - 2) & ~3, y0 - 2, bar);
     };
 
-    // BATCH (every thread; a stage barrier counts one arrival per warp, made by its lane 0 after
-    // the warp's own copies): the observation index of every problem (its rows padded to a
-    // 16-byte pitch where nx is not a multiple of 4) and the message planes of a problem with nx
-    // even (16-byte row strides) come by the tensor copies of its own maps (thread 0 registers
-    // their bytes first); the planes of an odd width by cp.async copies of the same box (a warp
-    // per box row), zero-filled outside the grid as the tensor copies are, each thread's copies
-    // tracked by the barrier
+    // BATCH (thread 0): the message planes and the observation index of the tile's problem by
+    // the tensor copies of its own maps (every member's plane rows are padded to an even pitch,
+    // its index rows to a multiple of 4 ints, so both have 16-byte row strides)
     auto fill = [&](int stage, int item) {
+        if (tid != 0) return;
         unsigned char *base = smem + stage * LY::stage;
         const uint32_t bar = smem_addr(&bars[stage]);
         const int4 w = locate(item);
         const int prob = w.x;
-        const DevProblem &q = ba.table[prob];
-        const int qnx = q.nx, qny = q.ny;
         const int x0 = w.y * TTX, y0 = w.z * TY;
-        const bool tma_planes = q.px % 2 == 0;
-        if (tid == 0) {
-            mbar_expect_tx_only(bar, (tma_planes ? LY::plane_bytes : 0u) + LY::optr_bytes);
-            if (tma_planes) tma_load_3d(smem_addr(base), &ba.maps[prob].planes[src], 2 * (x0 - 2), y0 - 2, 0, bar);
-            tma_load_2d(smem_addr(base + a128(LY::plane_bytes)), &ba.maps[prob].optr, (x0 - 2) & ~3, y0 - 2, bar);
-        }
-        if (!tma_planes) {
-            const float2 *P = (const float2 *)q.P[src];
-            const int64_t qn = q.pn;
-            const uint32_t dp = smem_addr(base);
-            for (int row = warp; row < 5 * RY; row += TW) {   // [5][RY][RX] cells from (x0 - 2, y0 - 2)
-                const int d = row / RY, gy = y0 - 2 + (row - d * RY);
-                const bool rin = gy >= 0 && gy < qny;
-                const float2 *src_row = P + d * qn + (int64_t)(rin ? gy : 0) * q.px;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int cx = lane + 32 * h, gx = x0 - 2 + cx;
-                    if (cx < RX) {
-                        const bool in = rin && gx >= 0 && gx < qnx;
-                        cp_async_zfill<8>(dp + 8u * (row * RX + cx), in ? src_row + gx : P, in ? 8u : 0u);
-                    }
-                }
-            }
-            cp_async_arrive(bar);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar);
+        mbar_expect_tx(bar, LY::plane_bytes + LY::optr_bytes);
+        tma_load_3d(smem_addr(base), &ba.maps[prob].planes[src], 2 * (x0 - 2), y0 - 2, 0, bar);
+        tma_load_2d(smem_addr(base + a128(LY::plane_bytes)), &ba.maps[prob].optr, (x0 - 2) & ~3, y0 - 2, bar);
     };
 
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(smem_addr(&bars[s]), BATCH ? TW : 1);
+        for (int s = 0; s < S; ++s) mbar_init(smem_addr(&bars[s]), 1);
         mbar_init(smem_addr(&bars[S]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -768,13 +717,14 @@ cudaError_t launch_batch_cfg(const TmaBatchArgs &ba, const DevProblem &first, in
     return cudaGetLastError();
 }
 
-bool tma_batch_shape_supported(int ty) { return ty == 22 || ty == 30; }
+bool tma_batch_shape_supported(int ty) { return ty == 14 || ty == 22 || ty == 30; }
 
 int tma_batch_grid(int ty, int max_tiles) {
     int grid = 0;
+    if (ty == 14 && persistent_grid<14, 2, 1, true>(grid) != cudaSuccess) return 0;
     if (ty == 22 && persistent_grid<22, 2, 1, true>(grid) != cudaSuccess) return 0;
     if (ty == 30 && persistent_grid<30, 2, 1, true>(grid) != cudaSuccess) return 0;
-    if (ty != 22 && ty != 30) return 0;
+    if (!tma_batch_shape_supported(ty)) return 0;
     return max_tiles < grid ? max_tiles : grid;
 }
 
@@ -785,6 +735,7 @@ cudaError_t launch_tma_batch(const TmaBatchArgs &ba, const DevProblem &first, in
                              double beta, cudaStream_t st) {
     if (max_tiles <= 0) return cudaSuccess;
     if (!ba.maps || !ba.table || !ba.items || !ba.nitems || !ba.err || first.nx < 1) return cudaErrorInvalidValue;
+    if (ty == 14) return launch_batch_cfg<14>(ba, first, max_tiles, src, beta, st);
     if (ty == 22) return launch_batch_cfg<22>(ba, first, max_tiles, src, beta, st);
     if (ty == 30) return launch_batch_cfg<30>(ba, first, max_tiles, src, beta, st);
     return cudaErrorInvalidValue;

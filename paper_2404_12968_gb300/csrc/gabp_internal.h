@@ -187,7 +187,7 @@ struct TmaBatchArgs {
     int *err;
     int debug_stall;   // test hook, as DevProblem::debug_stall
 };
-bool tma_batch_shape_supported(int ty);   // tile heights of the batched TMA kernel (22, 30)
+bool tma_batch_shape_supported(int ty);   // tile heights of the batched TMA kernel (14, 22, 30)
 int tma_batch_grid(int ty, int max_tiles);  // blocks of its launch (0 on error)
 cudaError_t launch_tma_batch(const TmaBatchArgs &ba, const DevProblem &first, int ty, int max_tiles, int src,
                              double beta, cudaStream_t st);

@@ -30,7 +30,7 @@ def _mixed_batch():
     return probs
 
 
-@pytest.mark.parametrize("kernel,tile_y", [("sweep", 32), ("tma", 22), ("tma", 30)])
+@pytest.mark.parametrize("kernel,tile_y", [("sweep", 32), ("tma", 14), ("tma", 22), ("tma", 30)])
 def test_batch_lockstep_bit_identical_to_single_contexts(kernel, tile_y):
     from paper_2404_12968_gb300 import Batch, GABP_KERNEL_SWEEP, GABP_KERNEL_TMA
     probs = _mixed_batch()
@@ -75,7 +75,7 @@ def test_batch_64_instances_config(orc):
     assert len(probs) == 64
     with Batch(probs, tol=1e-5) as b:   # the autotuner's choice
         assert (b.kernel, b.strip_height) in [(GABP_KERNEL_SWEEP, h) for h in (16, 32, 64, 128)] + \
-            [(GABP_KERNEL_TMA, 22), (GABP_KERNEL_TMA, 30)]
+            [(GABP_KERNEL_TMA, 14), (GABP_KERNEL_TMA, 22), (GABP_KERNEL_TMA, 30)]
         b.iterate(-1, 0.3)
         res = b.residuals()
         assert np.all(res <= 1e-5)
