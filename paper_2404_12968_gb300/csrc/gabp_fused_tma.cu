@@ -36,43 +36,15 @@
 
 #include "gabp_device.cuh"
 #include "gabp_internal.h"
+#include "gabp_packed.cuh"
 
 namespace gabp {
 
 namespace {
 
+using namespace tiles;
+
 constexpr int TTX = 30;   // tile width in cells: window width 32
-
-// Schedule of a single-problem launch: runs of `run` tiles (one tile column of a band of `run`
-// tile rows; the last band may be shorter), run u = band * ntx + column, dealt round-robin over
-// the G blocks; step_x = G % ntx and step_b = G / ntx advance a block to its next run.
-struct TileRuns {
-    int run, ntx, nty, step_x, step_b;
-};
-
-// A block's position on its schedule: run (cx, band), tile r of len in that run; len = 0 once
-// the block has no run left.
-struct TileWalk {
-    int cx, band, r, len;
-    __device__ __forceinline__ void start(int u, const TileRuns &tr) {
-        cx = u % tr.ntx;
-        band = u / tr.ntx;
-        r = 0;
-        len = max(0, min(tr.run, tr.nty - band * tr.run));
-    }
-    __device__ __forceinline__ void next(const TileRuns &tr) {
-        if (++r < len) return;
-        r = 0;
-        cx += tr.step_x;
-        band += tr.step_b;
-        if (cx >= tr.ntx) {
-            cx -= tr.ntx;
-            ++band;
-        }
-        len = max(0, min(tr.run, tr.nty - band * tr.run));
-    }
-    __device__ __forceinline__ int ty(const TileRuns &tr) const { return band * tr.run + r; }
-};
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -123,99 +95,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 
 __host__ __device__ constexpr size_t a128(size_t x) { return (x + 127) & ~size_t(127); }
 
-// ---- packed two-lane FP32 arithmetic on (eta, Lambda) pairs ----
-// Every (eta, Lambda) pair goes through the same sequence of roundings as the scalar formulas
-// in gabp_device.cuh (add_rn, mul_rn, fma_rn per component), so the results are bit-identical
-// to the other kernels; one packed instruction issues both components.
-__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {   // packed a - b, one instruction
-    unsigned long long ra, rb, rd;
-    memcpy(&ra, &a, 8);
-    memcpy(&rb, &b, 8);
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-    float2 d;
-    memcpy(&d, &rd, 8);
-    return d;
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-// Compensated (eta, Lambda) belief sums: TwoSum accumulation of both components at once.
-struct CompSum2 {
-    float2 hi, lo;
-    __device__ __forceinline__ explicit CompSum2(float2 first) : hi(first), lo(f2(0.f, 0.f)) {}
-    __device__ __forceinline__ void add(float2 x) {
-        const float2 t = add2(hi, x);
-        const float2 z = sub2(t, hi);
-        const float2 e = add2(sub2(hi, sub2(t, z)), sub2(x, z));
-        hi = t;
-        lo = add2(lo, e);
-    }
-    __device__ __forceinline__ void finish() {
-        const float2 t = add2(hi, lo);
-        lo = sub2(lo, sub2(t, hi));
-        hi = t;
-    }
-};
-
-// A compensated belief: hi = (eta_hi, Lambda_hi), lo = (eta_lo, Lambda_lo).
-struct Belief2 {
-    float2 hi, lo;
-};
-
-// Cavity (belief minus the edge's own message), (hi - own) + lo per component.
-__device__ __forceinline__ float2 cavity2(const Belief2 &b, float2 own) { return add2(sub2(b.hi, own), b.lo); }
-
-// Observation messages into one node from the base cells of one row, in increasing
-// observation index (the order every kernel uses): corner cl for [lo, mid), cr for [mid, hi).
-__device__ __forceinline__ void add_obs_pair2(CompSum2 &s, const float *O, int lo, int mid, int hi, int cl, int cr) {
-    for (int k = lo; k < hi; ++k) {
-        const int c = k < mid ? cl : cr;
-        s.add(*reinterpret_cast<const float2 *>(O + 8 * (int64_t)k + 2 * c));
-    }
-}
-
-// Factor-to-variable messages of a rank-1 factor with K slots on (eta, Lambda) pairs: the
-// arithmetic of factor_messages (App. A) with the (M, V) sums and the (eta, Lambda) outputs
-// carried as pairs.  cav[u] = cavity (eta, Lambda) of slot u; out[u] = message (eta, Lambda).
-// UNIT_A: every nonzero a_u^2 is at least 1.2e-18 (cell factors: -1 and kappa^2 + deg with
-// deg >= 1, as on every grid of four or more columns), so 1e-20 a_u^2 is a normal number and the
-// second floor of factor_messages is a no-op that can be left out.
-template <int K, bool UNIT_A>
-__device__ __forceinline__ void factor_messages2(const float (&a)[K], float var, float r, const float2 (&cav)[K],
-                                                 float2 (&out)[K]) {
-    float2 tp[K];   // (a eta / lam, a^2 / lam), lam floored as in factor_messages
-#pragma unroll
-    for (int u = 0; u < K; ++u) {
-        if (a[u] == 0.f) {
-            tp[u] = f2(0.f, 0.f);
-        } else {
-            const float a2 = mul_rn(a[u], a[u]);
-            float fl = mul_rn(lam_floor_rel<float>(), a2);
-            if (!UNIT_A) fl = fmaxf(fl, tiny_normal<float>());
-            const float rl = recip(fmaxf(cav[u].y, fl));
-            tp[u] = mul2(f2(a[u], a2), f2(mul_rn(cav[u].x, rl), rl));
-        }
-    }
-    float2 pre[K];   // prefix sums (M, V), V starting from var
-    pre[0] = f2(0.f, var);
-#pragma unroll
-    for (int v = 1; v < K; ++v) pre[v] = add2(pre[v - 1], tp[v - 1]);
-    float2 suf = f2(0.f, 0.f);
-#pragma unroll
-    for (int v = K - 1; v >= 0; --v) {
-        const float2 MV = add2(pre[v], suf);
-        const float rV = recip(MV.y);
-        out[v] = mul2(f2(mul_rn(a[v], add_rn(r, -MV.x)), mul_rn(a[v], a[v])), f2(rV, rV));
-        suf = add2(suf, tp[v]);
-    }
-}
-
-// Damped update of an (eta, Lambda) pair: fresh + beta (old - fresh) as one fused multiply-add.
-__device__ __forceinline__ float2 damp2(float2 old, float2 fresh, float2 beta2) {
-    return fma2(beta2, sub2(old, fresh), fresh);
-}
 
 // Update of the rank-1 factor of one cell (row of L, Eq. 5 / App. A): cavities of its five
 // slots from the compensated beliefs, the factor-to-variable messages, damping, and a
@@ -421,35 +300,31 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
             } else if (ok && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
                 const int rx = lane + 1, ry = ly + 1;
                 // observation ranges of the node: base row gy (corners 1, 0) and base row gy-1
-                // (corners 3, 2); the first message of each range is loaded before the prior
-                // sums, so that its latency overlaps them (the order of the sum is unchanged)
+                // (corners 3, 2; row -1 of the staged index is zero-filled, an empty range).  The
+                // first two messages of each range are loaded before the prior sums, so that their
+                // latency overlaps them (the order of the sum is unchanged).  A missing candidate
+                // is (-0, -0): adding -0 leaves a TwoSum's value unchanged, so the first candidates
+                // are added without a branch; the second ones only when some lane of the warp has
+                // one (a warp vote), as most warps have none.
                 int lo1 = 0, mid1 = 0, hi1 = 0, lo2 = 0, mid2 = 0, hi2 = 0;
-                float2 first1 = f2(0.f, 0.f), first2 = f2(0.f, 0.f), second1 = f2(0.f, 0.f), second2 = f2(0.f, 0.f);
+                const float2 nz = f2(-0.f, -0.f);
+                float2 first1 = nz, first2 = nz, second1 = nz, second2 = nz;
+                bool any2 = false;
                 if (m > 0) {
                     const bool last = gx == nx - 1;
                     mid1 = wptr(gx, gy);
                     lo1 = gx > 0 ? wptr(gx - 1, gy) : mid1;
                     hi1 = last ? mid1 : wptr(gx + 1, gy);
-                    if (gy > 0) {
-                        mid2 = wptr(gx, gy - 1);
-                        lo2 = gx > 0 ? wptr(gx - 1, gy - 1) : mid2;
-                        hi2 = last ? mid2 : wptr(gx + 1, gy - 1);
-                    }
-                    if (lo1 < hi1) {
-                        const int c = lo1 < mid1 ? 1 : 0;
-                        first1 = *reinterpret_cast<const float2 *>(O + 8 * (int64_t)lo1 + 2 * c);
-                    }
-                    if (lo1 + 1 < hi1) {
-                        const int c = lo1 + 1 < mid1 ? 1 : 0;
-                        second1 = *reinterpret_cast<const float2 *>(O + 8 * (int64_t)(lo1 + 1) + 2 * c);
-                    }
-                    if (lo2 < hi2) {
-                        const int c = lo2 < mid2 ? 3 : 2;
-                        first2 = *reinterpret_cast<const float2 *>(O + 8 * (int64_t)lo2 + 2 * c);
-                    }
-                    if (lo2 + 1 < hi2) {
-                        const int c = lo2 + 1 < mid2 ? 3 : 2;
-                        second2 = *reinterpret_cast<const float2 *>(O + 8 * (int64_t)(lo2 + 1) + 2 * c);
+                    mid2 = wptr(gx, gy - 1);
+                    lo2 = gx > 0 ? wptr(gx - 1, gy - 1) : mid2;
+                    hi2 = last ? mid2 : wptr(gx + 1, gy - 1);
+                    const float2 *O2 = reinterpret_cast<const float2 *>(O);   // (eta, Lambda) of k, corner c at 4 k + c
+                    if (lo1 < hi1) first1 = O2[4 * (int64_t)lo1 + (lo1 < mid1 ? 1 : 0)];
+                    if (lo2 < hi2) first2 = O2[4 * (int64_t)lo2 + (lo2 < mid2 ? 3 : 2)];
+                    any2 = __any_sync(__activemask(), lo1 + 1 < hi1 || lo2 + 1 < hi2);
+                    if (any2) {
+                        if (lo1 + 1 < hi1) second1 = O2[4 * (int64_t)(lo1 + 1) + (lo1 + 1 < mid1 ? 1 : 0)];
+                        if (lo2 + 1 < hi2) second2 = O2[4 * (int64_t)(lo2 + 1) + (lo2 + 1 < mid2 ? 3 : 2)];
                     }
                 }
                 CompSum2 s(sm[(DIR_C * RY + ry) * RX + rx]);
@@ -458,18 +333,16 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                 s.add(sm[(DIR_W * RY + ry) * RX + rx + 1]);
                 s.add(sm[(DIR_N * RY + ry - 1) * RX + rx]);
                 s.add(sm[(DIR_S * RY + ry + 1) * RX + rx]);
-                if (lo1 < hi1) {
+                if (m > 0) {
                     s.add(first1);
-                    if (lo1 + 1 < hi1) {
+                    if (any2) {
                         s.add(second1);
-                        add_obs_pair2(s, O, lo1 + 2, mid1, hi1, 1, 0);
+                        if (lo1 + 2 < hi1) add_obs_pair2(s, O, lo1 + 2, mid1, hi1, 1, 0);
                     }
-                }
-                if (lo2 < hi2) {
                     s.add(first2);
-                    if (lo2 + 1 < hi2) {
+                    if (any2) {
                         s.add(second2);
-                        add_obs_pair2(s, O, lo2 + 2, mid2, hi2, 3, 2);
+                        if (lo2 + 2 < hi2) add_obs_pair2(s, O, lo2 + 2, mid2, hi2, 3, 2);
                     }
                 }
                 s.finish();
@@ -556,20 +429,7 @@ __global__ void __launch_bounds__(TileLayout<TY, S, RW>::TNT, TileLayout<TY, S, 
                 const int lx = bx - x0 + 1, ly = r + 1;   // window coordinates of the base node
                 const Belief2 *ob[4] = {&sb[ly * BX + lx], &sb[ly * BX + lx + 1], &sb[(ly + 1) * BX + lx],
                                               &sb[(ly + 1) * BX + lx + 1]};
-                const float4 w4 = *reinterpret_cast<const float4 *>(Wt + 4 * k);
-                const float aw[4] = {w4.x, w4.y, w4.z, w4.w};
-                const float4 o01 = *reinterpret_cast<const float4 *>(O + 8 * k);   // (eta, Lambda) x 2
-                const float4 o23 = *reinterpret_cast<const float4 *>(O + 8 * k + 4);
-                float2 own4[4] = {f2(o01.x, o01.y), f2(o01.z, o01.w), f2(o23.x, o23.y), f2(o23.z, o23.w)}, cav[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) cav[u] = cavity2(*ob[u], own4[u]);
-                const float2 yv = *reinterpret_cast<const float2 *>(YV + 2 * k);
-                float2 msg[4];
-                factor_messages2<4, false>(aw, yv.y, yv.x, cav, msg);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) msg[u] = damp2(own4[u], msg[u], beta2);
-                *reinterpret_cast<float4 *>(OQ + 8 * k) = make_float4(msg[0].x, msg[0].y, msg[1].x, msg[1].y);
-                *reinterpret_cast<float4 *>(OQ + 8 * k + 4) = make_float4(msg[2].x, msg[2].y, msg[3].x, msg[3].y);
+                obs_factor2(ob, Wt, YV, O, OQ, k, beta2);
             }
         }
     }
