@@ -458,24 +458,31 @@ def pairwise_rate(p, device: int):
 
 
 def alpha4_rate(p, device: int):
-    """Iteration rate with the alpha = 4 prior (cell factors = rows of L^2, 13 slots; the split
-    kernels) on the same grid and observations: algorithmic bytes = 16 B per factor-variable
-    edge plus 20 B per observation, as for alpha = 2."""
+    """Iteration rate with the alpha = 4 prior (cell factors = rows of L^2, 13 slots) on the same
+    grid and observations, for the fused tile kernel (the FP32 default) and, for comparison, the
+    split kernels: algorithmic bytes = 16 B per factor-variable edge plus 20 B per observation,
+    as for alpha = 2."""
     import torch
-    from paper_2404_12968_gb300 import Solver
-    with Solver(p, precision="fp32", alpha=4, device=device) as s:
-        s.iterate(5, ALPHA4_DAMPING)
-        torch.cuda.synchronize(device)
-        t = time.perf_counter()
-        s.iterate(50, ALPHA4_DAMPING)
-        dt = (time.perf_counter() - t) / 50
-        st = s.stats()
+    from paper_2404_12968_gb300 import GABP_KERNEL_FUSED, GABP_KERNEL_SPLIT, Solver
+
+    def timed(kernel):
+        with Solver(p, precision="fp32", alpha=4, device=device, kernel=kernel) as s:
+            s.iterate(5, ALPHA4_DAMPING)
+            torch.cuda.synchronize(device)
+            t = time.perf_counter()
+            s.iterate(50, ALPHA4_DAMPING)
+            torch.cuda.synchronize(device)
+            return (time.perf_counter() - t) / 50, s.stats()
+
+    dt, st = timed(GABP_KERNEL_FUSED)
+    dt_split, _ = timed(GABP_KERNEL_SPLIT)
     nbytes = st["bytes_per_iter"]
     peak, _ = measured_peak_gbs()
     return {"ms_per_iter": dt * 1e3, "node_updates_per_s": p.n / dt, "edges": st["edges"],
             "algorithmic_gbs": nbytes / dt / 1e9, "frac_of_measured_hbm": nbytes / dt / 1e9 / peak,
-            "kernels": "k_beliefs_l2 + k_prior_l2 + k_obs", "damping": ALPHA4_DAMPING,
-            "accuracy": alpha4_accuracy(device)}
+            "kernels": "k_fused_l2 (28 x %d tiles, runs of %d)" % (st["tile_y"], st["tile_run"]),
+            "split_ms_per_iter": dt_split * 1e3, "split_kernels": "k_beliefs_l2 + k_prior_l2 + k_obs",
+            "damping": ALPHA4_DAMPING, "accuracy": alpha4_accuracy(device)}
 
 
 def alpha4_accuracy(device: int):

@@ -92,9 +92,11 @@ typedef struct {
     int alpha;     /* SPDE exponent (Sec. 3.1, (kappa^2 - Delta)^(alpha/2) f = W): 0 or 2 = the
                       operator L (one 5-slot factor per cell, a = row of L); 4 = L^2 (App. C,
                       powers of the operator: one 13-slot factor per cell, a = row of L^2,
-                      P = gamma (L^2)^T L^2).  alpha = 4 contexts run the split kernels
-                      (kernel AUTO or SPLIT, no tile shape) and their prior messages are 13
-                      planes; warm starts, multigrid and the pairwise form need alpha = 2
+                      P = gamma (L^2)^T L^2).  alpha = 4 contexts run, with FP32 messages, one
+                      fused tile kernel per iteration (kernel AUTO or FUSED; tiles 28x4, the
+                      default, or 28x8) or the split kernels (kernel SPLIT; the only form for
+                      FP64), with bit-identical messages; their prior messages are 13 planes;
+                      warm starts, multigrid and the pairwise form need alpha = 2
                       (GABP_ERR_STATE).  Other values: GABP_ERR_ARG. */
 } gabp_prior;
 
@@ -106,7 +108,8 @@ typedef struct {
     int tile_y;       /* fused-kernel tile height in cells; 0 = the default / autotuned shape.
                          GABP_KERNEL_FUSED: 32x8, 32x16, 32x32, 64x8, 64x16, 128x8;
                          GABP_KERNEL_TMA: 30x14, 30x22, 30x30;
-                         GABP_KERNEL_SWEEP: 30x16, 30x32, 30x64, 30x128 */
+                         GABP_KERNEL_SWEEP: 30x16, 30x32, 30x64, 30x128;
+                         GABP_KERNEL_FUSED with alpha = 4: 28x4, 28x8 */
     double tol;       /* relative-residual target of gabp_iterate(n < 0); default 1e-5 */
     int check_every;  /* iterations between residual checks when n < 0; default 50 */
     int max_iters;    /* iteration cap when n < 0; default 200000 */
@@ -121,7 +124,9 @@ typedef struct {
     int tile_run;     /* GABP_KERNEL_TMA: tiles per run of its schedule, 1..8 (the tile rows are cut
                          into bands of tile_run rows and a block walks one band's tile column top
                          to bottom, reusing two belief rows from tile to tile); 0 (default) = the
-                         length in 1..4 that balances the blocks best.  Results do not depend on
+                         length in 1..4 that balances the blocks best.  The fused alpha = 4
+                         kernel: the same, reusing four belief rows; 0 = the length among 1, 2,
+                         4, 8 and 16 that balances the blocks best.  Results do not depend on
                          it.  Other kernels ignore it; values outside 0..8: GABP_ERR_ARG. */
 } gabp_options;
 
@@ -136,7 +141,8 @@ typedef struct {
     int tile_x, tile_y;     /* tile shape in use by the fused kernel */
     double bytes_per_iter;  /* algorithmic HBM bytes of one iteration (messages read and
                                written once, plus the static observation data) */
-    int tile_run;           /* tiles per run of the TMA kernel's schedule (0 for other kernels) */
+    int tile_run;           /* tiles per run of the TMA or fused alpha = 4 kernel's schedule (0 for
+                               other kernels) */
 } gabp_stats;
 
 /* Fill *opt with the defaults listed above. */

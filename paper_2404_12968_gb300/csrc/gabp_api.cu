@@ -43,6 +43,7 @@ struct gabp_ctx {
     int kernel = GABP_KERNEL_FUSED;
     gabp::FusedShape shape{64, 16};
     gabp::TmaMaps maps;
+    int l2_run = 0;               // alpha = 4 fused kernel: tiles per run
     int cur = 0;                  // buffer holding the current messages
     int64_t iters = 0;
     double last_res = NAN;
@@ -163,6 +164,7 @@ cudaError_t launch_iteration(gabp_ctx *c, int src, double beta, cudaStream_t st)
     if (c->kernel == GABP_KERNEL_SPLIT) return gabp::launch_split_iteration(c->p, src, beta, st);
     if (c->kernel == GABP_KERNEL_TMA) return gabp::launch_tma_iteration(c->p, c->maps, src, beta, st);
     if (c->kernel == GABP_KERNEL_SWEEP) return gabp::launch_sweep_iteration(c->p, src, beta, c->shape.ty, st);
+    if (c->p.order == 2) return gabp::launch_fused_l2_iteration(c->p, c->shape.ty, c->l2_run, src, beta, st);
     return gabp::launch_fused_iteration(c->p, src, beta, c->shape, st);
 }
 
@@ -426,10 +428,16 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
     if (o.kernel < GABP_KERNEL_AUTO || o.kernel > GABP_KERNEL_SWEEP) return fail(c, GABP_ERR_ARG, "bad kernel");
     if (!(o.tol > 0.0) || o.check_every < 1 || o.max_iters < 1) return fail(c, GABP_ERR_ARG, "bad tol/check_every/max_iters");
     if (o.tile_run < 0 || o.tile_run > 8) return fail(c, GABP_ERR_ARG, "tile_run must be 0..8");
-    if (alpha == 4 && ((o.kernel != GABP_KERNEL_AUTO && o.kernel != GABP_KERNEL_SPLIT) || o.tile_x || o.tile_y))
-        return fail(c, GABP_ERR_ARG, "the alpha = 4 prior runs the split kernels (kernel AUTO or SPLIT, no tile shape)");
     if (alpha == 4) {
-        // nothing else to check
+        // FP32: the fused tile kernel (AUTO or FUSED, tiles 28 x 4 or 28 x 8) or the split kernels;
+        // FP64: the split kernels
+        if (o.kernel != GABP_KERNEL_AUTO && o.kernel != GABP_KERNEL_SPLIT && o.kernel != GABP_KERNEL_FUSED)
+            return fail(c, GABP_ERR_ARG, "the alpha = 4 prior runs the fused or the split kernels");
+        if (o.kernel == GABP_KERNEL_FUSED && o.precision != GABP_FP32)
+            return fail(c, GABP_ERR_ARG, "the fused alpha = 4 kernel needs FP32 messages");
+        const bool fused = o.precision == GABP_FP32 && o.kernel != GABP_KERNEL_SPLIT;
+        if ((o.tile_x || o.tile_y) && !(fused && o.tile_x == 28 && gabp::fused_l2_shape_supported(o.tile_y)))
+            return fail(c, GABP_ERR_ARG, "unsupported tile shape for the alpha = 4 prior (fused kernel: 28 x 4 or 28 x 8)");
     } else {
         // the kernel AUTO resolves to: the sweep for FP32, the plain fused kernel for FP64
         const int k = o.kernel != GABP_KERNEL_AUTO
@@ -654,7 +662,8 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
         return fail(c, GABP_ERR_ARG, "the TMA kernel needs FP32 messages and nx a multiple of 4");
     if (o.kernel == GABP_KERNEL_SWEEP && p.prec != 0)
         return fail(c, GABP_ERR_ARG, "the sweep kernel needs FP32 messages");
-    if (o.kernel == GABP_KERNEL_SPLIT || p.order == 2) c->kernel = GABP_KERNEL_SPLIT;
+    if (p.order == 2) c->kernel = o.kernel == GABP_KERNEL_SPLIT || p.prec ? GABP_KERNEL_SPLIT : GABP_KERNEL_FUSED;
+    else if (o.kernel == GABP_KERNEL_SPLIT) c->kernel = GABP_KERNEL_SPLIT;
     else if (o.kernel == GABP_KERNEL_TMA || (o.kernel == GABP_KERNEL_AUTO && tma_ok)) c->kernel = GABP_KERNEL_TMA;
     else if (o.kernel == GABP_KERNEL_SWEEP || (o.kernel == GABP_KERNEL_AUTO && p.prec == 0)) c->kernel = GABP_KERNEL_SWEEP;
     else c->kernel = GABP_KERNEL_FUSED;
@@ -666,6 +675,10 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
         c->maps.run = o.tile_run ? o.tile_run : gabp::tma_choose_run(p, c->shape.ty);
     } else if (p.order == 2) {
         c->shape = {0, 0};
+        if (c->kernel == GABP_KERNEL_FUSED) {
+            c->shape = {28, o.tile_y ? o.tile_y : 4};
+            c->l2_run = o.tile_run ? o.tile_run : gabp::fused_l2_choose_run(p, c->shape.ty);
+        }
     } else if (o.tile_x) {
         c->shape = {o.tile_x, o.tile_y};
     } else {
@@ -977,7 +990,7 @@ int gabp_get_stats(const gabp_ctx *c, gabp_stats *s) {
     s->tile_x = c->shape.tx;
     s->tile_y = c->shape.ty;
     s->bytes_per_iter = c->bytes_per_iter;
-    s->tile_run = c->kernel == GABP_KERNEL_TMA ? c->maps.run : 0;
+    s->tile_run = c->kernel == GABP_KERNEL_TMA ? c->maps.run : c->p.order == 2 && c->kernel == GABP_KERNEL_FUSED ? c->l2_run : 0;
     return GABP_OK;
 }
 

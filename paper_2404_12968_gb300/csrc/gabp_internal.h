@@ -94,6 +94,12 @@ cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st);
 // launch_init_cold (which dispatches on p.order, as do launch_beliefs, launch_residual and
 // launch_msg_change)
 cudaError_t launch_l2_iteration(const DevProblem &p, int src, double beta, cudaStream_t st);
+// the same iteration as one fused FP32 kernel (gabp_fused_l2.cu): 28 x ty tiles (ty = 4 or 8),
+// runs of `run` tiles down a tile column; messages bit-identical to the split kernels'.
+// fused_l2_choose_run: the run length (1..16) that balances the persistent blocks for p.
+bool fused_l2_shape_supported(int ty);
+int fused_l2_choose_run(const DevProblem &p, int ty);
+cudaError_t launch_fused_l2_iteration(const DevProblem &p, int ty, int run, int src, double beta, cudaStream_t st);
 // ---- the paper's pairwise re-weighted form (gabp_pairwise.cu) ----
 // coefficients P_ii (n), h (n), P_{i, i + off_d} (12 n) in the context's precision; messages are
 // 12 n (a, b) pairs per buffer

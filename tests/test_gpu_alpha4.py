@@ -68,6 +68,41 @@ def test_converges_to_the_exact_mean(orc, prec, tol, err):
         assert rel_l2(mu, orc.exact_mean(fl, p.nx)) < err
 
 
+def _fp32_values(buf):
+    # messages as FP32 values (np.array_equal treats -0 and +0 as equal)
+    return buf.view(np.float32)
+
+
+@pytest.mark.parametrize("shape", [(23, 17), (5, 4), (2, 9), (64, 3), (40, 37), (120, 61), (173, 90)])
+@pytest.mark.parametrize("ty,run", [(8, 0), (4, 0), (8, 3)])
+def test_fused_kernel_matches_split(shape, ty, run):
+    """The fused alpha = 4 tile kernel gives the split kernels' messages bit for bit: shapes
+    smaller than a tile, with ragged edge tiles in both directions, and with interior tiles (a
+    window whose every source cell exists); both tile heights; runs of 1, 3 and the chosen
+    length (carried belief rows)."""
+    from paper_2404_12968_gb300 import GABP_KERNEL_FUSED, GABP_KERNEL_SPLIT
+    p = _problem(*shape, seed=11)
+    out = []
+    for kern, extra in ((GABP_KERNEL_SPLIT, {}), (GABP_KERNEL_FUSED, {"tile_x": 28, "tile_y": ty, "tile_run": run})):
+        with solver(p, "fp32", alpha=4, kernel=kern, **extra) as s:
+            s.iterate(25, 0.5)
+            st = s.stats()
+            out.append(_fp32_values(s.get_messages()))
+        assert st["kernel"] == kern
+        if kern == GABP_KERNEL_FUSED:
+            assert st["tile_y"] == ty and (run == 0 or st["tile_run"] == run) and st["tile_run"] >= 1
+    assert np.array_equal(out[0], out[1])
+
+
+def test_fused_kernel_is_the_fp32_default():
+    from paper_2404_12968_gb300 import GABP_KERNEL_FUSED
+    p = _problem(60, 44)
+    with solver(p, "fp32", alpha=4) as s:
+        assert s.stats()["kernel"] == GABP_KERNEL_FUSED and s.stats()["tile_y"] == 4
+    with solver(p, "fp64", alpha=4) as s:
+        assert s.stats()["kernel"] == 2
+
+
 def test_message_change_and_checkpoint(orc):
     from oracle import early_stop as es
     p = _problem(30, 26, seed=9)
@@ -87,12 +122,19 @@ def test_message_change_and_checkpoint(orc):
 
 
 def test_alpha4_argument_and_state_errors():
-    from paper_2404_12968_gb300 import (GABP_KERNEL_TMA, GabpError, Multigrid, Pairwise)
+    from paper_2404_12968_gb300 import (GABP_KERNEL_FUSED, GABP_KERNEL_SPLIT, GABP_KERNEL_TMA, GabpError, Multigrid,
+                                        Pairwise)
     p = _problem(24, 20)
     with pytest.raises(GabpError, match="alpha must be 2 or 4"):
         solver(p, "fp32", alpha=3)
-    with pytest.raises(GabpError, match="split kernels"):
+    with pytest.raises(GabpError, match="fused or the split kernels"):
         solver(p, "fp32", alpha=4, kernel=GABP_KERNEL_TMA)
+    with pytest.raises(GabpError, match="needs FP32"):
+        solver(p, "fp64", alpha=4, kernel=GABP_KERNEL_FUSED)
+    with pytest.raises(GabpError, match="tile shape"):
+        solver(p, "fp32", alpha=4, tile_x=28, tile_y=16)
+    with pytest.raises(GabpError, match="tile shape"):
+        solver(p, "fp32", alpha=4, kernel=GABP_KERNEL_SPLIT, tile_x=28, tile_y=8)
     with solver(p, "fp32", alpha=4) as s:
         with pytest.raises(GabpError, match="alpha = 4"):
             s.warm_start(np.zeros(p.n), np.ones(p.n))
