@@ -8,9 +8,10 @@ belief sums, damping 0.3.  One step = ITERS_PER_STEP synchronous GaBP iterations
 kernel, CUDA-graph replays) + the FP64 relative residual + the marginal means, all on
 device-resident inputs.  The metric is node-updates/s = nodes x iterations / GPU time.
 
-`e2e` repeats the step through the public C ABI from host buffers: gabp_create from the host
-observation arrays (upload, sort, FP64 precompute), the iterations, the residual, the
-marginal means copied back to host memory, gabp_destroy.
+`e2e` repeats the step through the public C ABI from pinned host buffers: gabp_create from the
+host observation arrays (validation, upload, then on the GPU the sort by base cell and the FP64
+precompute), the iterations, the residual, the marginal means copied back to host memory,
+gabp_destroy.
 
 Under torchrun (N > 1) every rank solves its own instance (an ensemble member with its own
 seed): weak scaling, no collective on the data path; a barrier and a max over ranks frame
@@ -298,10 +299,16 @@ def own_arm(args):
         accuracy = main_accuracy(s, p, residuals[-1], (args.warmup + args.steps) * ITERS_PER_STEP)
     s.close()
 
-    # end to end through the public API from host buffers
-    obs_xy = np.ascontiguousarray(np.stack([p.obs_x, p.obs_y], 1))
-    y = np.ascontiguousarray(p.y)
-    nv = np.ascontiguousarray(p.noise_var)
+    # end to end through the public API from host buffers (pinned, as a caller streaming
+    # assimilation windows would hold them)
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True).numpy()
+        t[...] = a
+        return t
+
+    obs_xy = pinned(np.stack([p.obs_x, p.obs_y], 1))
+    y = pinned(p.y)
+    nv = pinned(p.noise_var)
     mean_host = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
 
     def e2e_step():
@@ -335,9 +342,10 @@ def own_arm(args):
     peak, peak_kind = measured_peak_gbs()
     achieved = st["bytes_per_iter"] / (iter_ms / 1e3) / 1e9
     traffic = profiled_traffic(KERNEL_NAMES[st["kernel"]])
-    # what gabp_create copies to the device: the sorted observations (x, y, value, variance as
-    # doubles) and their base cells (int32); the per-cell index is built on the device
-    h2d = 32 * p.m + 4 * p.m
+    # what gabp_create copies to the device: the observations as given (x, y, value, variance as
+    # doubles); their base cells, their order by base cell and the per-cell index are built on
+    # the device
+    h2d = 32 * p.m
     d2h = 8 * n + 16                          # marginal means + residual scalars
     launches_per_step = ITERS_PER_STEP + 6 + 2
     line = {

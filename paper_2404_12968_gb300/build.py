@@ -19,7 +19,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgabp.so")
 
 SOURCES = ["gabp_api.cu", "gabp_split.cu", "gabp_fused.cu", "gabp_fused_tma.cu", "gabp_fused_l2.cu", "gabp_sweep.cu",
-           "gabp_noalloc.cu", "gabp_nn_kernels.cu", "gabp_nn_tc.cu", "gabp_pairwise.cu", "gabp_wsnet.cu"]
+           "gabp_noalloc.cu", "gabp_obs_sort.cu", "gabp_nn_kernels.cu", "gabp_nn_tc.cu", "gabp_pairwise.cu", "gabp_wsnet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
            "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -60,7 +60,10 @@ struct gabp_ctx {
     double kappa = 0.0;
     double yscale = 1.0;          // spread of the observed values (network input scale)
     void *ws_x = nullptr;         // network input buffer (allocated on first use)
-    // host copy of the observations (sorted by base cell): the multigrid levels are built from it
+    // the observations sorted by base cell on the device (x, y pairs, then values, then noise
+    // variances; 4 m doubles), and a host copy made on first use: the multigrid levels are built
+    // from it
+    double *dsorted = nullptr;
     std::vector<double> hxy, hy, hvar;
     // prior mean (allocated on first use)
     double *fb = nullptr;         // n: prior mean f_b (NULL: zero)
@@ -453,9 +456,8 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
             return fail(c, GABP_ERR_ARG, "unsupported tile shape for the TMA kernel");
     }
     const int64_t n = (int64_t)nx * ny;
-    // validate the observations and compute their base cells (FP64 floor), in parallel chunks;
-    // the first invalid index decides the error
-    std::vector<int> base((size_t)m);
+    // validate the observations in parallel chunks; the first invalid index decides the error
+    // (their base cells and the order by base cell are computed on the GPU, below)
     const int nchunk = host_chunks(m);
     std::vector<int64_t> first_bad((size_t)nchunk, -1);
     std::vector<int> bad_kind((size_t)nchunk, 0);
@@ -471,10 +473,6 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
                 bad_kind[(size_t)ch] = kind;
                 return;
             }
-            int j0 = (int)std::floor(x), i0 = (int)std::floor(yy);
-            if (j0 > nx - 2) j0 = nx - 2;
-            if (i0 > ny - 2) i0 = ny - 2;
-            base[(size_t)k] = i0 * nx + j0;
         }
     });
     for (int ch = 0; ch < nchunk; ++ch) {
@@ -484,57 +482,6 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
         if (bad_kind[(size_t)ch] == 2) return fail(c, GABP_ERR_ARG, "observation " + std::to_string(k) + " outside the grid");
         return fail(c, GABP_ERR_ARG, "noise variance must be > 0");
     }
-    // stable LSD radix sort of the observations by base cell (two digits of half the key width,
-    // base < n <= 2^30): per chunk digit counts, offsets in (digit, chunk) order, then each
-    // chunk places its own elements in order, so the result is the stable order whatever the
-    // chunking; the per-cell index optr is then built on the GPU from the sorted base cells
-    std::vector<int> perm((size_t)m), tmp((size_t)m);
-    parallel_chunks(m, nchunk, [&](int, int64_t k0, int64_t k1) {
-        for (int64_t k = k0; k < k1; ++k) perm[(size_t)k] = (int)k;
-    });
-    {
-        int bits = 1;
-        while (bits < 30 && ((int64_t)1 << bits) < n) ++bits;
-        const int DIG = bits < 16 ? 8 : (bits + 1) / 2, NB = 1 << DIG;   // fewer buckets: cache-friendly scatter
-        std::vector<int64_t> cnt((size_t)nchunk * NB);
-        for (int pass = 0; pass < 2; ++pass) {
-            const int shift = pass * DIG;
-            parallel_chunks(m, nchunk, [&](int ch, int64_t k0, int64_t k1) {
-                int64_t *h = cnt.data() + (size_t)ch * NB;
-                std::fill(h, h + NB, 0);
-                for (int64_t k = k0; k < k1; ++k) ++h[(base[(size_t)perm[(size_t)k]] >> shift) & (NB - 1)];
-            });
-            int64_t run = 0;
-            for (int b = 0; b < NB; ++b)
-                for (int ch = 0; ch < nchunk; ++ch) {
-                    int64_t &v = cnt[(size_t)ch * NB + b];
-                    const int64_t t = v;
-                    v = run;
-                    run += t;
-                }
-            parallel_chunks(m, nchunk, [&](int ch, int64_t k0, int64_t k1) {
-                int64_t *o = cnt.data() + (size_t)ch * NB;
-                for (int64_t k = k0; k < k1; ++k) {
-                    const int src = perm[(size_t)k];
-                    tmp[(size_t)o[(base[(size_t)src] >> shift) & (NB - 1)]++] = src;
-                }
-            });
-            perm.swap(tmp);
-        }
-    }
-    std::vector<int> sbase((size_t)m);
-    std::vector<double> sxy((size_t)(2 * m)), sy((size_t)m), svar((size_t)m);
-    parallel_chunks(m, nchunk, [&](int, int64_t d0, int64_t d1) {
-        for (int64_t d = d0; d < d1; ++d) {
-            const int64_t k = perm[(size_t)d];
-            sbase[(size_t)d] = base[(size_t)k];
-            sxy[2 * (size_t)d] = obs_xy[2 * k];
-            sxy[2 * (size_t)d + 1] = obs_xy[2 * k + 1];
-            sy[(size_t)d] = y[k];
-            svar[(size_t)d] = noise_var[k];
-        }
-    });
-
     c->kappa = kappa;
     if (m >= 2) {
         // sample standard deviation of y: partial sums over a fixed partition (64 parts,
@@ -634,22 +581,30 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
     CK(cudaMallocHost((void **)&c->hscal, 4 * sizeof(double)), "alloc pinned scalars");
     CK(cudaMemsetAsync(p.scal, 0, 4 * sizeof(double), c->stream), "memset");
 
-    // upload the sorted observations; FP64 precompute of weights and 1/sigma^2 on the GPU (the
-    // raw values go through the staging buffer when it is large enough)
+    // upload the caller's observations as they are, then on the GPU: base cells, the stable
+    // sort by base cell (sorted raw data kept in c->dsorted: x, y pairs, values, variances),
+    // FP64 precompute of weights and 1/sigma^2.  The raw copy and the sort's scratch go through
+    // the staging buffer when it is large enough.
     if (m > 0) {
+        if ((rc = dalloc(c, &q, 4 * (size_t)m * sizeof(double), "alloc sorted observations"))) return rc;
+        c->dsorted = (double *)q;
+        const size_t need = 4 * (size_t)m * sizeof(double) + gabp::obs_sort_scratch_bytes(m);
         double *raw = nullptr;
-        const bool own_raw = 4 * m > 2 * n;
-        if (own_raw) CK(cudaMalloc((void **)&raw, 4 * (size_t)m * sizeof(double)), "alloc raw observations");
+        const bool own_raw = need > 2 * (size_t)n * sizeof(double);
+        if (own_raw) CK(cudaMalloc((void **)&raw, need), "alloc raw observations");
         else raw = c->stage;
-        cudaError_t e = cudaMemcpyAsync(raw, sxy.data(), 2 * (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 2 * m, sy.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 3 * m, svar.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync((void *)p.obase, sbase.data(), (size_t)m * sizeof(int), cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = gabp::launch_obs_precompute(p, raw, raw + 2 * m, raw + 3 * m, c->stream);
+        cudaError_t e = cudaMemcpyAsync(raw, obs_xy, 2 * (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 2 * m, y, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(raw + 3 * m, noise_var, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        double *sxy = c->dsorted, *sy = sxy + 2 * m, *svar = sxy + 3 * m;
+        if (e == cudaSuccess)
+            e = gabp::launch_obs_sort(m, nx, ny, raw, raw + 2 * m, raw + 3 * m, (int *)p.obase, sxy, sy, svar, raw + 4 * m,
+                                      c->stream);
+        if (e == cudaSuccess) e = gabp::launch_obs_precompute(p, sxy, sy, svar, c->stream);
         if (e == cudaSuccess && p.prec == 0) e = gabp::launch_df_precompute(p, c->stream);
         if (e == cudaSuccess && own_raw) e = cudaStreamSynchronize(c->stream);
         if (own_raw) cudaFree(raw);
-        if (e != cudaSuccess) return cuda_fail(c, e, "observation upload/precompute");
+        if (e != cudaSuccess) return cuda_fail(c, e, "observation upload/sort/precompute");
     }
     CK(gabp::launch_obs_pointers(p, c->stream), "observation pointers");
     CK(gabp::launch_rhs_norm(p, c->stream), "rhs norm");
@@ -695,9 +650,6 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
     }
     const double ebytes = 4.0 * (double)T;    // (eta, Lambda) read + write per edge
     c->bytes_per_iter = ebytes * (double)c->edges + 5.0 * (double)T * (double)m;
-    c->hxy = std::move(sxy);
-    c->hy = std::move(sy);
-    c->hvar = std::move(svar);
     return GABP_OK;
 }
 
@@ -1769,6 +1721,19 @@ int gabp_mg_create(gabp_mg **out, gabp_ctx *ctx, int levels) {
     g->levels = levels;
     g->lv.assign((size_t)levels, nullptr);
     DeviceGuard dg(ctx->dev);
+    if (m > 0 && ctx->hxy.empty()) {   // host copy of the sorted observations, once
+        std::vector<double> h(4 * (size_t)m);
+        if (cudaMemcpyAsync(h.data(), ctx->dsorted, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            delete g;
+            return fail(ctx, GABP_ERR_CUDA, "multigrid: observation download");
+        }
+        ctx->hxy.assign(h.begin(), h.begin() + 2 * m);
+        ctx->hy.assign(h.begin() + 2 * m, h.begin() + 3 * m);
+        ctx->hvar.assign(h.begin() + 3 * m, h.end());
+    }
     std::vector<double> xy((size_t)(2 * m));
     int rc = GABP_OK;
     for (int k = 1; k < levels && rc == GABP_OK; ++k) {

@@ -87,6 +87,13 @@ cudaError_t launch_obs_precompute(const DevProblem &p, const double *raw_xy, con
 cudaError_t launch_rhs_norm(const DevProblem &p, cudaStream_t st);   // scal[1] = ||b||^2
 // optr[c] = number of observations with base cell < c (c = 0 .. n), from the sorted obase
 cudaError_t launch_obs_pointers(const DevProblem &p, cudaStream_t st);
+// ---- observation layout (gabp_obs_sort.cu) ----
+// Base cells of m observations at xy (device, input order; validated: inside the grid) and their
+// stable sort by base cell: obase (m ints) = the sorted base cells; sxy (2 m), sy, svar (m each)
+// = the raw data in that order.  scratch: obs_sort_scratch_bytes(m) bytes of device memory.
+size_t obs_sort_scratch_bytes(int64_t m);
+cudaError_t launch_obs_sort(int64_t m, int nx, int ny, const double *xy, const double *y, const double *var,
+                            int *obase, double *sxy, double *sy, double *svar, void *scratch, cudaStream_t st);
 // residual of the messages in buffer src; leaves ||r||^2 in scal[0] (beliefs recomputed)
 cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st);
 // ---- the alpha = 4 prior (order 2: cell factors = rows of L^2, 13 planes; gabp_split.cu) ----

@@ -1,0 +1,66 @@
+"""The observation layout that gabp_create builds on the GPU: base cells and the stable sort of
+the observations by base cell (ties in input order), the order of the observation messages in
+the message buffer.  Pinned against the oracle's bilinear rule and numpy's stable argsort on
+problems with heavy ties: thousands of observations in one cell (more than one sort chunk),
+ties spread over chunk boundaries, observations on the last grid lines (clamped base cells),
+and grids whose cell count needs one, two and three radix passes."""
+import numpy as np
+import pytest
+
+import gabp_synth
+from gpu_common import decode_messages, ensure_built, rel_l2, solver, sorted_obs_order
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def _tied_problem(nx, ny, m, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, nx - 1, m)
+    y = rng.uniform(0, ny - 1, m)
+    # a third of the observations in one cell, a tenth in a handful of cells, some on the last
+    # grid lines (their base cell is clamped to the last full cell)
+    a = m // 3
+    x[:a] = min(1, nx - 2) + 0.999 * rng.uniform(0, 1, a)
+    y[:a] = min(2, ny - 2) + 0.999 * rng.uniform(0, 1, a)
+    b = a + m // 10
+    cells = rng.integers(0, 6, b - a)
+    x[a:b] = np.minimum((cells % 3) + 0.25 + 0.5 * rng.uniform(0, 1, b - a), nx - 1)
+    y[a:b] = (ny - 2) + 0.5 * (cells // 3) * rng.uniform(0, 1, b - a)
+    x[b:b + 50] = nx - 1.0
+    y[b + 50:b + 100] = ny - 1.0
+    perm = rng.permutation(m)   # spread the tied groups over the input order
+    x, y = x[perm], y[perm]
+    noise = rng.uniform(0.01, 0.2, m)   # distinct: each observation recognisable by its Lambda
+    return gabp_synth.Problem(nx, ny, 0.3, x, y, rng.normal(size=m), noise)
+
+
+@pytest.mark.parametrize("nx,ny,m", [(9, 7, 5000), (70, 50, 9000), (300, 250, 20000), (2, 2, 3000)])
+def test_observation_messages_in_stable_base_order(orc, nx, ny, m):
+    """Cold-start observation messages are (0, w_c^2 / sigma^2) per corner: decoded from the
+    buffer, they must follow the oracle's stable order of the observations by base cell."""
+    p = _tied_problem(nx, ny, m, seed=nx * 7 + m)
+    order, base, w = sorted_obs_order(orc, p)
+    with solver(p, "fp64") as s:
+        _, obs = decode_messages(s.get_messages(), p, "fp64")
+    expect = (w ** 2 / p.noise_var[:, None])[order]
+    assert np.all(obs[:, :, 0] == 0.0)
+    np.testing.assert_allclose(obs[:, :, 1], expect, rtol=1e-12, atol=0)
+
+
+def test_tied_problem_iterates_match_oracle(orc):
+    """Iterates on a tie-heavy problem against the oracle's GaBP (the observation index and the
+    message order agree with each other)."""
+    from gpu_common import oracle_factors
+    p = _tied_problem(40, 30, 4000, seed=5)
+    fl = oracle_factors(orc, p)
+    mu0, var0, _ = orc.gabp(fl, 0.5, 30)
+    with solver(p, "fp64") as s:
+        s.iterate(30, 0.5)
+        mu, var = s.marginals()
+    assert rel_l2(mu, mu0) < 1e-10
+    assert np.max(np.abs(var - var0) / var0) < 1e-10
