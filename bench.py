@@ -76,15 +76,16 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = {"k_fused": "gabp_fused.cu", "k_fused_tma": "gabp_fused_tma.cu", "k_sweep": "gabp_sweep.cu",
-                  "k_beliefs+k_prior+k_obs": "gabp_split.cu"}
+# the sources of each iteration kernel (with gabp_device.cuh, shared by all of them)
+KERNEL_SOURCES = {"k_fused": ("gabp_fused.cu",), "k_fused_tma": ("gabp_fused_tma.cu", "gabp_packed.cuh"),
+                  "k_sweep": ("gabp_sweep.cu",), "k_beliefs+k_prior+k_obs": ("gabp_split.cu",)}
 
 
 def kernel_source_hash(kernel: str) -> str:
     import hashlib
     csrc = os.path.join(ROOT, "paper_2404_12968_gb300", "csrc")
     data = b""
-    for fn in (KERNEL_SOURCES[kernel], "gabp_device.cuh"):
+    for fn in (*KERNEL_SOURCES[kernel], "gabp_device.cuh"):
         with open(os.path.join(csrc, fn), "rb") as f:
             data += f.read()
     return hashlib.sha256(data).hexdigest()[:16]
