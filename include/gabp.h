@@ -67,7 +67,8 @@ extern "C" {
 
 /* iteration kernel (gabp_options.kernel) */
 #define GABP_KERNEL_AUTO 0   /* FP32: GABP_KERNEL_TMA if nx is a multiple of 4, else
-                                GABP_KERNEL_SWEEP; FP64: GABP_KERNEL_FUSED */
+                                GABP_KERNEL_SWEEP; FP64: GABP_KERNEL_FUSED.  The alpha = 4
+                                prior: GABP_KERNEL_FUSED (FP32), GABP_KERNEL_SPLIT (FP64) */
 #define GABP_KERNEL_FUSED 1  /* one fused kernel per iteration (beliefs + all factors) */
 #define GABP_KERNEL_SPLIT 2  /* three kernels per iteration: beliefs, prior factors, obs factors */
 #define GABP_KERNEL_TMA 3    /* the fused kernel as persistent blocks fed by TMA tensor loads;
@@ -103,7 +104,7 @@ typedef struct {
 typedef struct {
     int precision;    /* GABP_FP32 (default) or GABP_FP64 */
     int init;         /* GABP_INIT_COLD (default) or GABP_INIT_PAPER */
-    int kernel;       /* GABP_KERNEL_AUTO (default), _FUSED or _SPLIT */
+    int kernel;       /* GABP_KERNEL_AUTO (default), _FUSED, _SPLIT, _TMA or _SWEEP */
     int tile_x;       /* fused-kernel tile width in cells; 0 = the default / autotuned shape */
     int tile_y;       /* fused-kernel tile height in cells; 0 = the default / autotuned shape.
                          GABP_KERNEL_FUSED: 32x8, 32x16, 32x32, 64x8, 64x16, 128x8;
