@@ -94,8 +94,8 @@ typedef struct {
                       operator L (one 5-slot factor per cell, a = row of L); 4 = L^2 (App. C,
                       powers of the operator: one 13-slot factor per cell, a = row of L^2,
                       P = gamma (L^2)^T L^2).  alpha = 4 contexts run, with FP32 messages, one
-                      fused tile kernel per iteration (kernel AUTO or FUSED; tiles 28x4, the
-                      default, or 28x8) or the split kernels (kernel SPLIT; the only form for
+                      fused tile kernel per iteration (kernel AUTO or FUSED; tiles 28x8, the
+                      default, or 28x4) or the split kernels (kernel SPLIT; the only form for
                       FP64), with bit-identical messages; their prior messages are 13 planes;
                       warm starts, multigrid and the pairwise form need alpha = 2
                       (GABP_ERR_STATE).  Other values: GABP_ERR_ARG. */

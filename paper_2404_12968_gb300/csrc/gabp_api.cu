@@ -631,7 +631,7 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
     } else if (p.order == 2) {
         c->shape = {0, 0};
         if (c->kernel == GABP_KERNEL_FUSED) {
-            c->shape = {28, o.tile_y ? o.tile_y : 4};
+            c->shape = {28, o.tile_y ? o.tile_y : 8};
             c->l2_run = o.tile_run ? o.tile_run : gabp::fused_l2_choose_run(p, c->shape.ty);
         }
     } else if (o.tile_x) {

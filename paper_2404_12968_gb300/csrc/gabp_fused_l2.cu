@@ -9,8 +9,9 @@
 //      node v adds slot d of the factor of cell v - offset(d) for d = 0..12 (the 13 incoming
 //      prior messages, in slot order), then its observation messages in increasing observation
 //      index (corners 1, 0 from base row y, then 3, 2 from base row y - 1);
-//   B. updates the tile's cell factors (warp w takes tile row w, lanes 0..27) and then the
-//      observation factors based in the tile, writing the damped messages to the other buffer.
+//   B. updates the tile's cell factors (28 x 8 tiles: cell t on thread t, 7 full warps; 28 x 4:
+//      warp w takes tile row w, lanes 0..27) and then the observation factors based in the
+//      tile, writing the damped messages to the other buffer.
 // Beliefs (and the tile rows' observation ranges) are double-buffered by tile parity, so one
 // block barrier per tile separates their writers from their readers.  Inside a run (consecutive
 // tiles of one tile column) window rows 0..3 of a tile are rows TY..TY+3 of the previous tile's
@@ -221,21 +222,31 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY)
         }
         __syncthreads();
 
-        // ---- B: cell factors of the tile, then the observation factors based in it ----
-        {
-            const int gx = x0 + lane, gy = y0 + warp;
-            if (lane < LTX && gx < nx && gy < ny) {
+        // ---- B: cell factors of the tile, then the observation factors based in it.  When the
+        // tile's cells fill whole warps (28 x 8: 224 cells, 7 warps), cell t of the tile runs on
+        // thread t and the remaining warp starts the observation factors; otherwise warp w takes
+        // tile row w on lanes 0..27 ----
+        constexpr int NC = LTX * TY;
+        constexpr bool LINEAR = NC % 32 == 0 && NC < TNT;
+        auto cell = [&](int tx, int ty) {
+            const int gx = x0 + tx, gy = y0 + ty;
+            if (gx < nx && gy < ny) {
                 const int64_t c = (int64_t)gy * nx + gx;
-                const Belief2 *bc = &sb[(warp + 2) * BX + lane + 2];
+                const Belief2 *bc = &sb[(ty + 2) * BX + tx + 2];
                 if (gx >= 2 && gx < nx - 2 && gy >= 2 && gy < ny - 2)
                     cell_factor_l2<true>(p, gy, gx, bc, P + c, Q + c, pn, var, beta);
                 else
                     cell_factor_l2<false>(p, gy, gx, bc, P + c, Q + c, pn, var, beta);
             }
+        };
+        if constexpr (LINEAR) {
+            if (tid < NC) cell(tid % LTX, tid / LTX);
+        } else {
+            if (lane < LTX) cell(lane, warp);
         }
         if (m > 0) {
             const int total = rpre[TY];
-            for (int q = tid; q < total; q += TNT) {
+            for (int q = LINEAR ? (tid + TNT - NC) % TNT : tid; q < total; q += TNT) {
                 int lo = 0, hi = TY - 1;   // last row r with rpre[r] <= q
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;

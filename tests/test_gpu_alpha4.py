@@ -98,7 +98,7 @@ def test_fused_kernel_is_the_fp32_default():
     from paper_2404_12968_gb300 import GABP_KERNEL_FUSED
     p = _problem(60, 44)
     with solver(p, "fp32", alpha=4) as s:
-        assert s.stats()["kernel"] == GABP_KERNEL_FUSED and s.stats()["tile_y"] == 4
+        assert s.stats()["kernel"] == GABP_KERNEL_FUSED and s.stats()["tile_y"] == 8
     with solver(p, "fp64", alpha=4) as s:
         assert s.stats()["kernel"] == 2
 
