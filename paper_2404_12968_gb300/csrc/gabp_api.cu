@@ -456,56 +456,60 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
             return fail(c, GABP_ERR_ARG, "unsupported tile shape for the TMA kernel");
     }
     const int64_t n = (int64_t)nx * ny;
-    // validate the observations in parallel chunks; the first invalid index decides the error
-    // (their base cells and the order by base cell are computed on the GPU, below)
-    const int nchunk = host_chunks(m);
-    std::vector<int64_t> first_bad((size_t)nchunk, -1);
-    std::vector<int> bad_kind((size_t)nchunk, 0);
-    parallel_chunks(m, nchunk, [&](int ch, int64_t k0, int64_t k1) {
-        for (int64_t k = k0; k < k1; ++k) {
-            const double x = obs_xy[2 * k], yy = obs_xy[2 * k + 1];
-            int kind = 0;
-            if (!std::isfinite(x) || !std::isfinite(yy) || !std::isfinite(y[k]) || !std::isfinite(noise_var[k])) kind = 1;
-            else if (x < 0.0 || x > nx - 1.0 || yy < 0.0 || yy > ny - 1.0) kind = 2;
-            else if (!(noise_var[k] > 0.0)) kind = 3;
-            if (kind) {
-                first_bad[(size_t)ch] = k;
-                bad_kind[(size_t)ch] = kind;
-                return;
-            }
-        }
-    });
-    for (int ch = 0; ch < nchunk; ++ch) {
-        const int64_t k = first_bad[(size_t)ch];
-        if (k < 0) continue;
-        if (bad_kind[(size_t)ch] == 1) return fail(c, GABP_ERR_ARG, "non-finite observation data at index " + std::to_string(k));
-        if (bad_kind[(size_t)ch] == 2) return fail(c, GABP_ERR_ARG, "observation " + std::to_string(k) + " outside the grid");
-        return fail(c, GABP_ERR_ARG, "noise variance must be > 0");
-    }
     c->kappa = kappa;
-    if (m >= 2) {
-        // sample standard deviation of y: partial sums over a fixed partition (64 parts,
-        // whatever the thread count), added in part order
-        constexpr int PARTS = 64;
-        std::vector<double> part((size_t)PARTS);
-        auto sum_parts = [&](auto term) {
-            parallel_chunks(PARTS, host_chunks(m) > 1 ? (int)std::min<int64_t>(PARTS, host_chunks(m)) : 1,
-                            [&](int, int64_t q0, int64_t q1) {
-                                for (int64_t q = q0; q < q1; ++q) {
-                                    double acc = 0.0;
-                                    for (int64_t k = m * q / PARTS; k < m * (q + 1) / PARTS; ++k) acc += term(k);
-                                    part[(size_t)q] = acc;
-                                }
-                            });
-            double total = 0.0;
-            for (double v : part) total += v;
-            return total;
-        };
-        const double mean = sum_parts([&](int64_t k) { return y[k]; }) / (double)m;
-        const double sq = sum_parts([&](int64_t k) { return (y[k] - mean) * (y[k] - mean); });
-        const double sd = std::sqrt(sq / (double)(m - 1));
-        c->yscale = sd > 0.0 ? sd : 1.0;
-    }
+    // host checks of the observations, run while the GPU copies and sorts them (below; those
+    // kernels index nothing by the values, so invalid input cannot make them fault): validation
+    // in parallel chunks, the first invalid index deciding the error, then the spread of y
+    auto host_checks = [&]() -> int {
+        const int nchunk = host_chunks(m);
+        std::vector<int64_t> first_bad((size_t)nchunk, -1);
+        std::vector<int> bad_kind((size_t)nchunk, 0);
+        parallel_chunks(m, nchunk, [&](int ch, int64_t k0, int64_t k1) {
+            for (int64_t k = k0; k < k1; ++k) {
+                const double x = obs_xy[2 * k], yy = obs_xy[2 * k + 1];
+                int kind = 0;
+                if (!std::isfinite(x) || !std::isfinite(yy) || !std::isfinite(y[k]) || !std::isfinite(noise_var[k])) kind = 1;
+                else if (x < 0.0 || x > nx - 1.0 || yy < 0.0 || yy > ny - 1.0) kind = 2;
+                else if (!(noise_var[k] > 0.0)) kind = 3;
+                if (kind) {
+                    first_bad[(size_t)ch] = k;
+                    bad_kind[(size_t)ch] = kind;
+                    return;
+                }
+            }
+        });
+        for (int ch = 0; ch < nchunk; ++ch) {
+            const int64_t k = first_bad[(size_t)ch];
+            if (k < 0) continue;
+            if (bad_kind[(size_t)ch] == 1) return fail(c, GABP_ERR_ARG, "non-finite observation data at index " + std::to_string(k));
+            if (bad_kind[(size_t)ch] == 2) return fail(c, GABP_ERR_ARG, "observation " + std::to_string(k) + " outside the grid");
+            return fail(c, GABP_ERR_ARG, "noise variance must be > 0");
+        }
+        if (m >= 2) {
+            // sample standard deviation of y: partial sums over a fixed partition (64 parts,
+            // whatever the thread count), added in part order
+            constexpr int PARTS = 64;
+            std::vector<double> part((size_t)PARTS);
+            auto sum_parts = [&](auto term) {
+                parallel_chunks(PARTS, host_chunks(m) > 1 ? (int)std::min<int64_t>(PARTS, host_chunks(m)) : 1,
+                                [&](int, int64_t q0, int64_t q1) {
+                                    for (int64_t q = q0; q < q1; ++q) {
+                                        double acc = 0.0;
+                                        for (int64_t k = m * q / PARTS; k < m * (q + 1) / PARTS; ++k) acc += term(k);
+                                        part[(size_t)q] = acc;
+                                    }
+                                });
+                double total = 0.0;
+                for (double v : part) total += v;
+                return total;
+            };
+            const double mean = sum_parts([&](int64_t k) { return y[k]; }) / (double)m;
+            const double sq = sum_parts([&](int64_t k) { return (y[k] - mean) * (y[k] - mean); });
+            const double sd = std::sqrt(sq / (double)(m - 1));
+            c->yscale = sd > 0.0 ? sd : 1.0;
+        }
+        return GABP_OK;
+    };
     DevProblem &p = c->p;
     p.nx = nx;
     p.px = (t_pad_odd_planes && nx % 2 && alpha == 2) ? nx + 1 : nx;
@@ -602,8 +606,12 @@ int create_impl(gabp_ctx *c, gabp_grid grid, double kappa_h, const gabp_prior *p
                                       c->stream);
         if (e == cudaSuccess) e = gabp::launch_obs_precompute(p, sxy, sy, svar, c->stream);
         if (e == cudaSuccess && p.prec == 0) e = gabp::launch_df_precompute(p, c->stream);
-        if (e == cudaSuccess && own_raw) e = cudaStreamSynchronize(c->stream);
+        const int hrc = host_checks();
+        // invalid observations: nothing more is launched; wait for the copies of the caller's
+        // arrays before returning
+        if ((hrc != GABP_OK || own_raw) && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (own_raw) cudaFree(raw);
+        if (hrc != GABP_OK) return hrc;
         if (e != cudaSuccess) return cuda_fail(c, e, "observation upload/sort/precompute");
     }
     CK(gabp::launch_obs_pointers(p, c->stream), "observation pointers");

@@ -64,3 +64,25 @@ def test_tied_problem_iterates_match_oracle(orc):
         mu, var = s.marginals()
     assert rel_l2(mu, mu0) < 1e-10
     assert np.max(np.abs(var - var0) / var0) < 1e-10
+
+
+def test_invalid_observations_rejected_while_the_gpu_sorts():
+    """Creation validates the observations on the host while the GPU copies and sorts them: the
+    first invalid index decides the error, nothing faults on the invalid values (NaN, negative
+    or out-of-grid coordinates, zero variance), and a valid problem afterwards is unaffected."""
+    from paper_2404_12968_gb300 import GabpError
+    p = _tied_problem(70, 50, 9000, seed=3)
+    cases = []
+    x = p.obs_x.copy(); x[4321] = np.nan
+    cases.append((x, p.obs_y, p.noise_var, "non-finite observation data at index 4321"))
+    x = p.obs_x.copy(); x[17] = -3.0; x[5000] = 1e9
+    cases.append((x, p.obs_y, p.noise_var, "observation 17 outside the grid"))
+    v = p.noise_var.copy(); v[8999] = 0.0
+    cases.append((p.obs_x, p.obs_y, v, "noise variance must be > 0"))
+    for ox, oy, nv, msg in cases:
+        q = gabp_synth.Problem(p.nx, p.ny, p.kappa, ox, oy, p.y, nv)
+        with pytest.raises(GabpError, match=msg):
+            solver(q, "fp64")
+    with solver(p, "fp64") as s:
+        s.iterate(5, 0.5)
+        assert np.isfinite(s.residual())
