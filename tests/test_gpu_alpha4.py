@@ -73,13 +73,14 @@ def _fp32_values(buf):
     return buf.view(np.float32)
 
 
-@pytest.mark.parametrize("shape", [(23, 17), (5, 4), (2, 9), (64, 3), (40, 37), (120, 61), (173, 90)])
+@pytest.mark.parametrize("shape", [(23, 17), (5, 4), (2, 9), (64, 3), (40, 37), (120, 61), (173, 90), (610, 404)])
 @pytest.mark.parametrize("ty,run", [(8, 0), (4, 0), (8, 3)])
 def test_fused_kernel_matches_split(shape, ty, run):
     """The fused alpha = 4 tile kernel gives the split kernels' messages bit for bit: shapes
-    smaller than a tile, with ragged edge tiles in both directions, and with interior tiles (a
-    window whose every source cell exists); both tile heights; runs of 1, 3 and the chosen
-    length (carried belief rows)."""
+    smaller than a tile, with ragged edge tiles in both directions, with interior tiles (a
+    window whose every source cell exists), and large enough for long runs of tiles down each
+    column; both tile heights (28 x 8: one cell per thread; 28 x 4: one warp per row); runs of
+    3 and the chosen length (carried belief rows)."""
     from paper_2404_12968_gb300 import GABP_KERNEL_FUSED, GABP_KERNEL_SPLIT
     p = _problem(*shape, seed=11)
     out = []
