@@ -454,12 +454,16 @@ def pairwise_rate(p, device: int):
     14 coefficients per node per iteration (FP32: 248 B/node)."""
     import torch
     from paper_2404_12968_gb300 import Pairwise, Solver
-    with Solver(p, precision="fp32", device=device) as s, Pairwise(s) as pw:
+    stream = torch.cuda.Stream(device)   # CUDA events on the stream the iterations run on
+    with Solver(p, precision="fp32", device=device, stream=stream.cuda_stream) as s, Pairwise(s) as pw:
         pw.iterate(5, 20.0, 0.6)
         torch.cuda.synchronize(device)
-        t = time.perf_counter()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
         pw.iterate(50, 20.0, 0.6)
-        dt = (time.perf_counter() - t) / 50
+        t1.record(stream)
+        torch.cuda.synchronize(device)
+        dt = t0.elapsed_time(t1) / 1e3 / 50
     nbytes = 248.0 * p.n
     peak, _ = measured_peak_gbs()
     return {"ms_per_iter": dt * 1e3, "node_updates_per_s": p.n / dt, "algorithmic_gbs": nbytes / dt / 1e9,
@@ -474,14 +478,18 @@ def alpha4_rate(p, device: int):
     import torch
     from paper_2404_12968_gb300 import GABP_KERNEL_FUSED, GABP_KERNEL_SPLIT, Solver
 
+    stream = torch.cuda.Stream(device)   # CUDA events on the stream the iterations run on
+
     def timed(kernel):
-        with Solver(p, precision="fp32", alpha=4, device=device, kernel=kernel) as s:
+        with Solver(p, precision="fp32", alpha=4, device=device, kernel=kernel, stream=stream.cuda_stream) as s:
             s.iterate(5, ALPHA4_DAMPING)
             torch.cuda.synchronize(device)
-            t = time.perf_counter()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
             s.iterate(50, ALPHA4_DAMPING)
+            t1.record(stream)
             torch.cuda.synchronize(device)
-            return (time.perf_counter() - t) / 50, s.stats()
+            return t0.elapsed_time(t1) / 1e3 / 50, s.stats()
 
     dt, st = timed(GABP_KERNEL_FUSED)
     dt_split, _ = timed(GABP_KERNEL_SPLIT)
