@@ -830,13 +830,27 @@ int gabp_marginals(gabp_ctx *c, double *mean, double *var) {
     DeviceGuard g(c->dev);
     if (!g.ok) return fail(c, GABP_ERR_CUDA, "cudaSetDevice failed");
     const int64_t n = c->p.n;
-    const bool dmean = is_device_ptr(mean);
-    const bool dvar = var ? is_device_ptr(var) : true;
-    double *kmean = dmean ? mean : c->stage;
-    double *kvar = var ? (dvar ? var : c->stage + n) : nullptr;
+    // where the kernels write: device memory directly; pinned host memory through its device
+    // address (the stores cross the host link while the kernel runs, no second pass); other host
+    // memory through the staging buffer and a copy
+    auto target = [&](double *ptr, double *stage, bool &copy) -> double * {
+        copy = false;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            a.type = cudaMemoryTypeUnregistered;
+        }
+        if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return ptr;
+        if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<double *>(a.devicePointer);
+        copy = true;
+        return stage;
+    };
+    bool cmean = false, cvar = false;
+    double *kmean = target(mean, c->stage, cmean);
+    double *kvar = var ? target(var, c->stage + n, cvar) : nullptr;
     CK(gabp::launch_marginals(c->p, c->cur, kmean, kvar, c->stream), "marginal kernels");
-    if (!dmean) CK(cudaMemcpyAsync(mean, kmean, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy mean");
-    if (var && !dvar) CK(cudaMemcpyAsync(var, kvar, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy var");
+    if (cmean) CK(cudaMemcpyAsync(mean, kmean, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy mean");
+    if (cvar) CK(cudaMemcpyAsync(var, kvar, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy var");
     CK(cudaStreamSynchronize(c->stream), "marginals sync");
     return GABP_OK;
 }

@@ -86,3 +86,26 @@ def test_invalid_observations_rejected_while_the_gpu_sorts():
     with solver(p, "fp64") as s:
         s.iterate(5, 0.5)
         assert np.isfinite(s.residual())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_marginals_into_pinned_host_memory(precision):
+    """gabp_marginals writes into pinned host buffers through their device address, into other
+    host buffers through a staging copy, and into device buffers directly: the same values."""
+    import torch
+    from paper_2404_12968_gb300 import gabp_marginals
+    p = _tied_problem(70, 50, 3000, seed=8)
+    with solver(p, precision) as s:
+        s.iterate(20, 0.5)
+        ref_m, ref_v = s.marginals()                        # pageable numpy arrays
+        pm = torch.empty(p.n, dtype=torch.float64, pin_memory=True)
+        pv = torch.empty(p.n, dtype=torch.float64, pin_memory=True)
+        gabp_marginals(s.ctx, pm.numpy(), pv.numpy())
+        assert np.array_equal(pm.numpy(), ref_m) and np.array_equal(pv.numpy(), ref_v)
+        pm2 = torch.empty(p.n, dtype=torch.float64, pin_memory=True)
+        v2 = np.empty(p.n)                                  # pinned mean, pageable variance
+        gabp_marginals(s.ctx, pm2.numpy(), v2)
+        assert np.array_equal(pm2.numpy(), ref_m) and np.array_equal(v2, ref_v)
+        dm = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        gabp_marginals(s.ctx, dm, None)
+        assert np.array_equal(dm.cpu().numpy(), ref_m)
