@@ -42,12 +42,9 @@ __device__ __forceinline__ void node_rc(int64_t v, int nx, int &i, int &j) {
 inline dim3 row_grid(int nx, int ny) { return dim3((unsigned)((nx + TPB - 1) / TPB), (unsigned)std::min(ny, 65535)); }
 
 // ---- beliefs (App. A, state update): sum of every incoming message, compensated ----
-template <typename T> __global__ void k_beliefs(DevProblem p, int src) {
-    const int64_t v = gtid();
-    if (v >= p.n) return;
+// compensated belief of node v = (i, j) from the messages of buffer src
+template <typename T> __device__ __forceinline__ BeliefStore<T> node_belief(const DevProblem &p, int64_t v, int i, int j, int src) {
     const int nx = p.nx, ny = p.ny;
-    int i, j;
-    node_rc(v, nx, i, j);
     const T2<T> *P = (const T2<T> *)p.P[src];
     const T *O = (const T *)p.O[src];
     const int64_t pn = p.pn, pv = plane_at(p, i, j);
@@ -67,7 +64,15 @@ template <typename T> __global__ void k_beliefs(DevProblem p, int src) {
     sl.finish();
     BeliefStore<T> b;
     b.ehi = se.hi; b.elo = se.lo; b.lhi = sl.hi; b.llo = sl.lo;
-    ((BeliefStore<T> *)p.belief)[v] = b;
+    return b;
+}
+
+template <typename T> __global__ void k_beliefs(DevProblem p, int src) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    int i, j;
+    node_rc(v, p.nx, i, j);
+    ((BeliefStore<T> *)p.belief)[v] = node_belief<T>(p, v, i, j, src);
 }
 
 template <typename T> __device__ __forceinline__ Belief<T> load_belief(const DevProblem &p, int64_t v) {
@@ -509,15 +514,24 @@ __global__ void k_df_precompute(DevProblem p) {
 
 // mu = eta / Lambda from the compensated FP32 belief (hi + lo pairs): quotient of the leading
 // parts, one correction with the exact remainder eta - Lambda q1
-__global__ void k_mu_df(DevProblem p) {
-    const int64_t v = gtid();
-    if (v >= p.n) return;
-    const BeliefStore<float> b = ((const BeliefStore<float> *)p.belief)[v];
+// mu = eta / Lambda of a compensated FP32 belief as a double-float pair: the quotient of the
+// leading parts plus one correction from the exact remainder eta - Lambda q1
+__device__ __forceinline__ dfl df_belief_mean(const BeliefStore<float> &b) {
     const dfl eta = {b.ehi, b.elo}, lam = {b.lhi, b.llo};
     const float q1 = __fdiv_rn(eta.hi, lam.hi);
     const dfl r = df_add(eta, df_neg(df_mul(lam, {q1, 0.f})));
     const float q2 = __fdiv_rn(r.hi, lam.hi);
-    df_st((float2 *)p.mu64, v, df_fast2sum(q1, q2));
+    return df_fast2sum(q1, q2);
+}
+
+// the same mean straight from the messages of buffer src (the belief kept in registers, not
+// stored): the FP32 residual's first pass
+__global__ void k_mu_direct_df(DevProblem p, int src) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    int i, j;
+    node_rc(v, p.nx, i, j);
+    df_st((float2 *)p.mu64, v, df_belief_mean(node_belief<float>(p, v, i, j, src)));
 }
 
 // e_k = s_k (h_k . mu - y_k)
@@ -645,10 +659,7 @@ template <typename T> __global__ void k_marg(DevProblem p, double *mean, double 
         // FP32 beliefs (hi + lo pairs): the mean as the residual forms it, a double-float
         // quotient with one correction from the exact remainder, widened to FP64 once (no FP64
         // division: FP64 throughput is a small fraction of FP32 here)
-        const dfl eta = {b.ehi, b.elo}, lam = {b.lhi, b.llo};
-        const float q1 = __fdiv_rn(eta.hi, lam.hi);
-        const dfl r = df_add(eta, df_neg(df_mul(lam, {q1, 0.f})));
-        const dfl q = df_fast2sum(q1, __fdiv_rn(r.hi, lam.hi));
+        const dfl q = df_belief_mean(b);
         mean[v] = (double)q.hi + (double)q.lo;
         if (var) var[v] = 1.0 / ((double)b.lhi + (double)b.llo);
     } else {
@@ -931,6 +942,15 @@ cudaError_t launch_residual_mu(const DevProblem &p, cudaStream_t st) {
 }
 
 cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st) {
+    if (p.order == 1 && p.prec == 0) {
+        // FP32 messages: the residual in double-float arithmetic (FP32 pipes, ~48-bit significands)
+        k_mu_direct_df<<<nblocks(p.n), TPB, 0, st>>>(p, src);
+        if (p.m > 0) k_obs_err_df<<<nblocks(p.m), TPB, 0, st>>>(p);
+        k_Lmu_df<<<nblocks(p.n), TPB, 0, st>>>(p);
+        k_res_df<<<RES_BLOCKS, TPB, 0, st>>>(p);
+        k_final_sum<<<1, TPB, 0, st>>>(p.part, RES_BLOCKS, p.scal);
+        return cudaGetLastError();
+    }
     cudaError_t e = launch_beliefs(p, src, st);
     if (e != cudaSuccess) return e;
     if (p.order == 2) {
@@ -943,15 +963,6 @@ cudaError_t launch_residual(const DevProblem &p, int src, cudaStream_t st) {
         k_Lx<<<nblocks(p.n), TPB, 0, st>>>(p, p.z64, p.mu64);
         k_Lx<<<nblocks(p.n), TPB, 0, st>>>(p, p.mu64, p.z64);
         k_res<<<RES_BLOCKS, TPB, 0, st>>>(p);
-        k_final_sum<<<1, TPB, 0, st>>>(p.part, RES_BLOCKS, p.scal);
-        return cudaGetLastError();
-    }
-    if (p.prec == 0) {
-        // FP32 messages: the residual in double-float arithmetic (FP32 pipes, ~48-bit significands)
-        k_mu_df<<<nblocks(p.n), TPB, 0, st>>>(p);
-        if (p.m > 0) k_obs_err_df<<<nblocks(p.m), TPB, 0, st>>>(p);
-        k_Lmu_df<<<nblocks(p.n), TPB, 0, st>>>(p);
-        k_res_df<<<RES_BLOCKS, TPB, 0, st>>>(p);
         k_final_sum<<<1, TPB, 0, st>>>(p.part, RES_BLOCKS, p.scal);
         return cudaGetLastError();
     }
