@@ -348,7 +348,7 @@ def own_arm(args):
     # the device
     h2d = 32 * p.m
     d2h = 8 * n + 16                          # marginal means + residual scalars
-    launches_per_step = ITERS_PER_STEP + 5 + 2   # iterations, residual (5 kernels), marginal means (2)
+    launches_per_step = ITERS_PER_STEP + 5 + 1   # iterations, residual (5 kernels), marginal means (1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -833,6 +833,7 @@ int gabp_marginals(gabp_ctx *c, double *mean, double *var) {
     // where the kernels write: device memory directly; pinned host memory through its device
     // address (the stores cross the host link while the kernel runs, no second pass); other host
     // memory through the staging buffer and a copy
+    bool mapped = false;   // a kernel writes across the host link
     auto target = [&](double *ptr, double *stage, bool &copy) -> double * {
         copy = false;
         cudaPointerAttributes a;
@@ -841,14 +842,17 @@ int gabp_marginals(gabp_ctx *c, double *mean, double *var) {
             a.type = cudaMemoryTypeUnregistered;
         }
         if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return ptr;
-        if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<double *>(a.devicePointer);
+        if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+            mapped = true;
+            return static_cast<double *>(a.devicePointer);
+        }
         copy = true;
         return stage;
     };
     bool cmean = false, cvar = false;
     double *kmean = target(mean, c->stage, cmean);
     double *kvar = var ? target(var, c->stage + n, cvar) : nullptr;
-    CK(gabp::launch_marginals(c->p, c->cur, kmean, kvar, c->stream), "marginal kernels");
+    CK(gabp::launch_marginals(c->p, c->cur, kmean, kvar, c->stream, !mapped), "marginal kernels");
     if (cmean) CK(cudaMemcpyAsync(mean, kmean, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy mean");
     if (cvar) CK(cudaMemcpyAsync(var, kvar, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy var");
     CK(cudaStreamSynchronize(c->stream), "marginals sync");

@@ -127,8 +127,12 @@ cudaError_t pw_marginals(const DevProblem &p, const void *Pd, const void *hv, co
                          double *var, int to_residual, cudaStream_t st);
 // residual of the mean already in p.mu64 (double-float pairs for FP32 contexts, FP64 otherwise)
 cudaError_t launch_residual_mu(const DevProblem &p, cudaStream_t st);
+// marginal means (and variances) into mean / var (device addresses; pinned host memory through
+// its device address).  direct: each node's belief formed in registers and the outputs written
+// at once (for outputs in device memory); otherwise the beliefs are stored first, so that a
+// kernel writing across the host link does not also hold the belief sums
 cudaError_t launch_marginals(const DevProblem &p, int src, double *mean, double *var,
-                             cudaStream_t st);
+                             cudaStream_t st, bool direct = true);
 
 // ---- learned warm start (gabp_split.cu kernels, network in gabp_wsnet.cu) ----
 cudaError_t launch_ws_input(const DevProblem &p, double scale, double kappa, int Hp, int Wp, void *x, cudaStream_t st);

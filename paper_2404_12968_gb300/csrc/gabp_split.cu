@@ -651,10 +651,9 @@ __global__ void k_res(DevProblem p) {
     if (threadIdx.x == 0) p.part[blockIdx.x] = s;
 }
 
-template <typename T> __global__ void k_marg(DevProblem p, double *mean, double *var) {
-    const int64_t v = gtid();
-    if (v >= p.n) return;
-    const BeliefStore<T> b = ((const BeliefStore<T> *)p.belief)[v];
+// marginal mean (and variance) of node v from its compensated belief
+template <typename T>
+__device__ __forceinline__ void marg_from_belief(const BeliefStore<T> &b, int64_t v, double *mean, double *var) {
     if constexpr (sizeof(T) == 4) {
         // FP32 beliefs (hi + lo pairs): the mean as the residual forms it, a double-float
         // quotient with one correction from the exact remainder, widened to FP64 once (no FP64
@@ -667,6 +666,22 @@ template <typename T> __global__ void k_marg(DevProblem p, double *mean, double 
         mean[v] = ((double)b.ehi + (double)b.elo) / L;
         if (var) var[v] = 1.0 / L;
     }
+}
+
+// the marginals straight from the messages of buffer src (the belief formed in registers)
+template <typename T> __global__ void k_marg(DevProblem p, int src, double *mean, double *var) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    int i, j;
+    node_rc(v, p.nx, i, j);
+    marg_from_belief<T>(node_belief<T>(p, v, i, j, src), v, mean, var);
+}
+
+// the marginals from the stored beliefs (the alpha = 4 prior's beliefs come from k_beliefs_l2)
+template <typename T> __global__ void k_marg_stored(DevProblem p, double *mean, double *var) {
+    const int64_t v = gtid();
+    if (v >= p.n) return;
+    marg_from_belief<T>(((const BeliefStore<T> *)p.belief)[v], v, mean, var);
 }
 
 // ---- learned warm start: network inputs, training targets, decoded initial beliefs ----
@@ -1025,11 +1040,16 @@ cudaError_t launch_ws_decode(const DevProblem &p, double scale, int Wp, const fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_marginals(const DevProblem &p, int src, double *mean, double *var, cudaStream_t st) {
-    cudaError_t e = launch_beliefs(p, src, st);
-    if (e != cudaSuccess) return e;
-    if (p.prec) k_marg<double><<<nblocks(p.n), TPB, 0, st>>>(p, mean, var);
-    else k_marg<float><<<nblocks(p.n), TPB, 0, st>>>(p, mean, var);
+cudaError_t launch_marginals(const DevProblem &p, int src, double *mean, double *var, cudaStream_t st, bool direct) {
+    if (p.order == 2 || !direct) {   // the beliefs first (13 planes; or outputs across the host link)
+        cudaError_t e = launch_beliefs(p, src, st);
+        if (e != cudaSuccess) return e;
+        if (p.prec) k_marg_stored<double><<<nblocks(p.n), TPB, 0, st>>>(p, mean, var);
+        else k_marg_stored<float><<<nblocks(p.n), TPB, 0, st>>>(p, mean, var);
+        return cudaGetLastError();
+    }
+    if (p.prec) k_marg<double><<<nblocks(p.n), TPB, 0, st>>>(p, src, mean, var);
+    else k_marg<float><<<nblocks(p.n), TPB, 0, st>>>(p, src, mean, var);
     return cudaGetLastError();
 }
 
